@@ -1,0 +1,224 @@
+/*
+ * ccw.h -- C ABI of the GB300 (sm_103a) CCWSIM best-match search library.
+ *
+ * CCWSIM (Bavandsavadkoohi et al., arXiv 2404.00441) simulates a categorical
+ * grid along a raster path of patches (Sec. 4.1). For every patch it takes
+ * the Haar DWT approximation of the patch's overlap data event (Sec. 4.2),
+ * cross-correlates it with every candidate position of the training image's
+ * (TI) approximation (Eq. CCW, Sec. 4.3), keeps the K best candidates, draws
+ * one (Algorithm 1, lines 11-12; Sec. 4.4), and pastes the Inverse-DWT of the
+ * drawn candidate (Algorithm 1, lines 13-14).
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are row-major with x fastest: a 2D grid of dims {nx, ny, 1} is
+ *    indexed x + nx*y, a 3D grid x + nx*(y + ny*z). dims[2] is 1 in 2D.
+ *  - Facies codes are uint8 in [0, n_facies); CCW_UNKNOWN (255) marks an
+ *    uninformed cell (or "no hard datum").
+ *  - Pointers named *_dev are device pointers on the current CUDA device;
+ *    the caller allocates them and keeps ownership. `stream` is a
+ *    cudaStream_t (NULL = legacy default stream). Every call is ordered on
+ *    `stream`; calls that say so synchronize it once before returning.
+ *  - Every call returns CCW_OK (0) or a negative CCW_E* code; the reason is
+ *    kept per host thread and read with ccw_last_error(). No C++ exception
+ *    crosses this boundary.
+ *  - Candidates are the origins x (level-J coordinates) with x + T/2^J <=
+ *    level-J TI size along every axis; candidate index = x fastest over the
+ *    candidate grid. Ranking order: hard-data mismatches ascending, score
+ *    descending, candidate index ascending.
+ *  - Scores are the full CCW similarity of the chosen score mode: one-hot
+ *    (default) sums Eq. CCW over the indicator image of every facies; the
+ *    literal mode applies Eq. CCW to the facies codes.
+ *  - Random draws use Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *    64-bit seed (low word first); the draw of patch p of realization r is
+ *    the first output word u of counter (r, p, 0, 0) and picks rank
+ *    floor(u * K' / 2^32), K' = min(K, P_c); an empty data event picks
+ *    candidate floor(u * P_c / 2^32).
+ */
+#ifndef CCW_H
+#define CCW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCW_OK 0
+#define CCW_EINVAL (-1)      /* bad argument or input value */
+#define CCW_ENOMEM (-2)      /* device allocation failed */
+#define CCW_ECUDA (-3)       /* a CUDA call failed */
+#define CCW_ETIMEOUT (-4)    /* a bounded device wait gave up */
+#define CCW_EUNSUPPORTED (-5)/* valid request this build does not handle */
+
+#define CCW_UNKNOWN 255
+#define CCW_MAX_TOPK 64
+#define CCW_LOG_FLAG_UNIFORM 1  /* patch log: empty data event, uniform pick */
+#define CCW_LOG_FLAG_DONE 2     /* patch log: the patch was simulated */
+
+/* Opaque TI state, owned by the library (device buffers on the device that
+ * was current at ccw_ti_prepare). */
+typedef struct ccw_ti ccw_ti;
+
+/* Simulation parameters (Algorithm 1 "Require" list: template and overlap
+ * size live in the ccw_ti; K, number of realizations here). */
+typedef struct {
+  int32_t ndim;        /* 2 or 3; must equal the TI's */
+  int32_t grid[3];     /* simulation grid dims {nx, ny, nz}; nz = 1 in 2D */
+  int32_t topk;        /* K, 1..CCW_MAX_TOPK (Algorithm 1, line 11) */
+  int32_t n_real;      /* realizations simulated by one call (>= 1) */
+  int32_t real_base;   /* id of the first realization (Philox counter word 0) */
+  int32_t path_random; /* 0: raster from the origin; 1: each realization
+                          mirrors its path along the axes given by bits of the
+                          first word of Philox counter (r, 0, 1, 0)
+                          (Algorithm 1, line 3) */
+  int32_t score_mode;  /* 0: one-hot facies indicators; 1: literal codes */
+  int32_t precision;   /* 0: exact FP32 FMA path (only value in this build) */
+  int32_t reserved[4]; /* must be 0 */
+} ccw_params;
+
+/* Shape information of a prepared TI. */
+typedef struct {
+  int32_t ndim, n_facies, level, scale; /* scale s = 2^level */
+  int32_t templ, overlap;               /* T, OR in fine cells */
+  int32_t dims[3];                      /* TI dims after cropping to multiples of s */
+  int32_t coarse[3];                    /* level-J dims = dims / s */
+  int32_t cand[3];                      /* candidate grid dims */
+  int64_t n_cand;                       /* P_c = product of cand */
+} ccw_ti_desc;
+
+/*
+ * ccw_ti_prepare -- Algorithm 1, line 2 (hoisted out of the realization
+ * loop): DWT of the TI at level J (Sec. 3.1, Sec. 4.2, Haar).
+ *  ti_dev    [dims[2]][dims[1]][dims[0]] uint8 facies codes, device.
+ *  dims      host array of 3 ints; dims[2] = 1 when ndim = 2.
+ *  n_facies  F in [2, 8]; every TI value must be < F.
+ *  level     J in [0, 4] for 2D, [0, 2] for 3D.
+ *  templ     T, overlap OR: fine cells, multiples of 2^J, T >= 2 OR, OR >= 0,
+ *            T <= TI size after cropping along every axis.
+ * The TI is cropped to multiples of s = 2^J (the candidate set is unchanged
+ * by the crop). Builds the level-J facies counts of every s^d block, the
+ * level-J code sums, and the full J-level Haar coefficient set of the codes
+ * (kept per s^d block) used by the Inverse-DWT. Synchronizes `stream` once
+ * to validate the TI values. *out receives the new handle; free it with
+ * ccw_ti_free. Errors: CCW_EINVAL (bad argument, TI value >= F, score range
+ * beyond the exact FP32 bound 2^24), CCW_ENOMEM, CCW_ECUDA.
+ */
+int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3],
+                   int32_t n_facies, int32_t level, int32_t templ, int32_t overlap,
+                   void* stream, ccw_ti** out);
+
+/* ccw_ti_describe -- fills *out with the shape of a prepared TI. */
+int ccw_ti_describe(const ccw_ti* ti, ccw_ti_desc* out);
+
+/* ccw_ti_free -- releases the handle and its device buffers (synchronizes the
+ * device first). NULL is accepted. */
+void ccw_ti_free(ccw_ti* ti);
+
+/*
+ * ccw_ti_export -- copies one of the prepared TI arrays to dst_dev (device,
+ * caller-sized), for inspection and tests:
+ *   what = 0: level-J facies counts, float32 [F-1][coarse], facies 0..F-2
+ *             (counts of every s^d block; the scaled-Haar approximation).
+ *   what = 1: level-J code sums, float32 [coarse].
+ *   what = 2: Haar coefficients of the codes, int16 [coarse][s^d]: for each
+ *             level-J block, the J-level scaled Haar transform of the block
+ *             computed in place (level j pairs samples 2^(j-1) apart along x,
+ *             then y, then z; the low-pass sum stays at the lower position,
+ *             the difference goes to the upper one), so entry 0 is the
+ *             block's approximation.
+ *   what = 3: the cropped TI, uint8 [dims].
+ */
+int ccw_ti_export(const ccw_ti* ti, int32_t what, void* dst_dev, void* stream);
+
+/*
+ * ccw_simulate -- Algorithm 1 for params->n_real realizations of one grid
+ * size, with hard-data conditioning (Sec. 4.4).
+ *  hd_cells_dev  int32 [n_hd][ndim] cell coordinates (x, y[, z]), device;
+ *                NULL when n_hd = 0. Every cell must lie inside the grid.
+ *  hd_vals_dev   uint8 [n_hd] facies codes (< F). Two hard data on one cell
+ *                keep the smaller code.
+ *  out_dev       uint8 [n_real][grid] realizations (caller-allocated).
+ *  patch_log_dev int32 [n_real][n_patches][4 + topk] or NULL: per patch, in
+ *                path order, {pick, score of pick, mismatches of pick, flags,
+ *                ranked candidates (unused slots -1)}; n_patches = product
+ *                over axes of 1 + ceil(max(grid - T, 0) / (T - OR)).
+ * The grid is padded to the patch lattice (T + (n - 1)(T - OR) per axis) and
+ * cropped at the end. Patches are processed in wavefronts w = i_x + 2 i_y +
+ * 4 i_z of the lattice index, which gives exactly the raster-order result
+ * because T >= 2 OR. Synchronizes `stream` once at the end to read the
+ * device status. Errors: CCW_EINVAL (parameters, hard data out of range or
+ * >= F, more than 1024 hard data in one template), CCW_ENOMEM, CCW_ECUDA.
+ */
+int ccw_simulate(const ccw_ti* ti, const ccw_params* params, const int32_t* hd_cells_dev,
+                 const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed, uint8_t* out_dev,
+                 int32_t* patch_log_dev, void* stream);
+
+/*
+ * ccw_ccf_search -- one batched best-match search step (Algorithm 1, lines
+ * 9-12; Eq. CCW; Sec. 4.4), for B independent data events.
+ *  de_dev     uint8 [B][T^d]: data events (the template window, codes or
+ *             255 where unknown; hard data must already be written in).
+ *  hd_dev     uint8 [B][T^d]: hard data of each window (255 = none), or NULL.
+ *  k          K in [1, CCW_MAX_TOPK]; score_mode 0 one-hot, 1 literal.
+ *  ctr_dev    uint32 [B][2]: (realization r, patch p) Philox counter words.
+ *  topk_*_dev int32 [B][k]: ranked candidates with their score and mismatch
+ *             count; slots past min(k, P_c), and all slots of an empty data
+ *             event, hold -1 / 0 / 0.
+ *  pick_dev   int32 [B]: the drawn candidate.
+ * Asynchronous. Input values outside [0, F) other than 255 are reported by
+ * ccw_ti_status. Errors: CCW_EINVAL, CCW_ENOMEM, CCW_ECUDA.
+ */
+int ccw_ccf_search(const ccw_ti* ti, int32_t B, const uint8_t* de_dev, const uint8_t* hd_dev,
+                   int32_t k, int32_t score_mode, uint64_t seed, const uint32_t* ctr_dev,
+                   int32_t* topk_idx_dev, int32_t* topk_score_dev, int32_t* topk_mis_dev,
+                   int32_t* pick_dev, void* stream);
+
+/*
+ * ccw_ccf_map -- the full CCW score map and hard-data mismatch map of B data
+ * events (Eq. CCW over every candidate), same inputs as ccw_ccf_search.
+ *  score_dev, mis_dev  int32 [B][P_c] (mis_dev may be NULL).
+ * An empty data event yields an all-zero map. Asynchronous.
+ */
+int ccw_ccf_map(const ccw_ti* ti, int32_t B, const uint8_t* de_dev, const uint8_t* hd_dev,
+                int32_t score_mode, int32_t* score_dev, int32_t* mis_dev, void* stream);
+
+/*
+ * ccw_idwt_paste -- Algorithm 1, lines 13-14: Inverse-DWT of candidate
+ * pick_dev[b] from the TI's approximation and detail coefficients, pasted
+ * with its first cell at dst_origin_dev[b] (int32 [B][3], x y z, may be
+ * negative) into sg_dev (uint8, dims sg_dims, host array of 3). Cells that
+ * fall outside the grid are skipped. Overlapping destinations within one
+ * call give an unspecified winner. Asynchronous.
+ */
+int ccw_idwt_paste(const ccw_ti* ti, int32_t B, const int32_t* pick_dev,
+                   const int32_t* dst_origin_dev, uint8_t* sg_dev, const int32_t sg_dims[3],
+                   void* stream);
+
+/*
+ * ccw_ti_status -- synchronizes `stream`, returns and clears the device
+ * status word of the handle: 0, or a bitwise OR of 1 (an input code >= F),
+ * 2 (more than 1024 hard data in one template), 4 (a bounded wait gave up).
+ */
+int ccw_ti_status(const ccw_ti* ti, void* stream, int32_t* status_out);
+
+/* ccw_last_error -- text of the last failure on the calling host thread. */
+const char* ccw_last_error(void);
+
+/*
+ * Profiling. When enabled, every launch of the search kernel is bracketed by
+ * CUDA events on its stream; ccw_profile_read returns the number of timed
+ * launches, their summed duration (ms, read after the stream synchronizes)
+ * and the algorithmic work they did: candidate evaluations and multiply-adds
+ * over the taps of the data events (masked level-J cells times channels).
+ * ccw_launch_count returns the number of kernels this library has launched
+ * in the process.
+ */
+int ccw_profile_enable(int32_t enable);
+int ccw_profile_read(int64_t* launches, double* total_ms, double* cand_evals, double* macs);
+int64_t ccw_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCW_H */

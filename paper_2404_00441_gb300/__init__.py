@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) CCWSIM best-match search: thin Python binding of libccw.so.
+
+Every step of the search runs in the library's CUDA kernels; this package only
+marshals arguments (PyTorch provides device memory and streams).
+"""
+from .ccw import (CCWError, TI, ccf_map, ccf_search, idwt_paste, launch_count,  # noqa: F401
+                  lattice, library_path, load, profile_enable, profile_read, simulate)

@@ -1,0 +1,255 @@
+"""ctypes binding of the C ABI in include/ccw.h (argument marshalling only).
+
+Tensors passed in must be contiguous CUDA tensors of the stated dtype on the
+current device; calls run on ``torch.cuda.current_stream()`` unless a stream is
+given. There is no CPU fallback: if ``libccw.so`` is missing the import of the
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libccw.so")
+_lib = None
+
+CCW_UNKNOWN = 255
+CCW_MAX_TOPK = 64
+
+
+class CCWError(RuntimeError):
+    pass
+
+
+class _Params(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("grid", C.c_int32 * 3), ("topk", C.c_int32),
+                ("n_real", C.c_int32), ("real_base", C.c_int32), ("path_random", C.c_int32),
+                ("score_mode", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("n_facies", C.c_int32), ("level", C.c_int32),
+                ("scale", C.c_int32), ("templ", C.c_int32), ("overlap", C.c_int32),
+                ("dims", C.c_int32 * 3), ("coarse", C.c_int32 * 3), ("cand", C.c_int32 * 3),
+                ("n_cand", C.c_int64)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libccw.so (built in-tree by ``paper_2404_00441_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: run paper_2404_00441_gb300.build.build() "
+                          "(nvcc, sm_103a) first; there is no CPU fallback")
+    lib = C.CDLL(_LIB_PATH)
+    P, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    lib.ccw_ti_prepare.argtypes = [P, i32, P, i32, i32, i32, i32, P, C.POINTER(P)]
+    lib.ccw_ti_describe.argtypes = [P, C.POINTER(_Desc)]
+    lib.ccw_ti_free.argtypes = [P]
+    lib.ccw_ti_free.restype = None
+    lib.ccw_ti_export.argtypes = [P, i32, P, P]
+    lib.ccw_simulate.argtypes = [P, C.POINTER(_Params), P, P, i32, u64, P, P, P]
+    lib.ccw_ccf_search.argtypes = [P, i32, P, P, i32, i32, u64, P, P, P, P, P, P]
+    lib.ccw_ccf_map.argtypes = [P, i32, P, P, i32, P, P, P]
+    lib.ccw_idwt_paste.argtypes = [P, i32, P, P, P, P, P]
+    lib.ccw_ti_status.argtypes = [P, P, C.POINTER(i32)]
+    lib.ccw_last_error.restype = C.c_char_p
+    lib.ccw_profile_enable.argtypes = [i32]
+    lib.ccw_profile_read.argtypes = [C.POINTER(i64), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.ccw_launch_count.restype = i64
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise CCWError(f"ccw error {rc}: {load().ccw_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _i3(v):
+    v = list(v) + [1] * (3 - len(v))
+    return (C.c_int32 * 3)(*v)
+
+
+def lattice(grid, T, O):
+    """Patches per axis and padded extent (Sec. 4.1 lattice), host-side."""
+    S = T - O
+    n, gp = [], []
+    for g in grid:
+        extra = max(g - T, 0)
+        n.append(1 + (extra + S - 1) // S)
+        gp.append(T + (n[-1] - 1) * S)
+    return tuple(n), tuple(gp)
+
+
+class TI:
+    """A training image prepared on the GPU (``ccw_ti_prepare``).
+
+    ``ti`` is a uint8 CUDA tensor [ny, nx] or [nz, ny, nx]."""
+
+    def __init__(self, ti: torch.Tensor, n_facies: int, level: int, templ: int, overlap: int,
+                 stream=None):
+        lib = load()
+        if ti.dtype != torch.uint8:
+            raise ValueError("TI must be uint8")
+        self.ndim = ti.dim()
+        dims = _i3(list(ti.shape)[::-1])
+        h = C.c_void_p()
+        _check(lib.ccw_ti_prepare(_ptr(ti), self.ndim, dims, n_facies, level, templ, overlap,
+                                  _stream(stream), C.byref(h)))
+        self._h = h
+        self._lib = lib
+        d = _Desc()
+        _check(lib.ccw_ti_describe(h, C.byref(d)))
+        self.n_facies = d.n_facies
+        self.level = d.level
+        self.scale = d.scale
+        self.templ = d.templ
+        self.overlap = d.overlap
+        self.dims = tuple(d.dims[:self.ndim])
+        self.coarse = tuple(d.coarse[:self.ndim])
+        self.cand = tuple(d.cand[:self.ndim])
+        self.n_cand = int(d.n_cand)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.ccw_ti_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def export(self, what: int, stream=None) -> torch.Tensor:
+        cshape = self.coarse[::-1]
+        sd = self.scale ** self.ndim
+        if what == 0:
+            out = torch.empty((self.n_facies - 1,) + cshape, dtype=torch.float32, device="cuda")
+        elif what == 1:
+            out = torch.empty(cshape, dtype=torch.float32, device="cuda")
+        elif what == 2:
+            out = torch.empty(cshape + (sd,), dtype=torch.int16, device="cuda")
+        elif what == 3:
+            out = torch.empty(self.dims[::-1], dtype=torch.uint8, device="cuda")
+        else:
+            raise ValueError(what)
+        _check(self._lib.ccw_ti_export(self._h, what, _ptr(out), _stream(stream)))
+        return out
+
+    def status(self, stream=None) -> int:
+        v = C.c_int32()
+        _check(self._lib.ccw_ti_status(self._h, _stream(stream), C.byref(v)))
+        return v.value
+
+
+def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None, real_base=0,
+             path_random=0, score_mode=0, precision=0, want_log=False, out=None, log=None,
+             stream=None):
+    """``ccw_simulate``: returns (realizations uint8 [n_real, *grid[::-1]], log or None)."""
+    lib = load()
+    p = _Params()
+    p.ndim = ti.ndim
+    p.grid = _i3(grid)
+    p.topk = topk
+    p.n_real = n_real
+    p.real_base = real_base
+    p.path_random = path_random
+    p.score_mode = score_mode
+    p.precision = precision
+    shape = (n_real,) + tuple(grid)[::-1]
+    if out is None:
+        out = torch.empty(shape, dtype=torch.uint8, device="cuda")
+    npch, _ = lattice(grid, ti.templ, ti.overlap)
+    n_patches = 1
+    for v in npch:
+        n_patches *= v
+    if want_log and log is None:
+        log = torch.empty((n_real, n_patches, 4 + topk), dtype=torch.int32, device="cuda")
+    n_hd = 0 if hd_vals is None else int(hd_vals.numel())
+    _check(lib.ccw_simulate(ti.handle, C.byref(p), _ptr(hd_cells) if n_hd else None,
+                            _ptr(hd_vals) if n_hd else None, n_hd, seed & (2 ** 64 - 1),
+                            _ptr(out), _ptr(log) if want_log else None, _stream(stream)))
+    return out, (log if want_log else None)
+
+
+def ccf_search(ti: TI, de: torch.Tensor, hd=None, k=1, score_mode=0, seed=0, ctr=None,
+               stream=None):
+    """``ccw_ccf_search`` on B data events de uint8 [B, T(, T), T]."""
+    lib = load()
+    B = de.shape[0]
+    if ctr is None:
+        ctr = torch.zeros((B, 2), dtype=torch.int32, device="cuda")
+    dev = de.device
+    ti_idx = torch.empty((B, k), dtype=torch.int32, device=dev)
+    ti_sc = torch.empty((B, k), dtype=torch.int32, device=dev)
+    ti_mm = torch.empty((B, k), dtype=torch.int32, device=dev)
+    pick = torch.empty((B,), dtype=torch.int32, device=dev)
+    _check(lib.ccw_ccf_search(ti.handle, B, _ptr(de), _ptr(hd), k, score_mode,
+                              seed & (2 ** 64 - 1), _ptr(ctr), _ptr(ti_idx), _ptr(ti_sc),
+                              _ptr(ti_mm), _ptr(pick), _stream(stream)))
+    return dict(topk_idx=ti_idx, topk_score=ti_sc, topk_mis=ti_mm, pick=pick)
+
+
+def ccf_map(ti: TI, de: torch.Tensor, hd=None, score_mode=0, stream=None):
+    """``ccw_ccf_map``: (scores int32 [B, P_c], mismatches int32 [B, P_c])."""
+    lib = load()
+    B = de.shape[0]
+    sc = torch.empty((B, ti.n_cand), dtype=torch.int32, device=de.device)
+    mm = torch.empty((B, ti.n_cand), dtype=torch.int32, device=de.device)
+    _check(lib.ccw_ccf_map(ti.handle, B, _ptr(de), _ptr(hd), score_mode, _ptr(sc), _ptr(mm),
+                           _stream(stream)))
+    return sc, mm
+
+
+def idwt_paste(ti: TI, picks: torch.Tensor, origins: torch.Tensor, sg: torch.Tensor,
+               stream=None):
+    """``ccw_idwt_paste`` into sg (uint8, [ny, nx] or [nz, ny, nx]) in place."""
+    lib = load()
+    _check(lib.ccw_idwt_paste(ti.handle, int(picks.numel()), _ptr(picks), _ptr(origins),
+                              _ptr(sg), _i3(list(sg.shape)[::-1]), _stream(stream)))
+    return sg
+
+
+def profile_enable(on: bool = True):
+    _check(load().ccw_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """(timed launches, total ms, candidate evaluations, multiply-adds)."""
+    n = C.c_int64()
+    ms, ce, mac = C.c_double(), C.c_double(), C.c_double()
+    _check(load().ccw_profile_read(C.byref(n), C.byref(ms), C.byref(ce), C.byref(mac)))
+    return n.value, ms.value, ce.value, mac.value
+
+
+def launch_count() -> int:
+    return int(load().ccw_launch_count())

@@ -1,0 +1,183 @@
+// prepare.cu -- training-image preparation (Algorithm 1, line 2: DWT of the
+// TI at level J), the hard-data overlay and the final crop of the simulation
+// grid.
+#include <algorithm>
+
+#include "ccw_internal.cuh"
+
+namespace ccw {
+
+// Copy the TI into its cropped buffer (dims multiples of s) and flag codes
+// >= F.
+__global__ void k_crop_ti(const uint8_t* __restrict__ src, int sx, int sy, uint8_t* __restrict__ dst,
+                          int nx, int ny, int nz, int F, int* status) {
+  const int64_t total = (int64_t)nx * ny * nz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const int y = (int)((i / nx) % ny);
+    const int z = (int)(i / ((int64_t)nx * ny));
+    const uint8_t v = src[x + (int64_t)sx * (y + (int64_t)sy * z)];
+    if (v >= F) atomicOr(status, kStatusBadCode);
+    dst[i] = v;
+  }
+}
+
+// Forward scaled Haar of one s^d block in place (the layout inverted by
+// haar_block_inverse in search.cu): level j = 1..J, axes x, y, z; samples
+// 2^(j-1) apart are replaced by their sum (lower position) and difference
+// (upper position).
+template <int D>
+__device__ void haar_block_forward(int* v, int s, int J) {
+  const int sz = (D == 3) ? s : 1;
+  for (int j = 1; j <= J; ++j) {
+    const int h = 1 << (j - 1);
+    for (int a = 0; a < D; ++a) {
+      const int stride = (a == 0) ? 1 : (a == 1 ? s : s * s);
+      const int hx = (a == 0) ? 2 * h : h, hy = (a == 1) ? 2 * h : h,
+                hz = (D == 3) ? ((a == 2) ? 2 * h : h) : 1;
+      for (int z = 0; z < sz; z += hz)
+        for (int y = 0; y < s; y += hy)
+          for (int x = 0; x < s; x += hx) {
+            const int p = x + s * (y + s * z), q = p + h * stride;
+            const int lo = v[p], hi = v[q];
+            v[p] = lo + hi;
+            v[q] = lo - hi;
+          }
+    }
+  }
+}
+
+// One thread per level-J block: facies counts (the level-J approximation of
+// each indicator image, facies 0..F-2), the code sum (approximation of the
+// code image) and the block's full J-level Haar coefficients of the codes.
+template <int D>
+__global__ void k_ti_pyramid(const uint8_t* __restrict__ ti, int nx, int ny, int ncx, int ncy,
+                             int ncz, int s, int J, int F, float* __restrict__ planes,
+                             int16_t* __restrict__ pyr) {
+  const int64_t ncv = (int64_t)ncx * ncy * ncz;
+  const int sd = (D == 3) ? s * s * s : s * s;
+  const int sz = (D == 3) ? s : 1;
+  int v[256];
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < ncv;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int bx = (int)(b % ncx);
+    const int by = (int)((b / ncx) % ncy);
+    const int bz = (int)(b / ((int64_t)ncx * ncy));
+    int counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int csum = 0;
+    for (int cz = 0; cz < sz; ++cz)
+      for (int cy = 0; cy < s; ++cy)
+        for (int cx = 0; cx < s; ++cx) {
+          const int gx = s * bx + cx, gy = s * by + cy, gz = (D == 3) ? s * bz + cz : 0;
+          const int c = ti[gx + (int64_t)nx * (gy + (int64_t)ny * gz)];
+          v[cx + s * (cy + s * cz)] = c;
+          csum += c;
+#pragma unroll
+          for (int f = 0; f < 8; ++f) counts[f] += (c == f);
+        }
+    for (int f = 0; f < F - 1; ++f) planes[f * ncv + b] = (float)counts[f];
+    planes[(int64_t)(F - 1) * ncv + b] = (float)csum;
+    haar_block_forward<D>(v, s, J);
+    int16_t* dst = pyr + b * sd;
+    for (int c = 0; c < sd; ++c) dst[c] = (int16_t)v[c];
+  }
+}
+
+// Hard-data overlay in grid coordinates; a cell with two hard data keeps the
+// smaller code (byte-wise atomic minimum by compare-and-swap on the word).
+__global__ void k_hd_overlay(const int32_t* __restrict__ cells, const uint8_t* __restrict__ vals,
+                             int n, int d, int gx, int gy, int gz, int F, uint8_t* overlay,
+                             int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int x = cells[i * d], y = cells[i * d + 1], z = (d == 3) ? cells[i * d + 2] : 0;
+  const unsigned v = vals[i];
+  if (x < 0 || y < 0 || z < 0 || x >= gx || y >= gy || z >= gz || v >= (unsigned)F) {
+    atomicOr(status, kStatusBadCode);
+    return;
+  }
+  const int64_t cell = x + (int64_t)gx * (y + (int64_t)gy * z);
+  unsigned int* word = reinterpret_cast<unsigned int*>(overlay + (cell & ~(int64_t)3));
+  const int sh = (int)(cell & 3) * 8;
+  unsigned int old = *word;
+  for (int it = 0; it < (1 << 20); ++it) {
+    const unsigned cur = (old >> sh) & 0xFFu;
+    if (v >= cur) return;
+    const unsigned int nw = (old & ~(0xFFu << sh)) | (v << sh);
+    const unsigned int prev = atomicCAS(word, old, nw);
+    if (prev == old) return;
+    old = prev;
+  }
+  atomicOr(status, kStatusTimeout);
+}
+
+// Crop the padded grids of n_real realizations into the caller's output.
+__global__ void k_crop_out(const uint8_t* __restrict__ sg, int64_t gp_vol, int gpx, int gpy,
+                           uint8_t* __restrict__ out, int gx, int gy, int gz, int d, int gpz,
+                           int path_random, uint64_t seed, int real_base) {
+  const int slot = blockIdx.y;
+  const uint32_t r = (uint32_t)(real_base + slot);
+  const uint32_t flips = path_random ? (draw_word(seed, r, 0u, 1u) & ((1u << d) - 1u)) : 0u;
+  const int ox = (flips & 1u) ? gpx - gx : 0;
+  const int oy = (flips & 2u) ? gpy - gy : 0;
+  const int oz = (flips & 4u) ? gpz - gz : 0;
+  const int64_t total = (int64_t)gx * gy * gz;
+  const uint8_t* src = sg + (int64_t)slot * gp_vol;
+  uint8_t* dst = out + (int64_t)slot * total;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % gx);
+    const int y = (int)((i / gx) % gy);
+    const int z = (int)(i / ((int64_t)gx * gy));
+    dst[i] = src[(x + ox) + (int64_t)gpx * ((y + oy) + (int64_t)gpy * (z + oz))];
+  }
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst, const int n[3],
+                           int F, int* status, cudaStream_t st) {
+  const int64_t total = (int64_t)n[0] * n[1] * n[2];
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_crop_ti<<<blocks, 256, 0, st>>>(src, sdims[0], sdims[1], dst, n[0], n[1], n[2], F, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ti_pyramid(int d, const uint8_t* ti, const int n[3], const int nc[3], int s,
+                              int J, int F, float* planes, int16_t* pyr, cudaStream_t st) {
+  const int64_t ncv = (int64_t)nc[0] * nc[1] * nc[2];
+  const int blocks = (int)std::min<int64_t>((ncv + 127) / 128, 152 * 16);
+  if (d == 3)
+    k_ti_pyramid<3><<<blocks, 128, 0, st>>>(ti, n[0], n[1], nc[0], nc[1], nc[2], s, J, F, planes,
+                                            pyr);
+  else
+    k_ti_pyramid<2><<<blocks, 128, 0, st>>>(ti, n[0], n[1], nc[0], nc[1], nc[2], s, J, F, planes,
+                                            pyr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hd_overlay(const int32_t* cells, const uint8_t* vals, int n, int d,
+                              const int g[3], int F, uint8_t* overlay, int* status,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_hd_overlay<<<(n + 255) / 256, 256, 0, st>>>(cells, vals, n, d, g[0], g[1], g[2], F, overlay,
+                                                status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crop_out(const uint8_t* sg, int64_t gp_vol, const int gp[3], uint8_t* out,
+                            const int g[3], int d, int n_real, int path_random, uint64_t seed,
+                            int real_base, cudaStream_t st) {
+  const int64_t total = (int64_t)g[0] * g[1] * g[2];
+  const int bx = (int)std::min<int64_t>((total + 255) / 256, 1024);
+  for (int r0 = 0; r0 < n_real; r0 += 65535) {
+    const int nr = std::min(65535, n_real - r0);
+    dim3 grid(bx, nr);
+    k_crop_out<<<grid, 256, 0, st>>>(sg + (int64_t)r0 * gp_vol, gp_vol, gp[0], gp[1],
+                                     out + (int64_t)r0 * total, g[0], g[1], g[2], d, gp[2],
+                                     path_random, seed, real_base + r0);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ccw

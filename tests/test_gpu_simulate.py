@@ -1,0 +1,139 @@
+"""GPU parity of whole simulations (Algorithm 1) against the CPU oracle.
+
+The CUDA path runs patches in wavefronts; the oracle runs the raster path one
+patch at a time. Realizations and patch logs must be identical.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from workloads import configs, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ccw():
+    import paper_2404_00441_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_pair(ccw, ti, F, J, T, Ov, grid, K, n_real=1, real_base=0, hd=None, seed=11,
+             path_random=0, score_mode=0):
+    g = ccw.TI(dev(ti), F, J, T, Ov)
+    hc = hv = None
+    if hd is not None:
+        hc, hv = dev(hd[0]), dev(hd[1])
+    out, log = ccw.simulate(g, grid, n_real=n_real, topk=K, seed=seed, hd_cells=hc, hd_vals=hv,
+                            real_base=real_base, path_random=path_random,
+                            score_mode=score_mode, want_log=True)
+    out, log = out.cpu().numpy(), log.cpu().numpy()
+    o = O.OracleTI(ti, F, J)
+    for i in range(n_real):
+        ref, rlog = o.simulate(grid, T, Ov, K=K, score_mode=score_mode,
+                               path_random=path_random,
+                               hd_cells=None if hd is None else hd[0],
+                               hd_vals=None if hd is None else hd[1], seed=seed,
+                               r=real_base + i)
+        assert np.array_equal(log[i], rlog), f"patch log of realization {i}"
+        assert np.array_equal(out[i], ref), f"realization {i}"
+    return out, log
+
+
+def test_c1_full_workload(ccw):
+    """Binary ribbon TI 250x250, one 250x250 realization, T40/OR10/J1, K=1."""
+    w = configs.workload("c1")
+    run_pair(ccw, w["ti"], w["F"], w["J"], w["T"], w["O"], w["grid"], w["K"], seed=w["seed"])
+
+
+def test_three_facies_hard_data_top5(ccw):
+    """c2 geometry (T64/OR16/J2, K=5, 3 facies, hard data) on a 520x456 grid,
+    two realizations with a realization offset and randomised paths."""
+    ti = configs.channel_lens_ti_1000()
+    field = synth.channel_lens_ti(520, 456, seed=3, tol=0.2)
+    hd = synth.sample_hard_data(field, 80, seed=4)
+    run_pair(ccw, ti, 3, 2, 64, 16, (520, 456), 5, n_real=2, real_base=7, hd=hd, seed=5,
+             path_random=1)
+
+
+def test_literal_score_mode(ccw):
+    ti = synth.channel_lens_ti(200, 180, seed=2, tol=0.2)
+    run_pair(ccw, ti, 3, 1, 16, 4, (90, 70), 3, score_mode=1, seed=3)
+
+
+def test_grid_smaller_than_template(ccw):
+    ti = configs.ribbon_ti_250()
+    run_pair(ccw, ti, 2, 1, 40, 10, (30, 22), 2, n_real=3, seed=8)
+
+
+def test_no_overlap(ccw):
+    """OR = 0: every data event is empty (uniform picks, Algorithm 1 line 6)."""
+    ti = configs.ribbon_ti_250()
+    run_pair(ccw, ti, 2, 1, 20, 0, (70, 50), 1, seed=2)
+
+
+def test_3d_four_facies_hard_data(ccw):
+    ti = synth.tube_lobe_ti_3d(60, 50, 40, seed=5)
+    field = synth.tube_lobe_ti_3d(50, 44, 30, seed=6)
+    hd = synth.sample_hard_data(field, 40, seed=7)
+    run_pair(ccw, ti, 4, 1, 12, 2, (50, 44, 30), 5, n_real=2, hd=hd, seed=9, path_random=1)
+
+
+def test_many_realizations_one_call(ccw):
+    ti = configs.ribbon_ti_250()
+    run_pair(ccw, ti, 2, 2, 32, 8, (100, 84), 4, n_real=6, real_base=100, seed=21)
+
+
+def test_full_size_c2_sampled(ccw):
+    """The 2000x2000 3-facies workload in the launch configuration the
+    benchmark times. Checked at full size:
+      * every hard datum is honoured;
+      * every cell equals the pattern of the last patch that covers it (the
+        Inverse-DWT paste), unless it holds a hard datum;
+      * for sampled patches, the data event rebuilt by replaying the logged
+        pastes of all earlier patches gives, in the oracle's search, exactly
+        the logged ranking, scores, mismatches and pick."""
+    w = configs.workload("c2")
+    ti, F, J, T, Ov, K, grid = w["ti"], w["F"], w["J"], w["T"], w["O"], w["K"], w["grid"]
+    cells, vals = w["hd"]
+    g = ccw.TI(dev(ti), F, J, T, Ov)
+    out, log = ccw.simulate(g, grid, n_real=1, topk=K, seed=w["seed"], hd_cells=dev(cells),
+                            hd_vals=dev(vals), want_log=True)
+    out, log = out.cpu().numpy()[0], log.cpu().numpy()[0]
+    assert np.array_equal(out[cells[:, 1], cells[:, 0]], vals)
+    o = O.OracleTI(ti, F, J)
+    npch, gp = O.lattice(2, grid, T, Ov)
+    S = T - Ov
+    hd_img = np.full((gp[1], gp[0]), 255, np.uint8)
+    hd_img[cells[:, 1], cells[:, 0]] = vals
+    # replay the pastes in raster order
+    state = np.full((gp[1], gp[0]), 255, np.uint8)
+    rng = np.random.default_rng(0)
+    n_patches = npch[0] * npch[1]
+    sample = set(rng.choice(n_patches, 24, replace=False).tolist()) | {0, 1, npch[0], n_patches - 1}
+    for p in range(n_patches):
+        iy, ix = divmod(p, npch[0])
+        oy, ox = S * iy, S * ix
+        win = (slice(oy, oy + T), slice(ox, ox + T))
+        hw = hd_img[win]
+        if p in sample:
+            de = np.where(hw != 255, hw, state[win])
+            ref = o.search(T, de, hw, K=K, seed=w["seed"], r=0, p=p)
+            e = log[p]
+            assert e[0] == ref["pick"], f"pick of patch {p}"
+            n = ref["n"]
+            if n:
+                assert np.array_equal(e[4:4 + n], ref["topk_idx"]), f"ranking of patch {p}"
+                sel = list(ref["topk_idx"]).index(ref["pick"])
+                assert e[1] == ref["topk_score"][sel] and e[2] == ref["topk_mis"][sel]
+        assert log[p, 3] & 2
+        pat = o.reconstruct(T, int(log[p, 0]))
+        state[win] = np.where(hw != 255, hw, pat)
+    assert np.array_equal(state[:grid[1], :grid[0]], out)

@@ -1,0 +1,66 @@
+"""The CUDA path runs the patches of one wavefront w = i_x + 2 i_y (+ 4 i_z)
+together. With T >= 2 OR this gives exactly the raster-order result of
+Algorithm 1: patches of one wavefront never share a cell, and every patch
+that shares a cell with patch p comes before p in both orders. Checked here
+on the CPU with the oracle's own search and reconstruction steps driven in
+wavefront order."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from workloads import synth
+
+
+def wave_of(ip):
+    return ip[0] + 2 * ip[1] + (4 * ip[2] if len(ip) > 2 else 0)
+
+
+@pytest.mark.parametrize("T,Ov", [(16, 4), (16, 8), (24, 6), (12, 2)])
+@pytest.mark.parametrize("d", [2, 3])
+def test_wavefront_dependencies(T, Ov, d):
+    S = T - Ov
+    n = (5, 4, 3)[:d]
+    pats = list(itertools.product(*[range(k) for k in n]))
+    def overlap(a, b):
+        return all(abs(x - y) * S < T for x, y in zip(a, b))
+    def raster(ip):
+        idx = 0
+        for ax in reversed(range(d)):
+            idx = idx * n[ax] + ip[ax]
+        return idx
+    for a in pats:
+        for b in pats:
+            if a == b or not overlap(a, b):
+                continue
+            assert wave_of(a) != wave_of(b)
+            assert (raster(a) < raster(b)) == (wave_of(a) < wave_of(b))
+
+
+def test_wavefront_driver_equals_raster_simulation():
+    ti = synth.channel_lens_ti(160, 150, seed=2, tol=0.2)
+    F, J, T, Ov, K = 3, 1, 16, 4, 3
+    grid = (75, 61)
+    cells, vals = synth.sample_hard_data(synth.channel_lens_ti(75, 61, seed=3, tol=0.3), 20, 4)
+    o = O.OracleTI(ti, F, J)
+    seed, r = 17, 2
+    ref, rlog = o.simulate(grid, T, Ov, K=K, hd_cells=cells, hd_vals=vals, seed=seed, r=r)
+    npch, gp = O.lattice(2, grid, T, Ov)
+    S = T - Ov
+    hd = np.full((gp[1], gp[0]), 255, np.uint8)
+    hd[cells[:, 1], cells[:, 0]] = vals
+    sg = np.full((gp[1], gp[0]), 255, np.uint8)
+    order = sorted(range(npch[0] * npch[1]),
+                   key=lambda p: (wave_of((p % npch[0], p // npch[0])), p))
+    order = order[::-1]                          # reversed inside each wave too
+    order = sorted(order, key=lambda p: wave_of((p % npch[0], p // npch[0])))
+    for p in order:
+        iy, ix = divmod(p, npch[0])
+        win = (slice(S * iy, S * iy + T), slice(S * ix, S * ix + T))
+        hw = hd[win]
+        de = np.where(hw != 255, hw, sg[win])
+        res = o.search(T, de, hw, K=K, seed=seed, r=r, p=p)
+        assert res["pick"] == rlog[p, 0]
+        sg[win] = np.where(hw != 255, hw, o.reconstruct(T, res["pick"]))
+    assert np.array_equal(sg[:grid[1], :grid[0]], ref)

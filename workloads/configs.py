@@ -1,0 +1,111 @@
+"""The five synthetic workloads (parameters and input draws only).
+
+The paper's TIs are unavailable (Sec. 5), so each workload draws a seeded
+stand-in with ``workloads.synth``:
+
+* ``c1`` -- 2D binary ribbon TI 250x250; one 250x250 realization, template
+  40, overlap 10, level 1, no hard data, K = 1.
+* ``c2`` -- 2D 3-facies channel/lens TI 1000x1000; one 2000x2000 realization,
+  template 64, overlap 16, level 2, 400 hard data drawn from a second field
+  (2000x2000, seed 3; sampling seed 4), K = 5.
+* ``c3`` -- c1's TI; 64 realizations of 1000x1000, template 64, overlap 16,
+  level 2, K = 1.
+* ``c4`` -- 3D 4-facies tube/lobe TI 180x150x120; 8 realizations of
+  200x200x100 and 8 of 100x100x100, template 24, overlap 6, level 1, 1000
+  hard data per grid size from a second field (seed 6), K = 5.
+* ``c5`` -- c1's TI; 256 realizations of 512x512, template 48, overlap 12,
+  level 2 (the learned-proposal geometry), K = 1.
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+
+import numpy as np
+
+from . import synth
+
+
+@lru_cache(maxsize=None)
+def ribbon_ti_250():
+    return synth.ribbon_ti(250, 250, n_ribbons=12, seed=1)
+
+
+@lru_cache(maxsize=None)
+def channel_lens_ti_1000():
+    return synth.channel_lens_ti(1000, 1000, seed=2)
+
+
+@lru_cache(maxsize=None)
+def hd_field_2000():
+    return synth.channel_lens_ti(2000, 2000, seed=3)
+
+
+@lru_cache(maxsize=None)
+def tube_ti_3d():
+    return synth.tube_lobe_ti_3d(180, 150, 120, seed=5)
+
+
+@lru_cache(maxsize=None)
+def hd_field_3d(nx, ny, nz):
+    return synth.tube_lobe_ti_3d(nx, ny, nz, seed=6)
+
+
+def workload(name: str) -> dict:
+    """Parameters and inputs of a workload; ``hd`` = (cells [n, ndim] int32
+    in (x, y[, z]) order, vals [n] uint8) or None."""
+    if name == "c1":
+        return dict(name="c1", ti=ribbon_ti_250(), F=2, J=1, T=40, O=10, K=1,
+                    grid=(250, 250), n_real=1, hd=None, seed=1)
+    if name == "c2":
+        cells, vals = synth.sample_hard_data(hd_field_2000(), 400, seed=4)
+        return dict(name="c2", ti=channel_lens_ti_1000(), F=3, J=2, T=64, O=16, K=5,
+                    grid=(2000, 2000), n_real=1, hd=(cells, vals), seed=2)
+    if name == "c3":
+        return dict(name="c3", ti=ribbon_ti_250(), F=2, J=2, T=64, O=16, K=1,
+                    grid=(1000, 1000), n_real=64, hd=None, seed=3)
+    if name == "c4a":
+        cells, vals = synth.sample_hard_data(hd_field_3d(200, 200, 100), 1000, seed=7)
+        return dict(name="c4a", ti=tube_ti_3d(), F=4, J=1, T=24, O=6, K=5,
+                    grid=(200, 200, 100), n_real=8, hd=(cells, vals), seed=4)
+    if name == "c4b":
+        cells, vals = synth.sample_hard_data(hd_field_3d(100, 100, 100), 1000, seed=8)
+        return dict(name="c4b", ti=tube_ti_3d(), F=4, J=1, T=24, O=6, K=5,
+                    grid=(100, 100, 100), n_real=8, hd=(cells, vals), seed=4)
+    if name == "c5":
+        return dict(name="c5", ti=ribbon_ti_250(), F=2, J=2, T=48, O=12, K=1,
+                    grid=(512, 512), n_real=256, hd=None, seed=5)
+    raise KeyError(name)
+
+
+def structured_events(ti: np.ndarray, T: int, O: int, n: int, rng: np.random.Generator,
+                      n_hd: int = 2, F: int | None = None, kinds=("L", "V", "H", "rand")):
+    """Data events with the shapes of Sec. 4.1 (Fig. 3a-c): an L-shaped,
+    vertical or horizontal overlap strip of width O cut from a random TI
+    window, or a random mask; plus ``n_hd`` hard data placed anywhere in the
+    template. Returns (de [n, T..], hd [n, T..]) uint8 with 255 = unknown."""
+    d = ti.ndim
+    F = int(ti.max()) + 1 if F is None else F
+    shape = (T,) * d
+    de = np.full((n,) + shape, 255, np.uint8)
+    hd = np.full((n,) + shape, 255, np.uint8)
+    for i in range(n):
+        org = [int(rng.integers(0, ti.shape[a] - T + 1)) for a in range(d)]
+        win = ti[tuple(slice(o, o + T) for o in org)]
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        m = np.zeros(shape, bool)
+        if kind == "rand":
+            m = rng.random(shape) < 0.3
+        else:
+            # the overlap lies at the low end of the axes already simulated
+            axes = {"L": range(d), "V": [d - 1], "H": [d - 2]}[kind]
+            for ax in axes:
+                sl = [slice(None)] * d
+                sl[ax] = slice(0, O)
+                m[tuple(sl)] = True
+        de[i][m] = win[m]
+        for _ in range(n_hd):
+            q = tuple(int(rng.integers(0, T)) for _ in range(d))
+            v = int(rng.integers(0, F))
+            hd[i][q] = v
+            de[i][q] = v
+    return de, hd

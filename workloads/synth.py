@@ -82,7 +82,8 @@ def channel_lens_ti(nx: int = 1000, ny: int = 1000, seed: int = 2,
     """3-facies TI: background 0, channels 1, elliptical lenses 2 (u8).
 
     Channels are added one at a time until facies 1 reaches its target, then
-    lenses (drawn over everything) until facies 2 reaches its target.
+    lenses (drawn over the background only, so channels cut through them)
+    until facies 2 reaches its target.
     """
     rng = _rng(seed, 0)
     ti = np.zeros((ny, nx), dtype=np.uint8)
@@ -110,7 +111,7 @@ def channel_lens_ti(nx: int = 1000, ny: int = 1000, seed: int = 2,
         dx, dy = xx - cx, yy - cy
         u = (dx * np.cos(th) + dy * np.sin(th)) / ax
         v = (-dx * np.sin(th) + dy * np.cos(th)) / ay
-        ti[u * u + v * v <= 1.0] = 2
+        ti[(u * u + v * v <= 1.0) & (ti == 0)] = 2
     p = np.array([(ti == f).mean() for f in range(3)])
     if np.any(np.abs(p - np.asarray(target)) > tol):
         raise RuntimeError(f"channel_lens_ti: proportions {p} off target")
