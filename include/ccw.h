@@ -174,6 +174,43 @@ int ccw_ccf_search(const ccw_ti* ti, int32_t B, const uint8_t* de_dev, const uin
                    int32_t* pick_dev, void* stream);
 
 /*
+ * ccw_ccf_search_noalloc -- the same search as ccw_ccf_search (same
+ * arguments, same results), for callers that cannot allocate device memory
+ * while they run: a serving process that has handed all of HBM to its own
+ * pool up front, or a latency-critical loop that must not pay for a driver
+ * allocation or the synchronization cudaMalloc may imply. ccw_ccf_search
+ * takes its scratch (per-tile ranking keys and per-event counters) from the
+ * stream-ordered allocator on every call; this variant uses instead one
+ * scratch array compiled into the library, CCW_NOALLOC_SCRATCH_BYTES bytes
+ * on every device that loads the library, kept until the process exits. It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - Size limit: the scratch needed is 256-byte-rounded 4 * min(B, 65535)
+ *    bytes of counters plus 8 * min(B, 65535) * tiles * k bytes of keys,
+ *    where tiles is the number of candidate tiles of the TI (64x16
+ *    candidates per tile in 2D, 32x8x4 in 3D). A call that needs more than
+ *    CCW_NOALLOC_SCRATCH_BYTES returns CCW_EINVAL without running; split the
+ *    batch.
+ *  - Set-up: the first call on a device looks up the device address of the
+ *    array (cudaGetSymbolAddress) with that device current; make that first
+ *    call before any stream capture that would contain it.
+ *  - Sharing: every call on a device uses the same array and leaves its
+ *    contents behind; each call clears the counters it needs on `stream`
+ *    before its search. Calls whose work overlaps on the GPU (different
+ *    streams, or host threads, without ordering between them) race on the
+ *    array and give wrong results: order them on one stream.
+ * The paper has no counterpart of this entry point; it only changes where
+ * the scratch memory comes from. Asynchronous. Errors: CCW_EINVAL (as
+ * ccw_ccf_search, or the batch needs more scratch than the array holds),
+ * CCW_ECUDA.
+ */
+#define CCW_NOALLOC_SCRATCH_BYTES (4 * 1024 * 1024)
+int ccw_ccf_search_noalloc(const ccw_ti* ti, int32_t B, const uint8_t* de_dev,
+                           const uint8_t* hd_dev, int32_t k, int32_t score_mode, uint64_t seed,
+                           const uint32_t* ctr_dev, int32_t* topk_idx_dev,
+                           int32_t* topk_score_dev, int32_t* topk_mis_dev, int32_t* pick_dev,
+                           void* stream);
+
+/*
  * ccw_ccf_map -- the full CCW score map and hard-data mismatch map of B data
  * events (Eq. CCW over every candidate), same inputs as ccw_ccf_search.
  *  score_dev, mis_dev  int32 [B][P_c] (mis_dev may be NULL).

@@ -436,6 +436,89 @@ int ccw_ccf_search(const ccw_ti* t, int32_t B, const uint8_t* de_dev, const uint
                        stream);
 }
 
+// Scratch of ccw_ccf_search_noalloc: one array per device, part of the
+// library image, so using it needs no allocation. Host code reaches it only
+// through the device address looked up below; the symbol itself is a host
+// stand-in that no kernel may be given.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CCW_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device; looked up once
+// per device, on the first call made with that device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(CCW_EUNSUPPORTED, "device index %d", dev);
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CCW_OK;
+}
+}  // namespace
+
+int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
+                           const uint8_t* hd_dev, int32_t k, int32_t score_mode, uint64_t seed,
+                           const uint32_t* ctr_dev, int32_t* topk_idx_dev,
+                           int32_t* topk_score_dev, int32_t* topk_mis_dev, int32_t* pick_dev,
+                           void* stream) {
+  if (!t) return fail(CCW_EINVAL, "ti is NULL");
+  if (B < 0) return fail(CCW_EINVAL, "B must be >= 0");
+  if (score_mode != 0 && score_mode != 1) return fail(CCW_EINVAL, "score_mode must be 0 or 1");
+  if (int rc = check_score_bound(t, score_mode)) return rc;
+  if (k < 1 || k > CCW_MAX_TOPK) return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
+  if (B == 0) return CCW_OK;
+  if (!de_dev || !ctr_dev || !topk_idx_dev || !topk_score_dev || !topk_mis_dev || !pick_dev)
+    return fail(CCW_EINVAL, "NULL input, output or counter");
+  SearchArgs a;
+  fill_ti_args(t, score_mode, a);
+  const int64_t chunk = std::min<int64_t>(B, 65535);
+  const int64_t cnt_bytes = (chunk * (int64_t)sizeof(unsigned int) + 255) & ~(int64_t)255;
+  const int64_t need = cnt_bytes + chunk * a.n_tiles * k * (int64_t)sizeof(unsigned long long);
+  if (need > CCW_NOALLOC_SCRATCH_BYTES)
+    return fail(CCW_EINVAL,
+                "ccw_ccf_search_noalloc: B=%d with k=%d needs %lld scratch bytes, more than "
+                "the %d-byte array; split the batch",
+                B, k, (long long)need, CCW_NOALLOC_SCRATCH_BYTES);
+  void* base = nullptr;
+  if (int rc = noalloc_scratch(&base)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  a.de = de_dev;
+  a.hd = hd_dev;
+  a.ctr = ctr_dev;
+  a.K = k;
+  a.seed = seed;
+  a.counters = (unsigned int*)base;
+  a.part = (unsigned long long*)((unsigned char*)base + cnt_bytes);
+  const int64_t tv = ipow(t->T, t->ndim);
+  const int smem = search_smem_bytes(t->ndim, a.nch, t->Tj, t->TjP);
+  for (int64_t i0 = 0; i0 < B; i0 += 65535) {
+    SearchArgs c = a;
+    c.n_items = (int)std::min<int64_t>(65535, B - i0);
+    c.de = de_dev + i0 * tv;
+    c.hd = hd_dev ? hd_dev + i0 * tv : nullptr;
+    c.ctr = ctr_dev + 2 * i0;
+    c.topk_idx = topk_idx_dev + i0 * k;
+    c.topk_score = topk_score_dev + i0 * k;
+    c.topk_mis = topk_mis_dev + i0 * k;
+    c.pick = pick_dev + i0;
+    cudaError_t e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned int) * c.n_items, st);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch clear");
+    e = launch_search(t->ndim, kModeSearch, c, smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "search kernel launch");
+    ++g_launches;
+  }
+  return CCW_OK;
+}
+
 int ccw_ccf_map(const ccw_ti* t, int32_t B, const uint8_t* de_dev, const uint8_t* hd_dev,
                 int32_t score_mode, int32_t* score_dev, int32_t* mis_dev, void* stream) {
   return search_common(t, kModeMap, B, de_dev, hd_dev, 1, score_mode, 0, nullptr, nullptr,
