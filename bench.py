@@ -33,8 +33,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # FP32 FMA roofline of GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-# (maximum SM clock); the search kernel's multiply-adds run on these lanes.
+# (maximum SM clock), for the CCF kernel on the FP32 lanes.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def tensor_peak_tflops():
+    """Measured dense BF16 GEMM throughput of this GPU pool (FP16 runs at the
+    same dense rate): the roofline of the tensor-core CCF kernel."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops)"
+    except Exception:
+        return 1900.0, "fallback (1.9 PFLOP/s dense bf16)"
 
 WORKLOAD_TEXT = {
     "c1": "2D binary ribbon TI 250x250; 1 realization 250x250; T40 OR10 J1; no hard data; K=1",
@@ -60,6 +71,9 @@ def parse_args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="0 FP32 FMA lanes, 1 FP16 tensor cores, 2 BF16 tensor cores "
+                         "(default: 1 for 2D workloads, 0 for 3D)")
     return ap.parse_args()
 
 
@@ -201,6 +215,7 @@ def run_ours(args, rank, world, local_rank):
         hv = torch.from_numpy(hd[1]).cuda()
     n_real = w["n_real"]
     grid = w["grid"]
+    precision = args.precision if args.precision is not None else (1 if len(grid) == 2 else 0)
     base = rank * n_real             # each rank simulates its own realizations
     out = torch.empty((n_real,) + tuple(grid)[::-1], dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -208,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step():
         ccw.simulate(g, grid, n_real=n_real, topk=w["K"], seed=w["seed"], hd_cells=hc,
-                     hd_vals=hv, real_base=base, out=out)
+                     hd_vals=hv, real_base=base, out=out, precision=precision)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -265,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
                 dc.copy_(hpc, non_blocking=True)
                 dv.copy_(hpv, non_blocking=True)
             ccw.simulate(g, grid, n_real=n_real, topk=w["K"], seed=w["seed"], hd_cells=dc,
-                         hd_vals=dv, real_base=base, out=out)
+                         hd_vals=dv, real_base=base, out=out, precision=precision)
             host_out.copy_(out, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
@@ -282,23 +297,31 @@ def run_ours(args, rank, world, local_rank):
     value = cells / (total_ms / 1e3)
     flops = 2.0 * macs
     achieved = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+    if precision == 0:
+        bound, peak, peak_src = "alu", FP32_PEAK_TFLOPS, \
+            "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        kname = "k_ccf_simt (masked CCF on the FP32 lanes, per-tile top-K)"
+    else:
+        bound = "tensor"
+        peak, peak_src = tensor_peak_tflops()
+        kname = "k_ccf_tc (masked CCF on tcgen05 tensor cores, per-CTA top-K)"
+    dtype = {0: "f32", 1: "f16", 2: "bf16"}[precision]
     line = {
         "metric": "simulated cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
         "cand_evals_per_s": cand_evals * world / (total_ms / 1e3),
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
-                   "realizations_per_gpu": n_real,
+                   "realizations_per_gpu": n_real, "precision": precision,
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
-        "roofline": {"bound": "alu", "kernel": "k_search (fused DWT + masked CCF + top-K + "
-                     "pick + IDWT paste)", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+        "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "launches": n_launch,
                      "kernel_ms_per_step": kern_ms / args.steps,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                     "work": "2 x (masked level-J cells x channels) flop per candidate"},
+                     "peak_source": peak_src,
+                     "work": "2 x (data-holding level-J cells x channels) flop per candidate"},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -72,7 +72,13 @@ typedef struct {
                           first word of Philox counter (r, 0, 1, 0)
                           (Algorithm 1, line 3) */
   int32_t score_mode;  /* 0: one-hot facies indicators; 1: literal codes */
-  int32_t precision;   /* 0: exact FP32 FMA path (only value in this build) */
+  int32_t precision;   /* CCF arithmetic: 0 FP32 FMA lanes; 1 FP16 and 2 BF16
+                          tensor cores (2D only), FP32 accumulation. Every
+                          mode is exact: 1 and 2 are refused (CCW_EINVAL)
+                          when an operand could exceed the format's exact
+                          integer range (2048 for FP16, 256 for BF16; the
+                          operands are at most 2^(d J) in the one-hot score,
+                          (F - 1) 2^(d J) in the literal one). */
   int32_t reserved[4]; /* must be 0 */
 } ccw_params;
 
@@ -159,7 +165,9 @@ int ccw_simulate(const ccw_ti* ti, const ccw_params* params, const int32_t* hd_c
  *  de_dev     uint8 [B][T^d]: data events (the template window, codes or
  *             255 where unknown; hard data must already be written in).
  *  hd_dev     uint8 [B][T^d]: hard data of each window (255 = none), or NULL.
- *  k          K in [1, CCW_MAX_TOPK]; score_mode 0 one-hot, 1 literal.
+ *  k          K in [1, CCW_MAX_TOPK].
+ *  score_mode bits 0-3: 0 one-hot, 1 literal score; bits 4-7: precision
+ *             (as ccw_params.precision).
  *  ctr_dev    uint32 [B][2]: (realization r, patch p) Philox counter words.
  *  topk_*_dev int32 [B][k]: ranked candidates with their score and mismatch
  *             count; slots past min(k, P_c), and all slots of an empty data
@@ -179,25 +187,27 @@ int ccw_ccf_search(const ccw_ti* ti, int32_t B, const uint8_t* de_dev, const uin
  * while they run: a serving process that has handed all of HBM to its own
  * pool up front, or a latency-critical loop that must not pay for a driver
  * allocation or the synchronization cudaMalloc may imply. ccw_ccf_search
- * takes its scratch (per-tile ranking keys and per-event counters) from the
+ * takes its scratch (per-event records, per-tile ranking keys) from the
  * stream-ordered allocator on every call; this variant uses instead one
  * scratch array compiled into the library, CCW_NOALLOC_SCRATCH_BYTES bytes
  * on every device that loads the library, kept until the process exits. It
  * calls no cudaMalloc, cudaFree or other allocating routine.
- *  - Size limit: the scratch needed is 256-byte-rounded 4 * min(B, 65535)
- *    bytes of counters plus 8 * min(B, 65535) * tiles * k bytes of keys,
- *    where tiles is the number of candidate tiles of the TI (64x16
- *    candidates per tile in 2D, 32x8x4 in 3D). A call that needs more than
- *    CCW_NOALLOC_SCRATCH_BYTES returns CCW_EINVAL without running; split the
- *    batch.
+ *  - Size limit: a call needs, per data event (of min(B, 65535)), one
+ *    event record (the event's level-J weights, its hard-data list and
+ *    bookkeeping: a few KB, set by the template) and 8 * tiles * k bytes of
+ *    ranking keys, where tiles is the number of
+ *    candidate tiles of the TI (64x16 candidates per tile in 2D, 32x8x4 in
+ *    3D). A call that needs more than CCW_NOALLOC_SCRATCH_BYTES returns
+ *    CCW_EINVAL without running; split the batch.
  *  - Set-up: the first call on a device looks up the device address of the
  *    array (cudaGetSymbolAddress) with that device current; make that first
  *    call before any stream capture that would contain it.
  *  - Sharing: every call on a device uses the same array and leaves its
- *    contents behind; each call clears the counters it needs on `stream`
- *    before its search. Calls whose work overlaps on the GPU (different
- *    streams, or host threads, without ordering between them) race on the
- *    array and give wrong results: order them on one stream.
+ *    contents behind; nothing in it needs to start at zero, since a call
+ *    writes every scratch slot before it reads it. Calls whose work
+ *    overlaps on the GPU (different streams, or host threads, without
+ *    ordering between them) race on the array and give wrong results:
+ *    order them on one stream.
  * The paper has no counterpart of this entry point; it only changes where
  * the scratch memory comes from. Asynchronous. Errors: CCW_EINVAL (as
  * ccw_ccf_search, or the batch needs more scratch than the array holds),
@@ -212,7 +222,8 @@ int ccw_ccf_search_noalloc(const ccw_ti* ti, int32_t B, const uint8_t* de_dev,
 
 /*
  * ccw_ccf_map -- the full CCW score map and hard-data mismatch map of B data
- * events (Eq. CCW over every candidate), same inputs as ccw_ccf_search.
+ * events (Eq. CCW over every candidate), same inputs as ccw_ccf_search
+ * (score_mode carries the precision in bits 4-7 here too).
  *  score_dev, mis_dev  int32 [B][P_c] (mis_dev may be NULL).
  * An empty data event yields an all-zero map. Asynchronous.
  */

@@ -202,7 +202,7 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
 
 
 def ccf_search(ti: TI, de: torch.Tensor, hd=None, k=1, score_mode=0, seed=0, ctr=None,
-               stream=None):
+               precision=0, stream=None):
     """``ccw_ccf_search`` on B data events de uint8 [B, T(, T), T]."""
     lib = load()
     B = de.shape[0]
@@ -213,19 +213,20 @@ def ccf_search(ti: TI, de: torch.Tensor, hd=None, k=1, score_mode=0, seed=0, ctr
     ti_sc = torch.empty((B, k), dtype=torch.int32, device=dev)
     ti_mm = torch.empty((B, k), dtype=torch.int32, device=dev)
     pick = torch.empty((B,), dtype=torch.int32, device=dev)
-    _check(lib.ccw_ccf_search(ti.handle, B, _ptr(de), _ptr(hd), k, score_mode,
+    _check(lib.ccw_ccf_search(ti.handle, B, _ptr(de), _ptr(hd), k, score_mode | (precision << 4),
                               seed & (2 ** 64 - 1), _ptr(ctr), _ptr(ti_idx), _ptr(ti_sc),
                               _ptr(ti_mm), _ptr(pick), _stream(stream)))
     return dict(topk_idx=ti_idx, topk_score=ti_sc, topk_mis=ti_mm, pick=pick)
 
 
-def ccf_map(ti: TI, de: torch.Tensor, hd=None, score_mode=0, stream=None):
+def ccf_map(ti: TI, de: torch.Tensor, hd=None, score_mode=0, precision=0, stream=None):
     """``ccw_ccf_map``: (scores int32 [B, P_c], mismatches int32 [B, P_c])."""
     lib = load()
     B = de.shape[0]
     sc = torch.empty((B, ti.n_cand), dtype=torch.int32, device=de.device)
     mm = torch.empty((B, ti.n_cand), dtype=torch.int32, device=de.device)
-    _check(lib.ccw_ccf_map(ti.handle, B, _ptr(de), _ptr(hd), score_mode, _ptr(sc), _ptr(mm),
+    _check(lib.ccw_ccf_map(ti.handle, B, _ptr(de), _ptr(hd), score_mode | (precision << 4),
+                           _ptr(sc), _ptr(mm),
                            _stream(stream)))
     return sc, mm
 

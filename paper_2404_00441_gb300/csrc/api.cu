@@ -1,4 +1,7 @@
 // api.cu -- host side of the C ABI declared in include/ccw.h.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -9,38 +12,41 @@
 #include "ccw_internal.cuh"
 
 namespace ccw {
-// search.cu
-int search_smem_bytes(int d, int nch, int Tj, int TjP);
-void search_tiles(int d, const int cd[3], int tiles[3]);
-cudaError_t launch_search(int d, int mode, const SearchArgs& a, int smem, cudaStream_t st);
-cudaError_t launch_idwt_paste(int d, const SearchArgs& a, int B, const int32_t* picks,
-                              const int32_t* origins, uint8_t* grid, const int gdim[3],
-                              cudaStream_t st);
+// events.cu
+cudaError_t launch_events(int mode, const WaveArgs& a, bool pdl, cudaStream_t st);
+// finish.cu
+cudaError_t launch_finish(int mode, const WaveArgs& a, bool pdl, cudaStream_t st);
+// ccf_simt.cu
+int simt_smem_bytes(int d, int nch, int rows, int chunks, int Tj, int TjP, int NB, int K,
+                    int nbuf);
+void simt_tile_shape(int d, int tile[3]);
+void simt_tma_box(int d, int Tj, int TjP, int box[3]);
+cudaError_t launch_ccf_simt(int mode, const WaveArgs& a, const CUtensorMap& tmap, int nbuf,
+                            int smem, bool pdl, cudaStream_t st);
+// tc.cu
+int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K);
+cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // prepare.cu
+cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
+                      int64_t nq, int nplanes, void* z8_f16, void* z8_bf16, cudaStream_t st);
 cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst, const int n[3],
                            int F, int* status, cudaStream_t st);
 cudaError_t launch_ti_pyramid(int d, const uint8_t* ti, const int n[3], const int nc[3], int s,
-                              int J, int F, float* planes, int16_t* pyr, cudaStream_t st);
+                              int J, int F, float* planes, int px, int16_t* pyr,
+                              cudaStream_t st);
 cudaError_t launch_hd_overlay(const int32_t* cells, const uint8_t* vals, int n, int d,
                               const int g[3], int F, uint8_t* overlay, int* status,
                               cudaStream_t st);
 cudaError_t launch_crop_out(const uint8_t* sg, int64_t gp_vol, const int gp[3], uint8_t* out,
                             const int g[3], int d, int n_real, int path_random, uint64_t seed,
                             int real_base, cudaStream_t st);
+cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3], const int cd[3],
+                              int Tj, int64_t P, int B, const int32_t* picks,
+                              const int32_t* origins, uint8_t* grid, const int gdim[3],
+                              int* status, cudaStream_t st);
 }  // namespace ccw
 
 using namespace ccw;
-
-struct ccw_ti {
-  int ndim, F, J, s, sd, T, O, Tj, TjP;
-  int n[3], nc[3], cd[3];
-  int64_t ncv, P;
-  int device;
-  uint8_t* d_ti;      // cropped fine TI
-  float* d_planes;    // F planes: counts of facies 0..F-2, then code sums
-  int16_t* d_pyr;     // [ncv][sd]
-  int* d_status;      // device status word
-};
 
 namespace {
 
@@ -60,46 +66,149 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 std::atomic<int64_t> g_launches{0};
 
-// profiling state
-struct Profiler {
-  std::mutex mu;
-  bool enabled = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
-  unsigned long long* d_work = nullptr;
-  int device = -1;
-} g_prof;
-
 int64_t ipow(int64_t b, int e) {
   int64_t r = 1;
   for (int i = 0; i < e; ++i) r *= b;
   return r;
 }
 
-// Fill the TI part of the kernel arguments.
-void fill_ti_args(const ccw_ti* t, int score_mode, SearchArgs& a) {
-  memset(&a, 0, sizeof(a));
-  a.nch = score_mode == 0 ? t->F - 1 : 1;
-  a.planes = t->d_planes + (score_mode == 0 ? 0 : (int64_t)(t->F - 1) * t->ncv);
-  a.ti = t->d_ti;
-  a.pyr = t->d_pyr;
-  a.F = t->F;
-  a.J = t->J;
-  a.s = t->s;
-  a.sd = t->sd;
-  a.T = t->T;
-  a.Tj = t->Tj;
-  a.TjP = t->TjP;
-  a.d = t->ndim;
-  a.score_mode = score_mode;
-  for (int i = 0; i < 3; ++i) {
-    a.n[i] = t->n[i];
-    a.nc[i] = t->nc[i];
-    a.cd[i] = t->cd[i];
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// profiling state
+struct Profiler {
+  std::mutex mu;
+  bool enabled = false;
+  int64_t launches = 0;
+  double total_ms = 0.0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // direct launches
+  unsigned long long* d_work = nullptr;
+} g_prof;
+
+unsigned long long* profiling_counters() {
+  // caller holds g_prof.mu
+  if (!g_prof.d_work) {
+    if (cudaMalloc(&g_prof.d_work, 2 * sizeof(unsigned long long)) != cudaSuccess)
+      return nullptr;
+    cudaMemset(g_prof.d_work, 0, 2 * sizeof(unsigned long long));
   }
-  a.ncv = t->ncv;
-  a.P = t->P;
-  search_tiles(t->ndim, t->cd, a.tiles);
-  a.n_tiles = a.tiles[0] * a.tiles[1] * a.tiles[2];
+  return g_prof.d_work;
+}
+
+// Event-record layout (see EvDev).
+void event_layout(int nch, int rows, int TjP, int hd_cap, EvDev& ev) {
+  int64_t off = 64;
+  ev.mask_off = (int)off;
+  off = align_up(off + 4LL * rows, 16);
+  ev.hd_off = (int)off;
+  off = align_up(off + 8LL * hd_cap, 16);
+  ev.w_off = (int)off;
+  off = align_up(off + 4LL * nch * rows * TjP, 256);
+  ev.stride = off;
+  ev.hd_cap = hd_cap;
+  ev.base = nullptr;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Simulation plan: workspace and the captured wave graph of one simulation
+// shape, reused while the shape does not change.
+// ---------------------------------------------------------------------------
+struct SimPlan {
+  int grid[3];
+  int n_real, K, score_mode, precision;
+  int g[3], np[3], gp[3];
+  int64_t gp_vol, g_vol, n_patches;
+  int n_waves, max_items;
+  std::vector<int64_t> wave_off;
+  void* sg = nullptr;
+  void* overlay = nullptr;
+  void* items = nullptr;
+  void* ev = nullptr;
+  void* part = nullptr;
+  void* bmat = nullptr;
+  CallDev* call = nullptr;
+  EvDev evl;
+  void* cp = nullptr;   // CcfPlan (defined with the kernels' host helpers)
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [profiling]
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  ~SimPlan() {
+    for (auto& e : exec)
+      if (e) cudaGraphExecDestroy(e);
+    for (auto& pr : prof_events) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    if (cap) cudaStreamDestroy(cap);
+    cudaFree(sg);
+    cudaFree(overlay);
+    cudaFree(items);
+    cudaFree(ev);
+    cudaFree(part);
+    cudaFree(bmat);
+    cudaFree(call);
+    release_cp();
+  }
+  void release_cp();
+};
+
+struct ccw_ti {
+  int ndim, F, J, s, sd, T, O, Tj, TjP, chunks, rows;
+  int n[3], nc[3], cd[3];
+  int64_t ncv, P;
+  int px;
+  int64_t plane_vol;
+  int device;
+  int tile[3], tiles[3], n_tiles;
+  uint8_t* d_ti = nullptr;      // cropped fine TI
+  float* d_planes = nullptr;    // F planes [nc2][nc1][px]: facies 0..F-2 counts, code sums
+  int16_t* d_pyr = nullptr;     // [ncv][sd]
+  int* d_status = nullptr;      // device status word
+  CUtensorMap tmap;             // TMA view of the planes, box = one CCF tile plus halo
+  // tensor-core view (2D): 8-shift copies of the planes, FP16 and BF16
+  int px8 = 0, ks = 0, mtiles = 0;
+  int64_t z8_nq = 0;
+  void* z8_f16 = nullptr;
+  void* z8_bf16 = nullptr;
+  std::mutex mu;
+  SimPlan* plan = nullptr;
+};
+
+namespace {
+
+// Fill the TI part of the kernel arguments.
+void fill_ti(const ccw_ti* t, int score_mode, WaveArgs& a) {
+  memset(&a, 0, sizeof(a));
+  TiDev& d = a.ti;
+  d.planes = t->d_planes;
+  d.px = t->px;
+  d.plane_vol = t->plane_vol;
+  d.plane0 = score_mode == 0 ? 0 : t->F - 1;
+  d.nch = score_mode == 0 ? t->F - 1 : 1;
+  d.ti = t->d_ti;
+  d.pyr = t->d_pyr;
+  d.F = t->F;
+  d.J = t->J;
+  d.s = t->s;
+  d.sd = t->sd;
+  d.T = t->T;
+  d.Tj = t->Tj;
+  d.TjP = t->TjP;
+  d.chunks = t->chunks;
+  d.rows = t->rows;
+  d.d = t->ndim;
+  d.score_mode = score_mode;
+  for (int i = 0; i < 3; ++i) {
+    d.n[i] = t->n[i];
+    d.nc[i] = t->nc[i];
+    d.cd[i] = t->cd[i];
+    d.tile[i] = t->tile[i];
+    d.tiles[i] = t->tiles[i];
+  }
+  d.ncv = t->ncv;
+  d.P = t->P;
+  d.n_tiles = t->n_tiles;
   a.status = t->d_status;
 }
 
@@ -116,56 +225,67 @@ int check_score_bound(const ccw_ti* t, int score_mode) {
   return CCW_OK;
 }
 
-// Launch the search kernel in chunks of at most 65535 items (grid.y limit),
-// with profiling events around each launch when enabled.
-int run_search(const ccw_ti* t, int mode, SearchArgs a, int n_items, int item_stride_sim,
-               cudaStream_t st) {
-  const int smem = search_smem_bytes(t->ndim, a.nch, t->Tj, t->TjP);
-  std::unique_lock<std::mutex> lk(g_prof.mu);
-  const bool prof = g_prof.enabled;
-  if (prof && !g_prof.d_work) {
-    if (cudaMalloc(&g_prof.d_work, 2 * sizeof(unsigned long long)) != cudaSuccess)
-      return fail(CCW_ENOMEM, "profiling counters");
-    cudaMemset(g_prof.d_work, 0, 2 * sizeof(unsigned long long));
+// Items per CTA and TI tile buffers of the CCF kernel.
+void choose_simt(const ccw_ti* t, int nch, int K, int n_items, int& nb, int& nbuf, int& smem) {
+  nb = (t->ndim == 3) ? 2 : 4;
+  while (nb > 1 && n_items < nb / 2 + 1) nb /= 2;
+  nbuf = 2;
+  smem = simt_smem_bytes(t->ndim, nch, t->rows, t->chunks, t->Tj, t->TjP, nb, K, nbuf);
+  if (smem > 110 * 1024) {
+    nbuf = 1;
+    smem = simt_smem_bytes(t->ndim, nch, t->rows, t->chunks, t->Tj, t->TjP, nb, K, nbuf);
   }
-  a.work = prof ? g_prof.d_work : nullptr;
-  lk.unlock();
-  const int64_t tv = ipow(t->T, t->ndim);
-  for (int i0 = 0; i0 < n_items; i0 += 65535) {
-    SearchArgs c = a;
-    c.n_items = std::min(65535, n_items - i0);
-    if (mode == kModeSim) {
-      c.items = a.items + i0;
-    } else {
-      c.de = a.de + (int64_t)i0 * tv;
-      c.hd = a.hd ? a.hd + (int64_t)i0 * tv : nullptr;
-      if (a.ctr) c.ctr = a.ctr + 2 * (int64_t)i0;
-      if (a.topk_idx) {
-        c.topk_idx = a.topk_idx + (int64_t)i0 * a.K;
-        c.topk_score = a.topk_score + (int64_t)i0 * a.K;
-        c.topk_mis = a.topk_mis + (int64_t)i0 * a.K;
-      }
-      if (a.pick) c.pick = a.pick + i0;
-      if (a.map_score) c.map_score = a.map_score + (int64_t)i0 * t->P;
-      if (a.map_mis) c.map_mis = a.map_mis + (int64_t)i0 * t->P;
-    }
-    (void)item_stride_sim;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (prof) {
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      cudaEventRecord(e0, st);
-    }
-    cudaError_t e = launch_search(t->ndim, mode, c, smem, st);
-    if (e != cudaSuccess) return cuda_fail(e, "search kernel launch");
-    ++g_launches;
-    if (prof) {
-      cudaEventRecord(e1, st);
-      std::lock_guard<std::mutex> g(g_prof.mu);
-      g_prof.events.emplace_back(e0, e1);
-    }
+  while (smem > 220 * 1024 && nb > 1) {
+    nb /= 2;
+    smem = simt_smem_bytes(t->ndim, nch, t->rows, t->chunks, t->Tj, t->TjP, nb, K, nbuf);
   }
+}
+
+int hd_capacity(const ccw_ti* t) { return (int)std::min<int64_t>(kMaxHd, ipow(t->T, t->ndim)); }
+
+// Precision check: the tensor-core path is exact while every operand fits
+// the 16-bit format exactly (FP16: |v| <= 2048, BF16: |v| <= 256).
+int check_precision(const ccw_ti* t, int precision, int score_mode) {
+  if (precision == 0) return CCW_OK;
+  if (precision != 1 && precision != 2) return fail(CCW_EINVAL, "precision must be 0, 1 or 2");
+  if (t->ndim != 2)
+    return fail(CCW_EUNSUPPORTED, "the tensor-core CCF is built for 2D training images only");
+  const int64_t vmax = (int64_t)(score_mode == 0 ? 1 : t->F - 1) * t->sd;
+  const int64_t lim = precision == 1 ? 2048 : 256;
+  if (vmax > lim)
+    return fail(CCW_EINVAL,
+                "%s operands up to %lld are beyond its exact integer range (%lld); lower the "
+                "level or use precision 0",
+                precision == 1 ? "FP16" : "BF16", (long long)vmax, (long long)lim);
   return CCW_OK;
+}
+
+int tc_a_nq(const ccw_ti* t, int mt) {
+  return 16 * (mt - 1) + (t->rows - 1) * t->px8 / 8 + 2 * (t->ks / 16 - 1) + 17;
+}
+
+// Tensor-core tiling: items per N-tile, M-tiles per CTA, shared memory.
+void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& smem) {
+  a.nt = n_items <= 16 ? 16 : n_items <= 32 ? 32 : n_items <= 64 ? 64 : 128;
+  a.ks = t->ks;
+  a.ksteps = nch * t->rows * (t->ks / 16);
+  a.px8 = t->px8;
+  a.mtiles = t->mtiles;
+  const int n_ntiles = (n_items + a.nt - 1) / a.nt;
+  // M-tiles per CTA: about one CTA per SM, at most 4 (and mt * nt TMEM
+  // columns <= 512)
+  int mt = (int)std::max<int64_t>(1, std::min<int64_t>(4, ((int64_t)t->mtiles * n_ntiles + 151) / 152));
+  while (mt * a.nt > 512) --mt;
+  for (;;) {
+    smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K);
+    if (smem <= 220 * 1024 || (mt == 1 && a.nt == 16)) break;
+    if (mt > 1) --mt;
+    else a.nt /= 2;
+  }
+  a.mt = mt;
+  a.a_nq = tc_a_nq(t, mt);
+  a.n_mgroups = (t->mtiles + mt - 1) / mt;
+  a.z8_nq = t->z8_nq;
 }
 
 struct DevBuf {
@@ -179,6 +299,220 @@ struct DevBuf {
     return cudaMallocAsync(&p, bytes ? bytes : 16, s);
   }
 };
+
+// How phase B runs for a batch shape: the FP32 SIMT kernel (precision 0) or
+// the tensor-core kernel (precision 1: FP16, 2: BF16), its tiling and the
+// scratch it needs per chunk of at most 65535 items.
+struct CcfPlan {
+  int precision = 0;
+  int nb = 1, nbuf = 1, smem = 0;   // SIMT
+  WaveArgs tc;                       // tensor-core tiling fields
+  int n_parts = 0;                   // partial key lists per item
+  int64_t ev_bytes = 0, part_bytes = 0, bmat_bytes = 0;
+};
+
+}  // namespace
+
+void SimPlan::release_cp() { delete static_cast<CcfPlan*>(cp); }
+
+namespace {
+
+void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
+              CcfPlan& cp) {
+  cp.precision = precision;
+  const int64_t chunk = std::min(n_items, 65535);
+  if (precision == 0) {
+    choose_simt(t, nch, K, (int)chunk, cp.nb, cp.nbuf, cp.smem);
+    cp.n_parts = t->n_tiles;
+    cp.bmat_bytes = 0;
+  } else {
+    memset(&cp.tc, 0, sizeof(cp.tc));
+    choose_tc(t, nch, K, (int)chunk, cp.tc, cp.smem);
+    cp.n_parts = cp.tc.n_mgroups;
+    cp.bmat_bytes = ((chunk + cp.tc.nt - 1) / cp.tc.nt) * (int64_t)cp.tc.ksteps * 32 * cp.tc.nt;
+  }
+  cp.ev_bytes = chunk * ev.stride;
+  cp.part_bytes = chunk * (int64_t)cp.n_parts * K * 8;
+}
+
+// Copy the phase-B configuration into the kernel arguments.
+void apply_ccf(const ccw_ti* t, const CcfPlan& cp, void* bmat, WaveArgs& c) {
+  c.precision = cp.precision;
+  c.nb = cp.nb;
+  c.n_parts = cp.n_parts;
+  if (cp.precision) {
+    c.z8 = cp.precision == 2 ? t->z8_bf16 : t->z8_f16;
+    c.z8_nq = cp.tc.z8_nq;
+    c.px8 = cp.tc.px8;
+    c.ks = cp.tc.ks;
+    c.ksteps = cp.tc.ksteps;
+    c.mtiles = cp.tc.mtiles;
+    c.mt = cp.tc.mt;
+    c.n_mgroups = cp.tc.n_mgroups;
+    c.nt = cp.tc.nt;
+    c.a_nq = cp.tc.a_nq;
+    c.bmat = bmat;
+  }
+}
+
+cudaError_t launch_ccf(const ccw_ti* t, int mode, const CcfPlan& cp, const WaveArgs& c, bool pdl,
+                       cudaStream_t st) {
+  if (cp.precision) return launch_ccf_tc(mode, c, cp.smem, pdl, st);
+  return launch_ccf_simt(mode, c, t->tmap, cp.nbuf, cp.smem, pdl, st);
+}
+
+// Phases A, B (and C when searching) on explicit data events, in chunks of
+// at most 65535 items. Scratch comes from the caller (sizes from plan_ccf).
+int run_explicit(const ccw_ti* t, int mode, WaveArgs a, int B, const CcfPlan& cp,
+                 unsigned char* ev_base, unsigned long long* part, void* bmat, cudaStream_t st) {
+  const int64_t tv = ipow(t->T, t->ndim);
+  unsigned long long* work = nullptr;
+  bool prof;
+  {
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    prof = g_prof.enabled;
+    if (prof) work = profiling_counters();
+  }
+  for (int i0 = 0; i0 < B; i0 += 65535) {
+    WaveArgs c = a;
+    c.n_items = std::min(65535, B - i0);
+    apply_ccf(t, cp, bmat, c);
+    c.ev.base = ev_base;
+    c.part = part;
+    c.work = work;
+    c.de = a.de + (int64_t)i0 * tv;
+    c.hd = a.hd ? a.hd + (int64_t)i0 * tv : nullptr;
+    if (a.ctr) c.ctr = a.ctr + 2 * (int64_t)i0;
+    if (a.topk_idx) {
+      c.topk_idx = a.topk_idx + (int64_t)i0 * a.K;
+      c.topk_score = a.topk_score + (int64_t)i0 * a.K;
+      c.topk_mis = a.topk_mis + (int64_t)i0 * a.K;
+    }
+    if (a.pick) c.pick = a.pick + i0;
+    if (a.map_score) c.map_score = a.map_score + (int64_t)i0 * t->P;
+    if (a.map_mis) c.map_mis = a.map_mis + (int64_t)i0 * t->P;
+    cudaError_t e = launch_events(mode, c, false, st);
+    if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
+    ++g_launches;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, st);
+    }
+    e = launch_ccf(t, mode, cp, c, !prof, st);
+    if (e != cudaSuccess) return cuda_fail(e, "CCF kernel launch");
+    ++g_launches;
+    if (prof) {
+      cudaEventRecord(e1, st);
+      std::lock_guard<std::mutex> g(g_prof.mu);
+      g_prof.pending.emplace_back(e0, e1);
+    }
+    if (mode == kModeSearch) {
+      e = launch_finish(mode, c, !prof, st);
+      if (e != cudaSuccess) return cuda_fail(e, "finish kernel launch");
+      ++g_launches;
+    }
+  }
+  return CCW_OK;
+}
+
+// score_mode argument of the search entry points: bits 0-3 the score mode,
+// bits 4-7 the precision.
+int split_mode(int32_t mode, int& score_mode, int& precision) {
+  score_mode = mode & 0xF;
+  precision = (mode >> 4) & 0xF;
+  if ((mode & ~0xFF) != 0 || (score_mode != 0 && score_mode != 1))
+    return fail(CCW_EINVAL, "score_mode must be 0 or 1 (bits 0-3), precision in bits 4-7");
+  return CCW_OK;
+}
+
+int search_common(const ccw_ti* t, int mode, int32_t B, const uint8_t* de, const uint8_t* hd,
+                  int32_t k, int32_t score_arg, uint64_t seed, const uint32_t* ctr,
+                  int32_t* ti_idx, int32_t* ti_sc, int32_t* ti_mm, int32_t* pick,
+                  int32_t* map_sc, int32_t* map_mm, void* stream) {
+  if (!t) return fail(CCW_EINVAL, "ti is NULL");
+  if (B < 0) return fail(CCW_EINVAL, "B must be >= 0");
+  int score_mode, precision;
+  if (int rc = split_mode(score_arg, score_mode, precision)) return rc;
+  if (int rc = check_score_bound(t, score_mode)) return rc;
+  if (int rc = check_precision(t, precision, score_mode)) return rc;
+  if (mode == kModeSearch && (k < 1 || k > CCW_MAX_TOPK))
+    return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
+  if (B == 0) return CCW_OK;
+  if (!de) return fail(CCW_EINVAL, "de_dev is NULL");
+  if (mode == kModeSearch) {
+    if (!ctr || !ti_idx || !ti_sc || !ti_mm || !pick)
+      return fail(CCW_EINVAL, "NULL output or counter");
+  } else if (!map_sc) {
+    return fail(CCW_EINVAL, "score_dev is NULL");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  WaveArgs a;
+  fill_ti(t, score_mode, a);
+  event_layout(a.ti.nch, t->rows, t->TjP, hd_capacity(t), a.ev);
+  a.de = de;
+  a.hd = hd;
+  a.ctr = ctr;
+  a.K = mode == kModeSearch ? k : 1;
+  a.seed = seed;
+  a.topk_idx = ti_idx;
+  a.topk_score = ti_sc;
+  a.topk_mis = ti_mm;
+  a.pick = pick;
+  a.map_score = map_sc;
+  a.map_mis = map_mm;
+  CcfPlan cp;
+  plan_ccf(t, precision, a.ti.nch, a.K, B, a.ev, cp);
+  DevBuf evb, part, bm;
+  if (evb.alloc((size_t)cp.ev_bytes, st) != cudaSuccess ||
+      (mode == kModeSearch && part.alloc((size_t)cp.part_bytes, st) != cudaSuccess) ||
+      (cp.bmat_bytes && bm.alloc((size_t)cp.bmat_bytes, st) != cudaSuccess))
+    return fail(CCW_ENOMEM, "search scratch");
+  return run_explicit(t, mode, a, B, cp, (unsigned char*)evb.p, (unsigned long long*)part.p,
+                      bm.p, st);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Scratch of ccw_ccf_search_noalloc: one array per device, part of the
+// library image, so using it needs no allocation. Host code reaches it only
+// through the device address looked up below; the symbol itself is a host
+// stand-in that no kernel may be given.
+__device__ __align__(256) unsigned char g_noalloc_scratch[CCW_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device; looked up once
+// per device, on the first call made with that device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(CCW_EUNSUPPORTED, "device index %d", dev);
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CCW_OK;
+}
 
 }  // namespace
 
@@ -196,18 +530,20 @@ int ccw_profile_enable(int32_t enable) {
 
 int ccw_profile_read(int64_t* launches, double* total_ms, double* cand_evals, double* macs) {
   std::lock_guard<std::mutex> g(g_prof.mu);
-  double ms = 0.0;
-  for (auto& pr : g_prof.events) {
+  for (auto& pr : g_prof.pending) {
     cudaEventSynchronize(pr.second);
     float t = 0.f;
     cudaEventElapsedTime(&t, pr.first, pr.second);
-    ms += t;
+    g_prof.total_ms += t;
+    ++g_prof.launches;
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
-  if (launches) *launches = (int64_t)g_prof.events.size();
-  if (total_ms) *total_ms = ms;
-  g_prof.events.clear();
+  g_prof.pending.clear();
+  if (launches) *launches = g_prof.launches;
+  if (total_ms) *total_ms = g_prof.total_ms;
+  g_prof.launches = 0;
+  g_prof.total_ms = 0.0;
   unsigned long long w[2] = {0, 0};
   if (g_prof.d_work) {
     cudaMemcpy(w, g_prof.d_work, sizeof(w), cudaMemcpyDeviceToHost);
@@ -233,82 +569,148 @@ int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3], i
     return fail(CCW_EINVAL, "template and overlap must be non-negative multiples of 2^level");
   if (templ < 2 * overlap) return fail(CCW_EINVAL, "template must be at least 2 x overlap");
   if (dims[2] != 1 && ndim == 2) return fail(CCW_EINVAL, "dims[2] must be 1 in 2D");
-  ccw_ti t;
-  memset(&t, 0, sizeof(t));
-  t.ndim = ndim;
-  t.F = n_facies;
-  t.J = level;
-  t.s = s;
-  t.sd = ndim == 2 ? s * s : s * s * s;
-  t.T = templ;
-  t.O = overlap;
-  t.Tj = templ / s;
-  t.TjP = 4 * ((t.Tj + 3) / 4);
+  ccw_ti* t = new ccw_ti();
+  t->ndim = ndim;
+  t->F = n_facies;
+  t->J = level;
+  t->s = s;
+  t->sd = ndim == 2 ? s * s : s * s * s;
+  t->T = templ;
+  t->O = overlap;
+  t->Tj = templ / s;
+  t->TjP = 4 * ((t->Tj + 3) / 4);
+  t->chunks = t->TjP / 4;
+  t->rows = ndim == 3 ? t->Tj * t->Tj : t->Tj;
+  auto reject = [&](int code, const char* msg) {
+    delete t;
+    return fail(code, "%s", msg);
+  };
   for (int a = 0; a < 3; ++a) {
     const int sa = a < ndim ? s : 1;
-    if (dims[a] <= 0) return fail(CCW_EINVAL, "dims must be positive");
-    t.nc[a] = dims[a] / sa;
-    t.n[a] = t.nc[a] * sa;
-    t.cd[a] = a < ndim ? t.nc[a] - t.Tj + 1 : 1;
-    if (t.cd[a] <= 0) return fail(CCW_EINVAL, "template larger than the TI along axis %d", a);
+    if (dims[a] <= 0) return reject(CCW_EINVAL, "dims must be positive");
+    t->nc[a] = dims[a] / sa;
+    t->n[a] = t->nc[a] * sa;
+    t->cd[a] = a < ndim ? t->nc[a] - t->Tj + 1 : 1;
+    if (t->cd[a] <= 0) return reject(CCW_EINVAL, "template larger than the TI");
   }
-  t.ncv = (int64_t)t.nc[0] * t.nc[1] * t.nc[2];
-  t.P = (int64_t)t.cd[0] * t.cd[1] * t.cd[2];
-  if (t.P >= (1 << 24)) return fail(CCW_EINVAL, "more than 2^24 - 1 candidates");
-  if (t.Tj > 255 * 4) return fail(CCW_EINVAL, "template too large");
+  t->ncv = (int64_t)t->nc[0] * t->nc[1] * t->nc[2];
+  t->P = (int64_t)t->cd[0] * t->cd[1] * t->cd[2];
+  if (t->P >= (1 << 24)) return reject(CCW_EINVAL, "more than 2^24 - 1 candidates");
+  if (t->chunks > kMaxChunks) return reject(CCW_EINVAL, "template too large (T/2^J > 128)");
+  if (check_score_bound(t, 0)) {
+    delete t;
+    return CCW_EINVAL;
+  }
+  t->px = (int)align_up(t->nc[0], 4);
+  t->plane_vol = (int64_t)t->px * t->nc[1] * t->nc[2];
+  simt_tile_shape(ndim, t->tile);
+  for (int a = 0; a < 3; ++a) t->tiles[a] = (t->cd[a] + t->tile[a] - 1) / t->tile[a];
+  t->n_tiles = t->tiles[0] * t->tiles[1] * t->tiles[2];
   {
-    int rc = check_score_bound(&t, 0);
-    if (rc) return rc;
+    int nb, nbuf, smem;
+    choose_simt(t, t->F - 1, CCW_MAX_TOPK, 1, nb, nbuf, smem);
+    if (smem > 227 * 1024) return reject(CCW_EUNSUPPORTED, "template too large for the CCF tile");
   }
-  const int smem = search_smem_bytes(ndim, t.F - 1, t.Tj, t.TjP);
-  if (smem > 227 * 1024)
-    return fail(CCW_EUNSUPPORTED, "template too large for the shared-memory tile (%d B)", smem);
-  cudaGetDevice(&t.device);
+  cudaGetDevice(&t->device);
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t nv = (int64_t)t.n[0] * t.n[1] * t.n[2];
+  const int64_t nv = (int64_t)t->n[0] * t->n[1] * t->n[2];
   cudaError_t e;
-  if ((e = cudaMalloc(&t.d_ti, nv)) != cudaSuccess ||
-      (e = cudaMalloc(&t.d_planes, sizeof(float) * t.ncv * t.F)) != cudaSuccess ||
-      (e = cudaMalloc(&t.d_pyr, sizeof(int16_t) * t.ncv * t.sd)) != cudaSuccess ||
-      (e = cudaMalloc(&t.d_status, sizeof(int))) != cudaSuccess) {
-    cudaFree(t.d_ti);
-    cudaFree(t.d_planes);
-    cudaFree(t.d_pyr);
-    cudaFree(t.d_status);
+  auto release = [&]() {
+    cudaFree(t->d_ti);
+    cudaFree(t->d_planes);
+    cudaFree(t->d_pyr);
+    cudaFree(t->d_status);
+    delete t;
+  };
+  if ((e = cudaMalloc(&t->d_ti, nv)) != cudaSuccess ||
+      (e = cudaMalloc(&t->d_planes, sizeof(float) * t->plane_vol * t->F)) != cudaSuccess ||
+      (e = cudaMalloc(&t->d_pyr, sizeof(int16_t) * t->ncv * t->sd)) != cudaSuccess ||
+      (e = cudaMalloc(&t->d_status, sizeof(int))) != cudaSuccess) {
+    release();
     return fail(CCW_ENOMEM, "TI buffers: %s", cudaGetErrorString(e));
   }
-  auto cleanup = [&]() {
-    cudaFree(t.d_ti);
-    cudaFree(t.d_planes);
-    cudaFree(t.d_pyr);
-    cudaFree(t.d_status);
-  };
-  cudaMemsetAsync(t.d_status, 0, sizeof(int), st);
+  if ((e = cudaMemsetAsync(t->d_status, 0, sizeof(int), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(t->d_planes, 0, sizeof(float) * t->plane_vol * t->F, st)) !=
+          cudaSuccess) {
+    release();
+    return cuda_fail(e, "prepare clear");
+  }
   const int sdims[3] = {dims[0], dims[1], dims[2]};
-  if ((e = launch_crop_ti(ti_dev, sdims, t.d_ti, t.n, t.F, t.d_status, st)) != cudaSuccess) {
-    cleanup();
+  if ((e = launch_crop_ti(ti_dev, sdims, t->d_ti, t->n, t->F, t->d_status, st)) != cudaSuccess) {
+    release();
     return cuda_fail(e, "crop kernel");
   }
   ++g_launches;
-  if ((e = launch_ti_pyramid(ndim, t.d_ti, t.n, t.nc, s, level, t.F, t.d_planes, t.d_pyr, st)) !=
-      cudaSuccess) {
-    cleanup();
+  if ((e = launch_ti_pyramid(ndim, t->d_ti, t->n, t->nc, s, level, t->F, t->d_planes, t->px,
+                             t->d_pyr, st)) != cudaSuccess) {
+    release();
     return cuda_fail(e, "pyramid kernel");
   }
   ++g_launches;
+  // TMA view of the planes: (x: px, y: nc1, z: nc2, plane: F), one tile box
+  auto encode = tensor_map_encoder();
+  if (!encode) {
+    release();
+    return fail(CCW_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  }
+  int box[3];
+  simt_tma_box(ndim, t->Tj, t->TjP, box);
+  if (box[0] > 256 || box[1] > 256 || box[2] > 256) {
+    release();
+    return fail(CCW_EUNSUPPORTED, "CCF tile box beyond the TMA limit");
+  }
+  cuuint64_t gdim[4] = {(cuuint64_t)t->px, (cuuint64_t)t->nc[1], (cuuint64_t)t->nc[2],
+                        (cuuint64_t)t->F};
+  cuuint64_t gstride[3] = {(cuuint64_t)t->px * 4, (cuuint64_t)t->px * t->nc[1] * 4,
+                           (cuuint64_t)t->plane_vol * 4};
+  cuuint32_t bdim[4] = {(cuuint32_t)box[0], (cuuint32_t)box[1], (cuuint32_t)box[2], 1};
+  cuuint32_t estride[4] = {1, 1, 1, 1};
+  CUresult cr = encode(&t->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, t->d_planes, gdim, gstride,
+                       bdim, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    release();
+    return fail(CCW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  }
+  if (ndim == 2) {
+    // 8-shift copies of the planes for the tensor-core CCF
+    t->px8 = (int)align_up(t->nc[0], 8);
+    t->ks = 16 * ((t->Tj + 15) / 16);
+    t->mtiles = (int)((int64_t)t->px8 * t->cd[1] + 127) / 128;
+    t->z8_nq = 16LL * t->mtiles + 128 + (int64_t)(t->rows - 1) * t->px8 / 8 + 2 * (t->ks / 16) + 32;
+    const size_t zb = (size_t)t->F * t->z8_nq * 128;
+    if ((e = cudaMalloc(&t->z8_f16, zb)) != cudaSuccess ||
+        (e = cudaMalloc(&t->z8_bf16, zb)) != cudaSuccess) {
+      cudaFree(t->z8_f16);
+      cudaFree(t->z8_bf16);
+      release();
+      return fail(CCW_ENOMEM, "tensor-core TI buffers: %s", cudaGetErrorString(e));
+    }
+    if ((e = launch_z8(t->d_planes, t->px, t->plane_vol, t->nc[0], t->nc[1], t->px8, t->z8_nq,
+                       t->F, t->z8_f16, t->z8_bf16, st)) != cudaSuccess) {
+      cudaFree(t->z8_f16);
+      cudaFree(t->z8_bf16);
+      release();
+      return cuda_fail(e, "8-shift kernel");
+    }
+    g_launches += 2;
+  }
   int status = 0;
-  if ((e = cudaMemcpyAsync(&status, t.d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+  if ((e = cudaMemcpyAsync(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
           cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-    cleanup();
+    cudaFree(t->z8_f16);
+    cudaFree(t->z8_bf16);
+    release();
     return cuda_fail(e, "prepare");
   }
   if (status) {
-    cleanup();
+    cudaFree(t->z8_f16);
+    cudaFree(t->z8_bf16);
+    release();
     return fail(CCW_EINVAL, "training image holds codes >= n_facies");
   }
-  ccw_ti* h = new ccw_ti(t);
-  *out = h;
+  *out = t;
   return CCW_OK;
 }
 
@@ -332,6 +734,9 @@ int ccw_ti_describe(const ccw_ti* t, ccw_ti_desc* out) {
 void ccw_ti_free(ccw_ti* t) {
   if (!t) return;
   cudaDeviceSynchronize();
+  delete t->plan;
+  cudaFree(t->z8_f16);
+  cudaFree(t->z8_bf16);
   cudaFree(t->d_ti);
   cudaFree(t->d_planes);
   cudaFree(t->d_pyr);
@@ -342,29 +747,31 @@ void ccw_ti_free(ccw_ti* t) {
 int ccw_ti_export(const ccw_ti* t, int32_t what, void* dst, void* stream) {
   if (!t || !dst) return fail(CCW_EINVAL, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
-  const void* src;
-  size_t bytes;
+  cudaError_t e = cudaSuccess;
   switch (what) {
     case 0:
-      src = t->d_planes;
-      bytes = sizeof(float) * t->ncv * (t->F - 1);
+    case 1: {
+      // drop the row padding: planes are [nc2][nc1][px]
+      const int p0 = what == 0 ? 0 : t->F - 1;
+      const int np = what == 0 ? t->F - 1 : 1;
+      for (int p = 0; p < np && e == cudaSuccess; ++p)
+        e = cudaMemcpy2DAsync((float*)dst + (int64_t)p * t->ncv, sizeof(float) * t->nc[0],
+                              t->d_planes + (int64_t)(p0 + p) * t->plane_vol,
+                              sizeof(float) * t->px, sizeof(float) * t->nc[0],
+                              (size_t)t->nc[1] * t->nc[2], cudaMemcpyDeviceToDevice, st);
       break;
-    case 1:
-      src = t->d_planes + (int64_t)(t->F - 1) * t->ncv;
-      bytes = sizeof(float) * t->ncv;
-      break;
+    }
     case 2:
-      src = t->d_pyr;
-      bytes = sizeof(int16_t) * t->ncv * t->sd;
+      e = cudaMemcpyAsync(dst, t->d_pyr, sizeof(int16_t) * t->ncv * t->sd,
+                          cudaMemcpyDeviceToDevice, st);
       break;
     case 3:
-      src = t->d_ti;
-      bytes = (size_t)t->n[0] * t->n[1] * t->n[2];
+      e = cudaMemcpyAsync(dst, t->d_ti, (size_t)t->n[0] * t->n[1] * t->n[2],
+                          cudaMemcpyDeviceToDevice, st);
       break;
     default:
       return fail(CCW_EINVAL, "unknown export %d", what);
   }
-  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "export copy");
   return CCW_OK;
 }
@@ -382,51 +789,6 @@ int ccw_ti_status(const ccw_ti* t, void* stream, int32_t* status_out) {
   return CCW_OK;
 }
 
-static int search_common(const ccw_ti* t, int mode, int32_t B, const uint8_t* de,
-                         const uint8_t* hd, int32_t k, int32_t score_mode, uint64_t seed,
-                         const uint32_t* ctr, int32_t* ti_idx, int32_t* ti_sc, int32_t* ti_mm,
-                         int32_t* pick, int32_t* map_sc, int32_t* map_mm, void* stream) {
-  if (!t) return fail(CCW_EINVAL, "ti is NULL");
-  if (B < 0) return fail(CCW_EINVAL, "B must be >= 0");
-  if (score_mode != 0 && score_mode != 1) return fail(CCW_EINVAL, "score_mode must be 0 or 1");
-  if (int rc = check_score_bound(t, score_mode)) return rc;
-  if (B == 0) return CCW_OK;
-  if (!de) return fail(CCW_EINVAL, "de_dev is NULL");
-  if (mode == kModeSearch) {
-    if (k < 1 || k > CCW_MAX_TOPK) return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
-    if (!ctr || !ti_idx || !ti_sc || !ti_mm || !pick)
-      return fail(CCW_EINVAL, "NULL output or counter");
-  } else if (!map_sc) {
-    return fail(CCW_EINVAL, "score_dev is NULL");
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  SearchArgs a;
-  fill_ti_args(t, score_mode, a);
-  a.de = de;
-  a.hd = hd;
-  a.ctr = ctr;
-  a.K = mode == kModeSearch ? k : 1;
-  a.seed = seed;
-  a.topk_idx = ti_idx;
-  a.topk_score = ti_sc;
-  a.topk_mis = ti_mm;
-  a.pick = pick;
-  a.map_score = map_sc;
-  a.map_mis = map_mm;
-  DevBuf part, cnt;
-  if (mode == kModeSearch) {
-    const int chunk = std::min<int>(B, 65535);
-    if (part.alloc(sizeof(unsigned long long) * (size_t)chunk * a.n_tiles * a.K, st) !=
-            cudaSuccess ||
-        cnt.alloc(sizeof(unsigned int) * (size_t)chunk, st) != cudaSuccess)
-      return fail(CCW_ENOMEM, "search scratch");
-    cudaMemsetAsync(cnt.p, 0, sizeof(unsigned int) * (size_t)chunk, st);
-    a.part = (unsigned long long*)part.p;
-    a.counters = (unsigned int*)cnt.p;
-  }
-  return run_search(t, mode, a, B, 0, st);
-}
-
 int ccw_ccf_search(const ccw_ti* t, int32_t B, const uint8_t* de_dev, const uint8_t* hd_dev,
                    int32_t k, int32_t score_mode, uint64_t seed, const uint32_t* ctr_dev,
                    int32_t* topk_idx_dev, int32_t* topk_score_dev, int32_t* topk_mis_dev,
@@ -436,35 +798,6 @@ int ccw_ccf_search(const ccw_ti* t, int32_t B, const uint8_t* de_dev, const uint
                        stream);
 }
 
-// Scratch of ccw_ccf_search_noalloc: one array per device, part of the
-// library image, so using it needs no allocation. Host code reaches it only
-// through the device address looked up below; the symbol itself is a host
-// stand-in that no kernel may be given.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[CCW_NOALLOC_SCRATCH_BYTES];
-
-namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device
-
-// Device address of the scratch array on the current device; looked up once
-// per device, on the first call made with that device current.
-int noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= 256) return fail(CCW_EUNSUPPORTED, "device index %d", dev);
-  std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
-  return CCW_OK;
-}
-}  // namespace
-
 int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
                            const uint8_t* hd_dev, int32_t k, int32_t score_mode, uint64_t seed,
                            const uint32_t* ctr_dev, int32_t* topk_idx_dev,
@@ -472,17 +805,22 @@ int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
                            void* stream) {
   if (!t) return fail(CCW_EINVAL, "ti is NULL");
   if (B < 0) return fail(CCW_EINVAL, "B must be >= 0");
-  if (score_mode != 0 && score_mode != 1) return fail(CCW_EINVAL, "score_mode must be 0 or 1");
-  if (int rc = check_score_bound(t, score_mode)) return rc;
+  int sm, precision;
+  if (int rc = split_mode(score_mode, sm, precision)) return rc;
+  if (int rc = check_score_bound(t, sm)) return rc;
+  if (int rc = check_precision(t, precision, sm)) return rc;
   if (k < 1 || k > CCW_MAX_TOPK) return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
   if (B == 0) return CCW_OK;
   if (!de_dev || !ctr_dev || !topk_idx_dev || !topk_score_dev || !topk_mis_dev || !pick_dev)
     return fail(CCW_EINVAL, "NULL input, output or counter");
-  SearchArgs a;
-  fill_ti_args(t, score_mode, a);
-  const int64_t chunk = std::min<int64_t>(B, 65535);
-  const int64_t cnt_bytes = (chunk * (int64_t)sizeof(unsigned int) + 255) & ~(int64_t)255;
-  const int64_t need = cnt_bytes + chunk * a.n_tiles * k * (int64_t)sizeof(unsigned long long);
+  WaveArgs a;
+  fill_ti(t, sm, a);
+  event_layout(a.ti.nch, t->rows, t->TjP, hd_capacity(t), a.ev);
+  CcfPlan cp;
+  plan_ccf(t, precision, a.ti.nch, k, B, a.ev, cp);
+  const int64_t part_off = align_up(cp.ev_bytes, 256);
+  const int64_t bmat_off = align_up(part_off + cp.part_bytes, 256);
+  const int64_t need = bmat_off + cp.bmat_bytes;
   if (need > CCW_NOALLOC_SCRATCH_BYTES)
     return fail(CCW_EINVAL,
                 "ccw_ccf_search_noalloc: B=%d with k=%d needs %lld scratch bytes, more than "
@@ -490,33 +828,20 @@ int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
                 B, k, (long long)need, CCW_NOALLOC_SCRATCH_BYTES);
   void* base = nullptr;
   if (int rc = noalloc_scratch(&base)) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* b = (unsigned char*)base;
   a.de = de_dev;
   a.hd = hd_dev;
   a.ctr = ctr_dev;
   a.K = k;
   a.seed = seed;
-  a.counters = (unsigned int*)base;
-  a.part = (unsigned long long*)((unsigned char*)base + cnt_bytes);
-  const int64_t tv = ipow(t->T, t->ndim);
-  const int smem = search_smem_bytes(t->ndim, a.nch, t->Tj, t->TjP);
-  for (int64_t i0 = 0; i0 < B; i0 += 65535) {
-    SearchArgs c = a;
-    c.n_items = (int)std::min<int64_t>(65535, B - i0);
-    c.de = de_dev + i0 * tv;
-    c.hd = hd_dev ? hd_dev + i0 * tv : nullptr;
-    c.ctr = ctr_dev + 2 * i0;
-    c.topk_idx = topk_idx_dev + i0 * k;
-    c.topk_score = topk_score_dev + i0 * k;
-    c.topk_mis = topk_mis_dev + i0 * k;
-    c.pick = pick_dev + i0;
-    cudaError_t e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned int) * c.n_items, st);
-    if (e != cudaSuccess) return cuda_fail(e, "scratch clear");
-    e = launch_search(t->ndim, kModeSearch, c, smem, st);
-    if (e != cudaSuccess) return cuda_fail(e, "search kernel launch");
-    ++g_launches;
-  }
-  return CCW_OK;
+  a.topk_idx = topk_idx_dev;
+  a.topk_score = topk_score_dev;
+  a.topk_mis = topk_mis_dev;
+  a.pick = pick_dev;
+  // event records, ranking keys, weight matrix; every slot read is written
+  // first in the same call, so nothing needs clearing
+  return run_explicit(t, kModeSearch, a, B, cp, b, (unsigned long long*)(b + part_off),
+                      cp.bmat_bytes ? b + bmat_off : nullptr, (cudaStream_t)stream);
 }
 
 int ccw_ccf_map(const ccw_ti* t, int32_t B, const uint8_t* de_dev, const uint8_t* hd_dev,
@@ -535,20 +860,164 @@ int ccw_idwt_paste(const ccw_ti* t, int32_t B, const int32_t* pick_dev,
   for (int a = 0; a < 3; ++a)
     if (sg_dims[a] <= 0 || (a >= t->ndim && sg_dims[a] != 1))
       return fail(CCW_EINVAL, "bad sg_dims");
-  SearchArgs a;
-  fill_ti_args(t, 0, a);
   const int gd[3] = {sg_dims[0], sg_dims[1], sg_dims[2]};
-  cudaError_t e = launch_idwt_paste(t->ndim, a, B, pick_dev, dst_origin_dev, sg_dev, gd,
+  cudaError_t e = launch_idwt_paste(t->ndim, t->J, t->d_pyr, t->nc, t->cd, t->Tj, t->P, B,
+                                    pick_dev, dst_origin_dev, sg_dev, gd, t->d_status,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "paste kernel");
   ++g_launches;
   return CCW_OK;
 }
 
-int ccw_simulate(const ccw_ti* t, const ccw_params* p, const int32_t* hd_cells_dev,
-                 const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed, uint8_t* out_dev,
-                 int32_t* patch_log_dev, void* stream) {
-  if (!t || !p || !out_dev) return fail(CCW_EINVAL, "NULL argument");
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ccw_simulate
+// ---------------------------------------------------------------------------
+namespace {
+
+int build_plan(ccw_ti* t, const ccw_params* p, SimPlan*& out) {
+  SimPlan* pl = new SimPlan();
+  const int d = t->ndim;
+  const int T = t->T, S = t->T - t->O;
+  for (int a = 0; a < 3; ++a) {
+    pl->grid[a] = p->grid[a];
+    pl->g[a] = p->grid[a];
+    if (a < d) {
+      const int extra = pl->g[a] > T ? pl->g[a] - T : 0;
+      pl->np[a] = 1 + (extra + S - 1) / S;
+      pl->gp[a] = T + (pl->np[a] - 1) * S;
+    } else {
+      pl->np[a] = 1;
+      pl->gp[a] = 1;
+    }
+  }
+  pl->n_real = p->n_real;
+  pl->K = p->topk;
+  pl->score_mode = p->score_mode;
+  pl->precision = p->precision;
+  pl->n_patches = (int64_t)pl->np[0] * pl->np[1] * pl->np[2];
+  pl->gp_vol = (int64_t)pl->gp[0] * pl->gp[1] * pl->gp[2];
+  pl->g_vol = (int64_t)pl->g[0] * pl->g[1] * pl->g[2];
+  // wavefront schedule: wave(p) = ix + 2 iy + 4 iz over the lattice index
+  pl->n_waves = (pl->np[0] - 1) + 2 * (pl->np[1] - 1) + 4 * (pl->np[2] - 1) + 1;
+  std::vector<std::vector<int>> wave_patches(pl->n_waves);
+  for (int64_t pp = 0; pp < pl->n_patches; ++pp) {
+    const int ix = (int)(pp % pl->np[0]), iy = (int)((pp / pl->np[0]) % pl->np[1]),
+              iz = (int)(pp / ((int64_t)pl->np[0] * pl->np[1]));
+    wave_patches[ix + 2 * iy + 4 * iz].push_back((int)pp);
+  }
+  std::vector<int2> items;
+  items.reserve((size_t)pl->n_patches * pl->n_real);
+  pl->wave_off.assign(pl->n_waves + 1, 0);
+  pl->max_items = 0;
+  for (int w = 0; w < pl->n_waves; ++w) {
+    pl->wave_off[w] = (int64_t)items.size();
+    for (int r = 0; r < pl->n_real; ++r)
+      for (int pp : wave_patches[w]) items.push_back(make_int2(r, pp));
+    pl->max_items = std::max<int>(pl->max_items, (int)(items.size() - pl->wave_off[w]));
+  }
+  pl->wave_off[pl->n_waves] = (int64_t)items.size();
+  const int nch = p->score_mode == 0 ? t->F - 1 : 1;
+  event_layout(nch, t->rows, t->TjP, hd_capacity(t), pl->evl);
+  CcfPlan* cp = new CcfPlan();
+  pl->cp = cp;
+  plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp);
+  cudaError_t e;
+  if ((e = cudaMalloc(&pl->sg, (size_t)pl->gp_vol * pl->n_real)) != cudaSuccess ||
+      (e = cudaMalloc(&pl->overlay, (size_t)align_up(pl->g_vol, 4))) != cudaSuccess ||
+      (e = cudaMalloc(&pl->items, sizeof(int2) * items.size())) != cudaSuccess ||
+      (e = cudaMalloc(&pl->ev, (size_t)cp->ev_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&pl->part, (size_t)cp->part_bytes)) != cudaSuccess ||
+      (cp->bmat_bytes && (e = cudaMalloc(&pl->bmat, (size_t)cp->bmat_bytes)) != cudaSuccess) ||
+      (e = cudaMalloc((void**)&pl->call, sizeof(CallDev))) != cudaSuccess) {
+    delete pl;
+    return fail(CCW_ENOMEM, "simulation workspace: %s", cudaGetErrorString(e));
+  }
+  pl->evl.base = (unsigned char*)pl->ev;
+  if ((e = cudaMemcpy(pl->items, items.data(), sizeof(int2) * items.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "simulation plan");
+  }
+  out = pl;
+  return CCW_OK;
+}
+
+// Launch phases A, B and C of every wave on `st` (while `st` is being
+// captured into the plan's graph).
+int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
+  WaveArgs a;
+  fill_ti(t, pl->score_mode, a);
+  a.ev = pl->evl;
+  a.sim.sg = (uint8_t*)pl->sg;
+  a.sim.overlay = (const uint8_t*)pl->overlay;
+  for (int i = 0; i < 3; ++i) {
+    a.sim.G[i] = pl->g[i];
+    a.sim.Gp[i] = pl->gp[i];
+    a.sim.np[i] = pl->np[i];
+  }
+  a.sim.S = t->T - t->O;
+  a.sim.gp_vol = pl->gp_vol;
+  a.sim.n_patches = pl->n_patches;
+  a.call = pl->call;
+  a.K = pl->K;
+  a.part = (unsigned long long*)pl->part;
+  const CcfPlan& cp = *static_cast<const CcfPlan*>(pl->cp);
+  size_t pe = 0;
+  for (int w = 0; w < pl->n_waves; ++w) {
+    for (int64_t i0 = pl->wave_off[w]; i0 < pl->wave_off[w + 1]; i0 += 65535) {
+      WaveArgs c = a;
+      c.items = (const int2*)pl->items + i0;
+      c.n_items = (int)std::min<int64_t>(65535, pl->wave_off[w + 1] - i0);
+      apply_ccf(t, cp, pl->bmat, c);
+      cudaError_t e = launch_events(kModeSim, c, true, st);
+      if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
+      if (prof) {
+        if (pe >= pl->prof_events.size()) {
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          pl->prof_events.emplace_back(e0, e1);
+        }
+        cudaEventRecordWithFlags(pl->prof_events[pe].first, st, cudaEventRecordExternal);
+      }
+      e = launch_ccf(t, kModeSim, cp, c, !prof, st);
+      if (e != cudaSuccess) return cuda_fail(e, "CCF kernel launch");
+      if (prof)
+        cudaEventRecordWithFlags(pl->prof_events[pe++].second, st, cudaEventRecordExternal);
+      e = launch_finish(kModeSim, c, !prof, st);
+      if (e != cudaSuccess) return cuda_fail(e, "finish kernel launch");
+    }
+  }
+  return CCW_OK;
+}
+
+int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+  int rc = launch_waves(t, pl, prof, pl->cap);
+  e = cudaStreamEndCapture(pl->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  e = cudaGraphInstantiate(&pl->exec[prof ? 1 : 0], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+  return CCW_OK;
+}
+
+}  // namespace
+
+extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t* hd_cells_dev,
+                            const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed,
+                            uint8_t* out_dev, int32_t* patch_log_dev, void* stream) {
+  if (!tc || !p || !out_dev) return fail(CCW_EINVAL, "NULL argument");
+  ccw_ti* t = const_cast<ccw_ti*>(tc);
   const int d = t->ndim;
   if (p->ndim != d) return fail(CCW_EINVAL, "params ndim %d != TI ndim %d", p->ndim, d);
   if (p->topk < 1 || p->topk > CCW_MAX_TOPK)
@@ -556,112 +1025,69 @@ int ccw_simulate(const ccw_ti* t, const ccw_params* p, const int32_t* hd_cells_d
   if (p->n_real < 1) return fail(CCW_EINVAL, "n_real must be >= 1");
   if (p->real_base < 0) return fail(CCW_EINVAL, "real_base must be >= 0");
   if (p->score_mode != 0 && p->score_mode != 1) return fail(CCW_EINVAL, "bad score_mode");
-  if (p->precision != 0)
-    return fail(CCW_EUNSUPPORTED, "precision %d is not available in this build", p->precision);
+  if (int rc = check_precision(t, p->precision, p->score_mode)) return rc;
   if (p->path_random != 0 && p->path_random != 1) return fail(CCW_EINVAL, "bad path_random");
   for (int i = 0; i < 4; ++i)
     if (p->reserved[i]) return fail(CCW_EINVAL, "reserved fields must be 0");
   if (n_hd < 0 || (n_hd > 0 && (!hd_cells_dev || !hd_vals_dev)))
     return fail(CCW_EINVAL, "bad hard data");
   if (int rc = check_score_bound(t, p->score_mode)) return rc;
-  int g[3], np_[3], gp[3];
-  const int T = t->T, S = t->T - t->O;
-  for (int a = 0; a < 3; ++a) {
-    g[a] = p->grid[a];
-    if (g[a] <= 0 || (a >= d && g[a] != 1)) return fail(CCW_EINVAL, "bad grid dims");
-    if (a < d) {
-      const int extra = g[a] > T ? g[a] - T : 0;
-      np_[a] = 1 + (extra + S - 1) / S;
-      gp[a] = T + (np_[a] - 1) * S;
-    } else {
-      np_[a] = 1;
-      gp[a] = 1;
-    }
-  }
-  const int64_t n_patches = (int64_t)np_[0] * np_[1] * np_[2];
-  const int64_t gp_vol = (int64_t)gp[0] * gp[1] * gp[2];
-  const int64_t g_vol = (int64_t)g[0] * g[1] * g[2];
-  const int n_real = p->n_real;
-  const int K = p->topk;
+  for (int a = 0; a < 3; ++a)
+    if (p->grid[a] <= 0 || (a >= d && p->grid[a] != 1)) return fail(CCW_EINVAL, "bad grid dims");
 
-  // wavefront schedule: wave(p) = ix + 2 iy + 4 iz over the path index
-  const int n_waves = (np_[0] - 1) + 2 * (np_[1] - 1) + 4 * (np_[2] - 1) + 1;
-  std::vector<std::vector<int>> wave_patches(n_waves);
-  for (int64_t pp = 0; pp < n_patches; ++pp) {
-    const int ix = (int)(pp % np_[0]), iy = (int)((pp / np_[0]) % np_[1]),
-              iz = (int)(pp / ((int64_t)np_[0] * np_[1]));
-    wave_patches[ix + 2 * iy + 4 * iz].push_back((int)pp);
-  }
-  std::vector<int2> items;
-  items.reserve((size_t)n_patches * n_real);
-  std::vector<int64_t> wave_off(n_waves + 1, 0);
-  int max_items = 0;
-  for (int w = 0; w < n_waves; ++w) {
-    wave_off[w] = (int64_t)items.size();
-    for (int r = 0; r < n_real; ++r)
-      for (int pp : wave_patches[w]) items.push_back(make_int2(r, pp));
-    max_items = std::max<int>(max_items, (int)(items.size() - wave_off[w]));
-  }
-  wave_off[n_waves] = (int64_t)items.size();
-
+  std::lock_guard<std::mutex> lock(t->mu);
   cudaStream_t st = (cudaStream_t)stream;
-  SearchArgs a;
-  fill_ti_args(t, p->score_mode, a);
-  const int chunk = std::min(max_items, 65535);
-  DevBuf sg, overlay, d_items, part, cnt;
-  if (sg.alloc((size_t)gp_vol * n_real, st) != cudaSuccess ||
-      overlay.alloc((size_t)((g_vol + 3) & ~3LL), st) != cudaSuccess ||
-      d_items.alloc(sizeof(int2) * items.size(), st) != cudaSuccess ||
-      part.alloc(sizeof(unsigned long long) * (size_t)chunk * a.n_tiles * K, st) != cudaSuccess ||
-      cnt.alloc(sizeof(unsigned int) * (size_t)chunk, st) != cudaSuccess)
-    return fail(CCW_ENOMEM, "simulation workspace");
+  SimPlan* pl = t->plan;
+  if (!pl || pl->grid[0] != p->grid[0] || pl->grid[1] != p->grid[1] ||
+      pl->grid[2] != p->grid[2] || pl->n_real != p->n_real || pl->K != p->topk ||
+      pl->score_mode != p->score_mode || pl->precision != p->precision) {
+    cudaDeviceSynchronize();
+    delete t->plan;
+    t->plan = nullptr;
+    if (int rc = build_plan(t, p, pl)) return rc;
+    t->plan = pl;
+  }
+  bool prof;
+  unsigned long long* work = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    prof = g_prof.enabled;
+    if (prof) work = profiling_counters();
+  }
+  CallDev call;
+  call.seed = seed;
+  call.real_base = p->real_base;
+  call.path_random = p->path_random;
+  call.log = patch_log_dev;
+  call.log_stride = 4 + p->topk;
+  call.work = work;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(sg.p, 0xFF, (size_t)gp_vol * n_real, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(overlay.p, 0xFF, (size_t)((g_vol + 3) & ~3LL), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(cnt.p, 0, sizeof(unsigned int) * (size_t)chunk, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(t->d_status, 0, sizeof(int), st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_items.p, items.data(), sizeof(int2) * items.size(),
-                           cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(pl->call, &call, sizeof(call), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(pl->sg, 0xFF, (size_t)pl->gp_vol * pl->n_real, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(pl->overlay, 0xFF, (size_t)align_up(pl->g_vol, 4), st)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(t->d_status, 0, sizeof(int), st)) != cudaSuccess)
     return cuda_fail(e, "simulation setup");
-  if ((e = launch_hd_overlay(hd_cells_dev, hd_vals_dev, n_hd, d, g, t->F, (uint8_t*)overlay.p,
-                             t->d_status, st)) != cudaSuccess)
+  if ((e = launch_hd_overlay(hd_cells_dev, hd_vals_dev, n_hd, d, pl->g, t->F,
+                             (uint8_t*)pl->overlay, t->d_status, st)) != cudaSuccess)
     return cuda_fail(e, "hard-data kernel");
   if (n_hd > 0) ++g_launches;
-  if (patch_log_dev) {
-    // patches never reached cannot exist here, but keep the log well defined
-    if ((e = cudaMemsetAsync(patch_log_dev, 0xFF,
-                             sizeof(int32_t) * (size_t)n_real * n_patches * (4 + K), st)) !=
-        cudaSuccess)
-      return cuda_fail(e, "log clear");
-  }
-
-  a.sg = (uint8_t*)sg.p;
-  a.overlay = (const uint8_t*)overlay.p;
-  for (int i = 0; i < 3; ++i) {
-    a.G[i] = g[i];
-    a.Gp[i] = gp[i];
-    a.np[i] = np_[i];
-  }
-  a.S = S;
-  a.path_random = p->path_random;
-  a.real_base = p->real_base;
-  a.gp_vol = gp_vol;
-  a.n_patches = n_patches;
-  a.K = K;
-  a.seed = seed;
-  a.part = (unsigned long long*)part.p;
-  a.counters = (unsigned int*)cnt.p;
-  a.log = patch_log_dev;
-  a.log_stride = 4 + K;
-  for (int w = 0; w < n_waves; ++w) {
-    const int n = (int)(wave_off[w + 1] - wave_off[w]);
-    if (n == 0) continue;
-    SearchArgs c = a;
-    c.items = (const int2*)d_items.p + wave_off[w];
-    if (int rc = run_search(t, kModeSim, c, n, 0, st)) return rc;
-  }
-  if ((e = launch_crop_out((const uint8_t*)sg.p, gp_vol, gp, out_dev, g, d, n_real,
-                           p->path_random, seed, p->real_base, st)) != cudaSuccess)
+  if (patch_log_dev &&
+      (e = cudaMemsetAsync(patch_log_dev, 0xFF,
+                           sizeof(int32_t) * (size_t)pl->n_real * pl->n_patches * (4 + p->topk),
+                           st)) != cudaSuccess)
+    return cuda_fail(e, "log clear");
+  const int gi = prof ? 1 : 0;
+  if (!pl->exec[gi])
+    if (int rc = capture_waves(t, pl, prof)) return rc;
+  if ((e = cudaGraphLaunch(pl->exec[gi], st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+  int64_t wave_launches = 0;
+  for (int w = 0; w < pl->n_waves; ++w)
+    wave_launches += 3 * ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
+  g_launches += wave_launches;
+  if ((e = launch_crop_out((const uint8_t*)pl->sg, pl->gp_vol, pl->gp, out_dev, pl->g, d,
+                           pl->n_real, p->path_random, seed, p->real_base, st)) != cudaSuccess)
     return cuda_fail(e, "crop kernel");
   ++g_launches;
   int status = 0;
@@ -669,6 +1095,16 @@ int ccw_simulate(const ccw_ti* t, const ccw_params* p, const int32_t* hd_cells_d
           cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_fail(e, "simulation");
+  if (prof) {
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    for (auto& pr : pl->prof_events) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        g_prof.total_ms += ms;
+        ++g_prof.launches;
+      }
+    }
+  }
   if (status & kStatusBadCode)
     return fail(CCW_EINVAL, "hard data out of the grid or with a code >= n_facies");
   if (status & kStatusHdOverflow)
@@ -676,5 +1112,3 @@ int ccw_simulate(const ccw_ti* t, const ccw_params* p, const int32_t* hd_cells_d
   if (status & kStatusTimeout) return fail(CCW_ETIMEOUT, "a bounded device wait gave up");
   return CCW_OK;
 }
-
-}  // extern "C"

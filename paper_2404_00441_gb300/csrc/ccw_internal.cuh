@@ -16,11 +16,13 @@ enum : int {
   kStatusTimeout = 4,
 };
 
-constexpr int kThreads = 256;     // threads per CTA of the search kernel
+constexpr int kThreads = 256;     // threads per CTA of the CCF and event kernels
+constexpr int kWarps = kThreads / 32;
 constexpr int kRx = 4;            // consecutive x-candidates per thread
 constexpr int kMaxHd = 1024;      // hard data kept per template window
 constexpr int kMaxLevel2D = 4;
 constexpr int kMaxLevel3D = 2;
+constexpr int kMaxChunks = 32;    // 4-wide tap chunks per template row (Tj <= 128)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): the round multiplies
@@ -93,44 +95,91 @@ constexpr uint64_t kNoKey = ~0ull;
 // ---------------------------------------------------------------------------
 enum Mode : int { kModeSim = 0, kModeSearch = 1, kModeMap = 2 };
 
-struct SearchArgs {
-  // training image
-  const float* planes;     // nch level-J planes, each ncv floats
-  const uint8_t* ti;       // cropped fine TI
-  const int16_t* pyr;      // per-block Haar coefficients [ncv][s^d]
-  int nch;                 // channels scored (F-1 one-hot, 1 literal)
-  int F, J, s, sd, T, Tj, TjP, d, score_mode;
+// The prepared training image as the kernels see it.
+struct TiDev {
+  const float* planes;  // [F planes][nc2][nc1][px] floats: counts of facies 0..F-2, code sums
+  int px;               // plane row pitch (floats, multiple of 4, zero padded)
+  int64_t plane_vol;    // floats per plane
+  int plane0, nch;      // planes scored by the active score mode
+  const uint8_t* ti;    // cropped fine TI [n]
+  const int16_t* pyr;   // per-block Haar coefficients [ncv][sd]
+  int F, J, s, sd, T, Tj, TjP, chunks, rows, d, score_mode;
   int n[3], nc[3], cd[3];
   int64_t ncv, P;
-  int tiles[3], n_tiles;   // candidate tiles per axis, total
-  // items of this launch
-  int n_items;
-  const int2* items;       // sim: (realization slot, patch) pairs
-  // simulation state
+  int tile[3];          // candidates per CTA tile along x, y, z
+  int tiles[3], n_tiles;
+};
+
+// Per-item event records written by the event kernel (phase A) and read by
+// the CCF kernel (phase B). Record of item i starts at base + i * stride:
+//   int32 meta[16] (kEv*), uint32 rowmask[rows] (bit g: 4-wide tap chunk g
+//   holds a non-zero weight in some channel), int2 hd[hd_cap] (.x: offset of
+//   the hard datum in the cropped fine TI relative to a candidate's first
+//   cell; .y: (offset in the template window << 8) | code),
+//   float w[nch][rows][TjP].
+enum { kEvKnown = 0, kEvConst = 1, kEvMaskCells = 2, kEvNHd = 3 };
+struct EvDev {
+  unsigned char* base;
+  int64_t stride;
+  int mask_off, hd_off, w_off, hd_cap;
+};
+
+struct SimDev {
   uint8_t* sg;             // [n_real][Gp] padded grids, 255 = not simulated
   const uint8_t* overlay;  // [G] hard data, 255 = none
-  int G[3], Gp[3], np[3], S, path_random, real_base;
+  int G[3], Gp[3], np[3], S;
   int64_t gp_vol, n_patches;
-  // explicit data events
+};
+
+// Per-call values of a simulation, read from device memory so that a
+// captured wave graph can be replayed with another seed or output.
+struct CallDev {
+  uint64_t seed;
+  int real_base, path_random;
+  int32_t* log;
+  int log_stride;
+  unsigned long long* work;  // profiling counters [2] or NULL
+};
+
+struct WaveArgs {
+  TiDev ti;
+  EvDev ev;
+  SimDev sim;
+  const CallDev* call;      // simulation mode
+  const int2* items;        // simulation: (realization slot, patch)
+  int n_items;
+  int nb;                   // items per CTA in the CCF kernel
+  // explicit data events (search / map)
   const uint8_t* de;
   const uint8_t* hd;
   const uint32_t* ctr;
+  uint64_t seed;
+  // tensor-core path (precision 1: FP16, 2: BF16)
+  int precision;
+  const void* z8;           // [F planes][z8_nq][8][8] 16-bit 8-shift view of the planes
+  int64_t z8_nq;            // core matrices per plane
+  int px8;                  // line pitch of the planes (multiple of 8)
+  int ks;                   // taps per template row padded to a multiple of 16
+  int ksteps;               // K steps of 16 taps: nch * rows * ks / 16
+  int mtiles;               // 128-position M-tiles over the candidate lines
+  int mt;                   // M-tiles per CTA
+  int n_mgroups;            // CTAs along M
+  int nt;                   // items per N-tile
+  int a_nq;                 // core matrices of one channel's A region per CTA
+  void* bmat;               // [N-tiles][ksteps][nt/8][2][8][8] 16-bit weights
   // selection
   int K;
-  uint64_t seed;
-  unsigned long long* part;     // [n_items][n_tiles][K]
-  unsigned int* counters;       // [n_items]
+  int n_parts;              // per-item partial lists written by the CCF kernel
+  unsigned long long* part;     // [n_items][n_parts][K] partial ranking keys
   // outputs
   int32_t* topk_idx;
   int32_t* topk_score;
   int32_t* topk_mis;
   int32_t* pick;
-  int32_t* log;
-  int log_stride;
   int32_t* map_score;
   int32_t* map_mis;
   int* status;
-  unsigned long long* work;     // profiling: [0] candidate evals, [1] MACs (or NULL)
+  unsigned long long* work;     // profiling counters for search/map mode (or NULL)
 };
 
 }  // namespace ccw

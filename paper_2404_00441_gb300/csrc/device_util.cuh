@@ -1,0 +1,302 @@
+// device_util.cuh -- device helpers shared by the kernels: reductions,
+// mbarrier / TMA wrappers with bounded waits, the Inverse-DWT paste and the
+// decoding of simulation items.
+#pragma once
+
+#include <cuda.h>
+
+#include <utility>
+
+#include "ccw_internal.cuh"
+
+namespace ccw {
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (w < v) ? w : v;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor in the
+// stream runs; pdl_wait() blocks until the predecessor has completed and its
+// memory is visible, pdl_trigger() lets the successor start launching.
+// Both are no-ops for kernels launched without the attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `kernel` on `st`, with the programmatic stream-serialization
+// attribute when `pdl` is set.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, int smem,
+                              cudaStream_t st, bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier and bulk-tensor copies (PTX ISA: mbarrier.*, cp.async.bulk.tensor)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier. Returns false when the
+// iteration limit is reached (the caller records kStatusTimeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint32_t max_iters = (1u << 22)) {
+  for (uint32_t i = 0; i < max_iters; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 4D tiled bulk-tensor load (global -> shared), completion on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct PasteGeom {
+  const int16_t* pyr;
+  int nc0, nc1;      // level-J TI dims (x, y)
+  int cd0, cd1;      // candidate grid dims (x, y)
+  int Tj;
+  uint8_t* grid;
+  int g[3];          // grid dims
+  int o[3];          // window origin in grid coordinates
+};
+
+// Visit the cells (qx, qy, qz) of a T^d window with consecutive threads on
+// consecutive x (coalesced rows); indices advance without divisions.
+template <int D, typename Fn>
+__device__ __forceinline__ void for_window(int T, int nthreads, Fn&& fn) {
+  const int nrows = (D == 3) ? T * T : T;
+  if (T <= nthreads) {
+    const int rpi = nthreads / T;
+    const int qx = threadIdx.x % T, r0 = threadIdx.x / T;
+    if (r0 >= rpi) return;
+    int qy = r0, qz = 0;
+    while (qy >= T) {
+      qy -= T;
+      ++qz;
+    }
+    for (int row = r0; row < nrows; row += rpi) {
+      fn(qx, qy, qz);
+      qy += rpi;
+      while (qy >= T) {
+        qy -= T;
+        ++qz;
+      }
+    }
+  } else {
+    for (int row = 0; row < nrows; ++row)
+      for (int qx = threadIdx.x; qx < T; qx += nthreads) fn(qx, row % T, row / T);
+  }
+}
+
+// Copy the level-J blocks covered by candidate `pick` (Tj^d blocks of s^d
+// coefficients, one contiguous run of Tj blocks per coarse row) into shared
+// memory, ordered (ux fastest, then uy, uz). Needs a following barrier.
+template <int D>
+__device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, int nthreads) {
+  const int s = 1 << J;
+  const int sd = (D == 3) ? s * s * s : s * s;
+  const int pcx = pick % p.cd0;
+  const int pcy = (pick / p.cd0) % p.cd1;
+  const int pcz = pick / (p.cd0 * p.cd1);
+  const int Tj = p.Tj;
+  const int nrows = (D == 3) ? Tj * Tj : Tj;
+  const int run = Tj * sd;   // coefficients per coarse row
+  if (sd % 4 == 0) {
+    const int run4 = run / 4;
+    for (int i = threadIdx.x; i < nrows * run4; i += nthreads) {
+      const int row = i / run4, k = i % run4;
+      const int uy = row % Tj, uz = row / Tj;
+      const int16_t* src =
+          p.pyr + ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
+      reinterpret_cast<uint2*>(sm + (int64_t)row * run)[k] =
+          __ldg(reinterpret_cast<const uint2*>(src) + k);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nrows * run; i += nthreads) {
+      const int row = i / run, k = i % run;
+      const int uy = row % Tj, uz = row / Tj;
+      const int16_t* src =
+          p.pyr + ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
+      sm[(int64_t)row * run + k] = __ldg(src + k);
+    }
+  }
+}
+
+// CTA-cooperative Inverse-DWT paste of candidate `pick` (Algorithm 1, lines
+// 13-14). Each fine cell q of the pattern is the Haar expansion of Sec. 3.1
+// evaluated at q: with s = 2^J, the scaled-Haar synthesis gives
+//   s^d x(q) = cA_J + sum_{j=1..J} 2^(d (J - j)) sum_{b != 0} sign_{j,b}(q) Z_{j,b}
+// where Z_{j,b} is the level-j detail coefficient of band b covering q and
+// sign_{j,b}(q) is the product, over the axes of band b, of +1 (q in the
+// lower half of its level-j cell along that axis) or -1 (upper half). In the
+// per-block in-place layout Z_{j,b} sits at the cell's origin plus 2^(j-1)
+// along every axis of b. Coefficients come from `staged` (stage_blocks) when
+// given, else from global memory. Cells outside the grid are skipped. The
+// caller re-imposes hard data afterwards (after a barrier).
+template <int D>
+__device__ void paste_pixels(const PasteGeom& p, int pick, int J, int nthreads,
+                             const int16_t* staged = nullptr) {
+  const int s = 1 << J;
+  const int sd = (D == 3) ? s * s * s : s * s;
+  const int pcx = pick % p.cd0;
+  const int pcy = (pick / p.cd0) % p.cd1;
+  const int pcz = pick / (p.cd0 * p.cd1);
+  const int Tj = p.Tj;
+  const int T = Tj * s;
+  for_window<D>(T, nthreads, [&](int qx, int qy, int qz) {
+    const int gx = p.o[0] + qx, gy = p.o[1] + qy, gz = p.o[2] + qz;
+    if (gx < 0 || gy < 0 || gz < 0 || gx >= p.g[0] || gy >= p.g[1] || gz >= p.g[2]) return;
+    const int ux = qx >> J, uy = qy >> J, uz = qz >> J;
+    const int cx = qx & (s - 1), cy = qy & (s - 1), cz = qz & (s - 1);
+    const int16_t* blk =
+        staged ? staged + (ux + Tj * (uy + Tj * uz)) * sd
+               : p.pyr + ((int64_t)(pcx + ux) +
+                          (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
+    int acc = blk[0];
+    for (int j = 1; j <= J; ++j) {
+      const int h = 1 << (j - 1);
+      const int m = ~((1 << j) - 1);
+      const int bx = cx & m, by = cy & m, bz = cz & m;
+      const int sx = (cx & h) ? -1 : 1, sy = (cy & h) ? -1 : 1, sz = (cz & h) ? -1 : 1;
+      const int f = 1 << (D * (J - j));
+      for (int b = 1; b < (1 << D); ++b) {
+        const int px = bx + ((b & 1) ? h : 0), py = by + ((b & 2) ? h : 0),
+                  pz = bz + ((b & 4) ? h : 0);
+        const int sign = ((b & 1) ? sx : 1) * ((b & 2) ? sy : 1) * ((b & 4) ? sz : 1);
+        acc += f * sign * (int)blk[px + s * (py + s * pz)];
+      }
+    }
+    p.grid[gx + (int64_t)p.g[0] * (gy + (int64_t)p.g[1] * gz)] = (uint8_t)(acc >> (D * J));
+  });
+}
+
+// Re-impose the hard data of a pasted window (event-record list, int2 .y =
+// (window offset << 8) | code). Call after a barrier that follows the paste.
+template <int D>
+__device__ void paste_hard_data(const PasteGeom& p, const int2* hdl, int n_hd, int T,
+                                int nthreads) {
+  for (int k = threadIdx.x; k < n_hd; k += nthreads) {
+    const int e = hdl[k].y;
+    const int q = e >> 8;
+    const int qx = q % T, qy = (q / T) % T, qz = (D == 3) ? q / (T * T) : 0;
+    const int gx = p.o[0] + qx, gy = p.o[1] + qy, gz = p.o[2] + qz;
+    if (gx < 0 || gy < 0 || gz < 0 || gx >= p.g[0] || gy >= p.g[1] || gz >= p.g[2]) continue;
+    p.grid[gx + (int64_t)p.g[0] * (gy + (int64_t)p.g[1] * gz)] = (uint8_t)(e & 0xFF);
+  }
+}
+
+// Position of a simulation item (realization slot, patch) in its padded
+// grid, with the path mirroring of its realization (Algorithm 1, line 3).
+struct ItemPos {
+  int slot, patch;
+  uint32_t r, p;
+  int o[3], off[3];
+};
+
+template <int D>
+__device__ __forceinline__ ItemPos decode_sim_item(const WaveArgs& a, int item) {
+  ItemPos it;
+  const int2 v = a.items[item];
+  it.slot = v.x;
+  it.patch = v.y;
+  const CallDev* c = a.call;
+  it.r = (uint32_t)(c->real_base + it.slot);
+  it.p = (uint32_t)it.patch;
+  const uint32_t flips =
+      c->path_random ? (draw_word(c->seed, it.r, 0u, 1u) & ((1u << D) - 1u)) : 0u;
+  const SimDev& s = a.sim;
+  const int ip[3] = {it.patch % s.np[0], (it.patch / s.np[0]) % s.np[1],
+                     it.patch / (s.np[0] * s.np[1])};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const bool f = (flips >> ax) & 1u;
+    if (ax < D) {
+      it.o[ax] = f ? s.Gp[ax] - a.ti.T - s.S * ip[ax] : s.S * ip[ax];
+      it.off[ax] = f ? s.Gp[ax] - s.G[ax] : 0;
+    } else {
+      it.o[ax] = 0;
+      it.off[ax] = 0;
+    }
+  }
+  return it;
+}
+
+template <int D>
+__device__ __forceinline__ PasteGeom sim_paste_geom(const WaveArgs& a, const ItemPos& it) {
+  PasteGeom g;
+  g.pyr = a.ti.pyr;
+  g.nc0 = a.ti.nc[0];
+  g.nc1 = a.ti.nc[1];
+  g.cd0 = a.ti.cd[0];
+  g.cd1 = a.ti.cd[1];
+  g.Tj = a.ti.Tj;
+  g.grid = a.sim.sg + (int64_t)it.slot * a.sim.gp_vol;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    g.g[ax] = a.sim.Gp[ax];
+    g.o[ax] = it.o[ax];
+  }
+  return g;
+}
+
+}  // namespace ccw

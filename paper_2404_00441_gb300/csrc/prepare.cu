@@ -1,6 +1,11 @@
 // prepare.cu -- training-image preparation (Algorithm 1, line 2: DWT of the
 // TI at level J), the hard-data overlay and the final crop of the simulation
 // grid.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include <algorithm>
 
 #include "ccw_internal.cuh"
@@ -53,9 +58,10 @@ __device__ void haar_block_forward(int* v, int s, int J) {
 // code image) and the block's full J-level Haar coefficients of the codes.
 template <int D>
 __global__ void k_ti_pyramid(const uint8_t* __restrict__ ti, int nx, int ny, int ncx, int ncy,
-                             int ncz, int s, int J, int F, float* __restrict__ planes,
+                             int ncz, int s, int J, int F, float* __restrict__ planes, int px,
                              int16_t* __restrict__ pyr) {
   const int64_t ncv = (int64_t)ncx * ncy * ncz;
+  const int64_t plane_vol = (int64_t)px * ncy * ncz;
   const int sd = (D == 3) ? s * s * s : s * s;
   const int sz = (D == 3) ? s : 1;
   int v[256];
@@ -76,8 +82,9 @@ __global__ void k_ti_pyramid(const uint8_t* __restrict__ ti, int nx, int ny, int
 #pragma unroll
           for (int f = 0; f < 8; ++f) counts[f] += (c == f);
         }
-    for (int f = 0; f < F - 1; ++f) planes[f * ncv + b] = (float)counts[f];
-    planes[(int64_t)(F - 1) * ncv + b] = (float)csum;
+    const int64_t pb = bx + (int64_t)px * (by + (int64_t)ncy * bz);
+    for (int f = 0; f < F - 1; ++f) planes[f * plane_vol + pb] = (float)counts[f];
+    planes[(int64_t)(F - 1) * plane_vol + pb] = (float)csum;
     haar_block_forward<D>(v, s, J);
     int16_t* dst = pyr + b * sd;
     for (int c = 0; c < sd; ++c) dst[c] = (int16_t)v[c];
@@ -134,6 +141,48 @@ __global__ void k_crop_out(const uint8_t* __restrict__ sg, int64_t gp_vol, int g
   }
 }
 
+// The 8-shift view of the linearised level-J planes used by the tensor-core
+// CCF. Plane p is read as a line lin_p[x + px8 * y] = plane p at (x, y),
+// 0 for x >= nc0 or y >= nc1; z8[p][q][r][e] = lin_p[8 q + r + e] (16-bit,
+// exact for the integer counts). With this copy the im2col matrix of any
+// 128 consecutive line positions and 16 consecutive taps is a plain strided
+// view (8 x 8 core matrices 128 bytes apart along both the candidate and the
+// tap direction).
+template <typename Th>
+__global__ void k_z8(const float* __restrict__ planes, int px, int64_t plane_vol, int nc0, int nc1,
+                     int px8, int64_t nq, int nplanes, Th* __restrict__ z8) {
+  const int64_t per = nq * 64;
+  const int64_t total = per * nplanes;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(i / per);
+    const int64_t rem = i - p * per;
+    const int64_t q = rem >> 6;
+    const int r = (int)((rem >> 3) & 7), e = (int)(rem & 7);
+    const int64_t L = 8 * q + r + e;
+    const int64_t x = L % px8, y = L / px8;
+    float v = 0.f;
+    if (x < nc0 && y < nc1) v = planes[p * plane_vol + x + (int64_t)px * y];
+    if constexpr (sizeof(Th) == 2 && std::is_same<Th, __half>::value)
+      z8[i] = __float2half_rn(v);
+    else
+      z8[i] = __float2bfloat16_rn(v);
+  }
+}
+
+cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
+                      int64_t nq, int nplanes, void* z8_f16, void* z8_bf16, cudaStream_t st) {
+  const int64_t total = nq * 64 * nplanes;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  k_z8<__half><<<blocks, 256, 0, st>>>(planes, px, plane_vol, nc0, nc1, px8, nq, nplanes,
+                                       (__half*)z8_f16);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_z8<__nv_bfloat16><<<blocks, 256, 0, st>>>(planes, px, plane_vol, nc0, nc1, px8, nq, nplanes,
+                                              (__nv_bfloat16*)z8_bf16);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst, const int n[3],
                            int F, int* status, cudaStream_t st) {
@@ -144,15 +193,16 @@ cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst,
 }
 
 cudaError_t launch_ti_pyramid(int d, const uint8_t* ti, const int n[3], const int nc[3], int s,
-                              int J, int F, float* planes, int16_t* pyr, cudaStream_t st) {
+                              int J, int F, float* planes, int px, int16_t* pyr,
+                              cudaStream_t st) {
   const int64_t ncv = (int64_t)nc[0] * nc[1] * nc[2];
   const int blocks = (int)std::min<int64_t>((ncv + 127) / 128, 152 * 16);
   if (d == 3)
     k_ti_pyramid<3><<<blocks, 128, 0, st>>>(ti, n[0], n[1], nc[0], nc[1], nc[2], s, J, F, planes,
-                                            pyr);
+                                            px, pyr);
   else
     k_ti_pyramid<2><<<blocks, 128, 0, st>>>(ti, n[0], n[1], nc[0], nc[1], nc[2], s, J, F, planes,
-                                            pyr);
+                                            px, pyr);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,388 @@
+// tc.cu -- phase B of a search step on the 5th-generation tensor cores
+// (tcgen05, sm_103a): the masked cross-correlation of Eq. CCW (Algorithm 1,
+// line 10) of a batch of data events as one contraction
+//     S[c, n] = sum_k A[c, k] B[n, k],
+// c over candidates, n over the data events (items) of the step, k over
+// (channel, template row, tap). FP16 or BF16 operands, FP32 accumulation in
+// tensor memory; exact because every operand is an integer within the
+// format's exact range and every partial sum is an integer below 2^24 (both
+// checked on the host).
+//
+// Layout (2D). The candidate positions of the level-J TI are read as a line
+// of pitch px8 (a multiple of 8): position L = x + px8 y. For the 128
+// positions L0..L0+127 of one M-tile, template row ky and taps kx in
+// [16 k16, 16 k16 + 16), A[m, kx] = plane[L0 + m + ky px8 + kx]. With the
+// 8-shift copy z8[q][r][e] = plane[8q + r + e] prepared with the TI, the
+// 8 x 8 core matrix (m-group i, k-group j) of that tile is z8[q0 + i + j] with
+// q0 = (L0 + ky px8)/8 + 2 k16: a no-swizzle K-major operand whose core
+// matrices are 128 bytes apart along both M and K. One bulk copy per channel
+// brings every core matrix a CTA needs into shared memory. B (the items'
+// weights) is written by the event kernel directly in the canonical K-major
+// layout and arrives with one more bulk copy.
+//
+// Each CTA owns mt (<= 4) consecutive M-tiles and one N-tile of nt items.
+// The accumulators of its M-tiles (128 lanes x nt columns of FP32 each) live
+// side by side in tensor memory. In the epilogue each of 8 warps reads one
+// lane quarter (a candidate per lane and M-tile) and every other item: it
+// turns the scores into ranking keys with the hard-data mismatches, keeps the
+// K best of its 32 x mt candidates per item, and the CTA merges the warps
+// into one K-list per item.
+#include "device_util.cuh"
+
+namespace ccw {
+
+// ---------------------------------------------------------------------------
+// tcgen05 / bulk-copy wrappers (PTX ISA: tcgen05.*, cp.async.bulk)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading (K direction) and
+// stride (M/N direction) byte offsets between 8 x 16-byte core matrices, no
+// swizzle, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = F16 or BF16, both
+// K-major, shape M x N.
+__host__ __device__ constexpr uint32_t instr_desc(bool bf16, int M, int N) {
+  return (1u << 4) | (bf16 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One 32-bit TMEM column of this thread's lane (completion not awaited).
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+  uint32_t v;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(v) : "r"(taddr));
+  return v;
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+constexpr int kTcThreads = 256;   // 8 warps: TMEM lane quarter w % 4, item parity w / 4
+constexpr int kTcMaxMt = 4;
+
+struct TcSmem {
+  int bar_off, meta_off, list_off, a_off, b_off, bytes;
+};
+
+__host__ __device__ inline TcSmem tc_smem(int nch, int a_nq, int ksteps, int nt, int K) {
+  TcSmem L;
+  int off = 0;
+  L.bar_off = off;
+  off += 128;
+  L.meta_off = off;               // per item: known, const, n_hd, active
+  off += ((nt * 16 + 127) / 128) * 128;
+  L.list_off = off;               // [8 warps][nt][K] best keys of each warp
+  off += ((8 * nt * K * 8 + 127) / 128) * 128;
+  L.a_off = off;
+  off += nch * a_nq * 128;
+  L.b_off = off;
+  off += ksteps * 32 * nt;
+  L.bytes = off + 128;   // slack for aligning the dynamic shared memory base
+  return L;
+}
+
+int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K) {
+  return tc_smem(nch, a_nq, ksteps, nt, K).bytes;
+}
+
+enum { kTcBarA = 0, kTcBarB = 1, kTcBarMma = 2 };
+
+template <int MODE, bool BF16>
+__global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ WaveArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const TiDev& t = a.ti;
+  const int nt = a.nt, K = a.K, nch = t.nch;
+  const TcSmem L = tc_smem(nch, a.a_nq, a.ksteps, nt, K);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.bar_off + 64);
+  int* flag = reinterpret_cast<int*>(smem + L.bar_off + 72);
+  int4* meta = reinterpret_cast<int4*>(smem + L.meta_off);
+  uint64_t* lists = reinterpret_cast<uint64_t*>(smem + L.list_off);
+  unsigned char* As = smem + L.a_off;
+  unsigned char* Bs = smem + L.b_off;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quarter = warp & 3, parity = warp >> 2;
+  const int mg = blockIdx.x, ntile = blockIdx.y;
+  const int64_t L_start = (int64_t)mg * a.mt * 128;
+  const int n_mt = min(a.mt, a.mtiles - mg * a.mt);
+  const int Kp = (int)((int64_t)K < t.P ? K : t.P);
+  const uint32_t a_bytes = (uint32_t)a.a_nq * 128u;
+  const uint32_t b_bytes = (uint32_t)a.ksteps * 32u * (uint32_t)nt;
+
+  // ---- barriers and the (static) A region --------------------------------
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
+    fence_mbar_init();
+    flag[0] = 0;
+    mbar_arrive_expect_tx(&bar[kTcBarA], (uint32_t)nch * a_bytes);
+    const unsigned char* z8 = reinterpret_cast<const unsigned char*>(a.z8);
+    for (int ch = 0; ch < nch; ++ch) {
+      const unsigned char* src =
+          z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + L_start / 8) * 128;
+      bulk_g2s(As + (int64_t)ch * a_bytes, src, a_bytes, &bar[kTcBarA]);
+    }
+  }
+  pdl_trigger();
+  pdl_wait();   // event records and weights of this step are complete
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar[kTcBarB], b_bytes);
+    bulk_g2s(Bs, reinterpret_cast<const unsigned char*>(a.bmat) + (int64_t)ntile * b_bytes,
+             b_bytes, &bar[kTcBarB]);
+  }
+  for (int i = tid; i < nt; i += kTcThreads) {
+    const int item = ntile * nt + i;
+    int4 m = make_int4(0, 0, 0, 0);
+    if (item < a.n_items) {
+      const int* em = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+      m.x = em[kEvKnown];
+      m.y = em[kEvConst];
+      m.z = em[kEvNHd];
+      m.w = (MODE == kModeMap) ? 1 : (m.x > 0);
+    }
+    meta[i] = m;
+  }
+  unsigned long long* work = (MODE == kModeSim) ? a.call->work : a.work;
+  if (work && mg == 0 && MODE != kModeMap) {
+    // profiling: candidate evaluations and algorithmic multiply-adds (data
+    // cells of the template times channels) of every item, counted once
+    for (int i = tid; i < nt; i += kTcThreads) {
+      const int item = ntile * nt + i;
+      if (item >= a.n_items) continue;
+      const int* em = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+      if (em[kEvKnown] <= 0) continue;
+      atomicAdd(&work[0], (unsigned long long)t.P);
+      atomicAdd(&work[1], (unsigned long long)t.P * em[kEvMaskCells] * nch);
+    }
+  }
+  // TMEM: one nt-column accumulator per M-tile
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(a.mt * nt)) ncols <<= 1;
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // ---- MMAs of every M-tile, one commit ------------------------------------
+  if (tid == 0) {
+    if (!mbar_wait_bounded(&bar[kTcBarA], 0u) || !mbar_wait_bounded(&bar[kTcBarB], 0u)) {
+      flag[0] = 1;
+    } else {
+      tc_fence_after();
+      const uint32_t idesc = instr_desc(BF16, 128, nt);
+      const int k16n = a.ks / 16;
+      const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+      for (int j = 0; j < n_mt; ++j) {
+        const uint32_t d = tmem + (uint32_t)(j * nt);
+        for (int k = 0; k < a.ksteps; ++k) {
+          const int k16 = k % k16n;
+          const int rc = k / k16n;          // ch * rows + row
+          const int row = rc % t.rows, ch = rc / t.rows;
+          const uint32_t q = (uint32_t)((128 * j + row * a.px8) / 8 + 2 * k16);
+          const uint64_t ad = smem_desc(a_base + (uint32_t)ch * a_bytes + q * 128u, 128u, 128u);
+          const uint64_t bd = smem_desc(b_base + (uint32_t)k * 32u * (uint32_t)nt, 128u, 256u);
+          mma_f16(d, ad, bd, idesc, k > 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(&bar[kTcBarMma]);
+    }
+  }
+  __syncthreads();
+  bool failed = flag[0] != 0;
+  if (!failed) {
+    if (tid == 0 && !mbar_wait_bounded(&bar[kTcBarMma], 0u)) flag[0] = 1;
+    __syncthreads();
+    failed = flag[0] != 0;
+  }
+
+  // ---- epilogue: lane = candidate of each M-tile, warps split the items ----
+  if (!failed) {
+    mbar_try_wait(&bar[kTcBarMma], 0u);
+    tc_fence_after();
+    const int m = quarter * 32 + lane;
+    int cidx[kTcMaxMt];
+    const uint8_t* tb[kTcMaxMt];
+#pragma unroll
+    for (int j = 0; j < kTcMaxMt; ++j) {
+      const int64_t Lpos = L_start + 128 * j + m;
+      const int cx = (int)(Lpos % a.px8), cy = (int)(Lpos / a.px8);
+      const bool valid = j < n_mt && cx < t.cd[0] && cy < t.cd[1];
+      cidx[j] = valid ? cx + t.cd[0] * cy : -1;
+      tb[j] = t.ti + (int64_t)t.s * cx + (int64_t)t.n[0] * ((int64_t)t.s * cy);
+    }
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+    for (int n = parity; n < nt; n += 2) {
+      const int4 mt4 = meta[n];
+      if (!mt4.w) continue;
+      uint32_t v[kTcMaxMt];
+#pragma unroll
+      for (int j = 0; j < kTcMaxMt; ++j)
+        v[j] = (j < n_mt) ? tmem_ld1(lane_base + (uint32_t)(j * nt + n)) : 0u;
+      tmem_wait_ld();
+      const int item = ntile * nt + n;
+      const int2* hdl = reinterpret_cast<const int2*>(a.ev.base + (int64_t)item * a.ev.stride +
+                                                      a.ev.hd_off);
+      uint64_t keys[kTcMaxMt];
+#pragma unroll
+      for (int j = 0; j < kTcMaxMt; ++j) {
+        keys[j] = kNoKey;
+        if (cidx[j] < 0) continue;
+        const int score = __float2int_rn(__uint_as_float(v[j])) + mt4.y;
+        int mis = 0;
+#pragma unroll 1
+        for (int k = 0; k < mt4.z; ++k) {
+          const int2 e = __ldg(hdl + k);
+          mis += (__ldg(tb[j] + e.x) != (uint8_t)(e.y & 0xFF));
+        }
+        if (MODE == kModeMap) {
+          a.map_score[(int64_t)item * t.P + cidx[j]] = mt4.x ? score : 0;
+          if (a.map_mis) a.map_mis[(int64_t)item * t.P + cidx[j]] = mt4.x ? mis : 0;
+        } else {
+          keys[j] = make_key(mis, score, cidx[j]);
+        }
+      }
+      if (MODE == kModeMap) continue;
+      // the K best of this warp's 32 x n_mt candidates
+      uint64_t* lst = lists + ((int64_t)warp * nt + n) * K;
+      uint64_t prev = 0;
+#pragma unroll 1
+      for (int r = 0; r < Kp; ++r) {
+        uint64_t best = kNoKey;
+#pragma unroll
+        for (int j = 0; j < kTcMaxMt; ++j)
+          if ((r == 0 || keys[j] > prev) && keys[j] < best) best = keys[j];
+        best = warp_min_u64(best);
+        if (lane == 0) lst[r] = best;
+        prev = best;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (!failed && MODE != kModeMap) {
+    // merge the lists of the 4 warps that saw each item into the CTA's list
+    for (int n = warp; n < nt; n += 8) {
+      if (!meta[n].w) continue;
+      const int item = ntile * nt + n;
+      const int p = n & 1;   // the warps of parity p handled item n
+      unsigned long long* part = a.part + ((int64_t)item * a.n_parts + mg) * K;
+      uint64_t prev = 0;
+      for (int r = 0; r < Kp; ++r) {
+        uint64_t best = kNoKey;
+        for (int e = lane; e < 4 * Kp; e += 32) {
+          const int w = 4 * p + e / Kp;
+          const uint64_t val = lists[((int64_t)w * nt + n) * K + (e % Kp)];
+          if ((r == 0 || val > prev) && val < best) best = val;
+        }
+        best = warp_min_u64(best);
+        if (lane == 0) part[r] = best;
+        prev = best;
+      }
+    }
+  }
+  if (failed && tid == 0) {
+    atomicOr(a.status, kStatusTimeout);
+    // let the copies and MMAs in flight finish before the CTA exits
+    mbar_wait_bounded(&bar[kTcBarA], 0u);
+    mbar_wait_bounded(&bar[kTcBarB], 0u);
+    mbar_wait_bounded(&bar[kTcBarMma], 0u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+template <int MODE, bool BF16>
+static cudaError_t launch_t(const WaveArgs& a, int smem, bool pdl, cudaStream_t st) {
+  auto fn = k_ccf_tc<MODE, BF16>;
+  static int configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  dim3 grid(a.n_mgroups, (a.n_items + a.nt - 1) / a.nt);
+  return launch_pdl(fn, grid, dim3(kTcThreads), smem, st, pdl, a);
+}
+
+cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st) {
+  const bool bf = a.precision == 2;
+  if (mode == kModeSim)
+    return bf ? launch_t<kModeSim, true>(a, smem, pdl, st) : launch_t<kModeSim, false>(a, smem, pdl, st);
+  if (mode == kModeSearch)
+    return bf ? launch_t<kModeSearch, true>(a, smem, pdl, st)
+              : launch_t<kModeSearch, false>(a, smem, pdl, st);
+  return bf ? launch_t<kModeMap, true>(a, smem, pdl, st) : launch_t<kModeMap, false>(a, smem, pdl, st);
+}
+
+}  // namespace ccw
