@@ -159,6 +159,31 @@ int ccw_simulate(const ccw_ti* ti, const ccw_params* params, const int32_t* hd_c
                  const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed, uint8_t* out_dev,
                  int32_t* patch_log_dev, void* stream);
 
+/* One grid size of a batch simulated by ccw_simulate_groups. */
+typedef struct {
+  int32_t grid[3];              /* grid dims {nx, ny, nz}; nz = 1 in 2D */
+  int32_t n_real;               /* realizations of this size (>= 1) */
+  int32_t real_base;            /* id of the first one (Philox counter word 0);
+                                   give groups disjoint id ranges */
+  const int32_t* hd_cells_dev;  /* int32 [n_hd][ndim] hard-data cells, or NULL */
+  const uint8_t* hd_vals_dev;   /* uint8 [n_hd] hard-data codes, or NULL */
+  int32_t n_hd;
+  uint8_t* out_dev;             /* uint8 [n_real][grid] realizations */
+  int32_t* patch_log_dev;       /* int32 [n_real][n_patches][4 + topk], or NULL */
+} ccw_group;
+
+/*
+ * ccw_simulate_groups -- ccw_simulate for realizations of several grid
+ * sizes at once (each group with its own hard data, outputs and patch log).
+ * params->grid, n_real and real_base are ignored; the other fields apply to
+ * every group. The patches of every group advance together, one wavefront
+ * per step, so the groups share the kernel launches; each realization is
+ * exactly what ccw_simulate gives for it. Synchronizes `stream` once at the
+ * end. Errors as ccw_simulate.
+ */
+int ccw_simulate_groups(const ccw_ti* ti, const ccw_params* params, const ccw_group* groups,
+                        int32_t n_groups, uint64_t seed, void* stream);
+
 /*
  * ccw_ccf_search -- one batched best-match search step (Algorithm 1, lines
  * 9-12; Eq. CCW; Sec. 4.4), for B independent data events.

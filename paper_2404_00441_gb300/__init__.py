@@ -4,4 +4,5 @@ Every step of the search runs in the library's CUDA kernels; this package only
 marshals arguments (PyTorch provides device memory and streams).
 """
 from .ccw import (CCWError, TI, ccf_map, ccf_search, idwt_paste, launch_count,  # noqa: F401
-                  lattice, library_path, load, profile_enable, profile_read, simulate)
+                  lattice, library_path, load, profile_enable, profile_read, simulate,
+                  simulate_groups)

@@ -31,6 +31,12 @@ class _Params(C.Structure):
                 ("reserved", C.c_int32 * 4)]
 
 
+class _Group(C.Structure):
+    _fields_ = [("grid", C.c_int32 * 3), ("n_real", C.c_int32), ("real_base", C.c_int32),
+                ("hd_cells_dev", C.c_void_p), ("hd_vals_dev", C.c_void_p), ("n_hd", C.c_int32),
+                ("out_dev", C.c_void_p), ("patch_log_dev", C.c_void_p)]
+
+
 class _Desc(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("n_facies", C.c_int32), ("level", C.c_int32),
                 ("scale", C.c_int32), ("templ", C.c_int32), ("overlap", C.c_int32),
@@ -58,6 +64,7 @@ def load():
     lib.ccw_ti_free.restype = None
     lib.ccw_ti_export.argtypes = [P, i32, P, P]
     lib.ccw_simulate.argtypes = [P, C.POINTER(_Params), P, P, i32, u64, P, P, P]
+    lib.ccw_simulate_groups.argtypes = [P, C.POINTER(_Params), C.POINTER(_Group), i32, u64, P]
     lib.ccw_ccf_search.argtypes = [P, i32, P, P, i32, i32, u64, P, P, P, P, P, P]
     lib.ccw_ccf_map.argtypes = [P, i32, P, P, i32, P, P, P]
     lib.ccw_idwt_paste.argtypes = [P, i32, P, P, P, P, P]
@@ -199,6 +206,50 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
                             _ptr(hd_vals) if n_hd else None, n_hd, seed & (2 ** 64 - 1),
                             _ptr(out), _ptr(log) if want_log else None, _stream(stream)))
     return out, (log if want_log else None)
+
+
+def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0, precision=0,
+                    want_log=False, stream=None):
+    """``ccw_simulate_groups``: several grid sizes in one batch. ``groups`` is
+    a list of dicts with keys grid, n_real, real_base and optionally hd_cells,
+    hd_vals (CUDA tensors). Returns a list of (realizations, log or None)."""
+    lib = load()
+    p = _Params()
+    p.ndim = ti.ndim
+    p.grid = _i3([1] * ti.ndim)
+    p.topk = topk
+    p.n_real = 1
+    p.path_random = path_random
+    p.score_mode = score_mode
+    p.precision = precision
+    arr = (_Group * len(groups))()
+    results = []
+    keep = []
+    for i, g in enumerate(groups):
+        grid = tuple(g["grid"])
+        n_real = int(g["n_real"])
+        out = torch.empty((n_real,) + grid[::-1], dtype=torch.uint8, device="cuda")
+        npch, _ = lattice(grid, ti.templ, ti.overlap)
+        n_patches = 1
+        for v in npch:
+            n_patches *= v
+        log = (torch.empty((n_real, n_patches, 4 + topk), dtype=torch.int32, device="cuda")
+               if want_log else None)
+        hc, hv = g.get("hd_cells"), g.get("hd_vals")
+        n_hd = 0 if hv is None else int(hv.numel())
+        arr[i].grid = _i3(grid)
+        arr[i].n_real = n_real
+        arr[i].real_base = int(g.get("real_base", 0))
+        arr[i].hd_cells_dev = _ptr(hc) if n_hd else None
+        arr[i].hd_vals_dev = _ptr(hv) if n_hd else None
+        arr[i].n_hd = n_hd
+        arr[i].out_dev = _ptr(out)
+        arr[i].patch_log_dev = _ptr(log) if want_log else None
+        keep.append((hc, hv))
+        results.append((out, log))
+    _check(lib.ccw_simulate_groups(ti.handle, C.byref(p), arr, len(groups), seed & (2 ** 64 - 1),
+                                   _stream(stream)))
+    return results
 
 
 def ccf_search(ti: TI, de: torch.Tensor, hd=None, k=1, score_mode=0, seed=0, ctr=None,

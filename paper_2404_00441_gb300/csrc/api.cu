@@ -114,20 +114,26 @@ void event_layout(int nch, int rows, int TjP, int hd_cap, EvDev& ev) {
 // Simulation plan: workspace and the captured wave graph of one simulation
 // shape, reused while the shape does not change.
 // ---------------------------------------------------------------------------
-struct SimPlan {
-  int grid[3];
-  int n_real, K, score_mode, precision;
+struct GroupPlan {
+  int grid[3], n_real;
   int g[3], np[3], gp[3];
   int64_t gp_vol, g_vol, n_patches;
-  int n_waves, max_items;
-  std::vector<int64_t> wave_off;
   void* sg = nullptr;
   void* overlay = nullptr;
+};
+
+struct SimPlan {
+  int n_groups = 0;
+  std::vector<GroupPlan> groups;
+  int K, score_mode, precision;
+  int n_waves, max_items;
+  std::vector<int64_t> wave_off;
   void* items = nullptr;
   void* ev = nullptr;
   void* part = nullptr;
   void* bmat = nullptr;
   CallDev* call = nullptr;
+  SimGroup* dgroups = nullptr;
   EvDev evl;
   void* cp = nullptr;   // CcfPlan (defined with the kernels' host helpers)
   cudaStream_t cap = nullptr;
@@ -141,13 +147,16 @@ struct SimPlan {
       cudaEventDestroy(pr.second);
     }
     if (cap) cudaStreamDestroy(cap);
-    cudaFree(sg);
-    cudaFree(overlay);
+    for (auto& g : groups) {
+      cudaFree(g.sg);
+      cudaFree(g.overlay);
+    }
     cudaFree(items);
     cudaFree(ev);
     cudaFree(part);
     cudaFree(bmat);
     cudaFree(call);
+    cudaFree(dgroups);
     release_cp();
   }
   void release_cp();
@@ -872,50 +881,74 @@ int ccw_idwt_paste(const ccw_ti* t, int32_t B, const int32_t* pick_dev,
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// ccw_simulate
+// ccw_simulate / ccw_simulate_groups
 // ---------------------------------------------------------------------------
 namespace {
 
-int build_plan(ccw_ti* t, const ccw_params* p, SimPlan*& out) {
+bool plan_matches(const SimPlan* pl, const ccw_params* p, const ccw_group* groups, int n_groups) {
+  if (!pl || pl->n_groups != n_groups || pl->K != p->topk || pl->score_mode != p->score_mode ||
+      pl->precision != p->precision)
+    return false;
+  for (int i = 0; i < n_groups; ++i) {
+    const GroupPlan& g = pl->groups[i];
+    if (g.n_real != groups[i].n_real) return false;
+    for (int a = 0; a < 3; ++a)
+      if (g.grid[a] != groups[i].grid[a]) return false;
+  }
+  return true;
+}
+
+int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_groups,
+               SimPlan*& out) {
   SimPlan* pl = new SimPlan();
   const int d = t->ndim;
   const int T = t->T, S = t->T - t->O;
-  for (int a = 0; a < 3; ++a) {
-    pl->grid[a] = p->grid[a];
-    pl->g[a] = p->grid[a];
-    if (a < d) {
-      const int extra = pl->g[a] > T ? pl->g[a] - T : 0;
-      pl->np[a] = 1 + (extra + S - 1) / S;
-      pl->gp[a] = T + (pl->np[a] - 1) * S;
-    } else {
-      pl->np[a] = 1;
-      pl->gp[a] = 1;
-    }
-  }
-  pl->n_real = p->n_real;
+  pl->n_groups = n_groups;
+  pl->groups.resize(n_groups);
   pl->K = p->topk;
   pl->score_mode = p->score_mode;
   pl->precision = p->precision;
-  pl->n_patches = (int64_t)pl->np[0] * pl->np[1] * pl->np[2];
-  pl->gp_vol = (int64_t)pl->gp[0] * pl->gp[1] * pl->gp[2];
-  pl->g_vol = (int64_t)pl->g[0] * pl->g[1] * pl->g[2];
-  // wavefront schedule: wave(p) = ix + 2 iy + 4 iz over the lattice index
-  pl->n_waves = (pl->np[0] - 1) + 2 * (pl->np[1] - 1) + 4 * (pl->np[2] - 1) + 1;
-  std::vector<std::vector<int>> wave_patches(pl->n_waves);
-  for (int64_t pp = 0; pp < pl->n_patches; ++pp) {
-    const int ix = (int)(pp % pl->np[0]), iy = (int)((pp / pl->np[0]) % pl->np[1]),
-              iz = (int)(pp / ((int64_t)pl->np[0] * pl->np[1]));
-    wave_patches[ix + 2 * iy + 4 * iz].push_back((int)pp);
+  pl->n_waves = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    GroupPlan& g = pl->groups[i];
+    g.n_real = groups[i].n_real;
+    for (int a = 0; a < 3; ++a) {
+      g.grid[a] = groups[i].grid[a];
+      g.g[a] = groups[i].grid[a];
+      if (a < d) {
+        const int extra = g.g[a] > T ? g.g[a] - T : 0;
+        g.np[a] = 1 + (extra + S - 1) / S;
+        g.gp[a] = T + (g.np[a] - 1) * S;
+      } else {
+        g.np[a] = 1;
+        g.gp[a] = 1;
+      }
+    }
+    g.n_patches = (int64_t)g.np[0] * g.np[1] * g.np[2];
+    g.gp_vol = (int64_t)g.gp[0] * g.gp[1] * g.gp[2];
+    g.g_vol = (int64_t)g.g[0] * g.g[1] * g.g[2];
+    pl->n_waves = std::max(pl->n_waves,
+                           (g.np[0] - 1) + 2 * (g.np[1] - 1) + 4 * (g.np[2] - 1) + 1);
   }
-  std::vector<int2> items;
-  items.reserve((size_t)pl->n_patches * pl->n_real);
+  // wavefront schedule: wave(p) = ix + 2 iy + 4 iz over the lattice index of
+  // every group; the items of one wave of all groups share the launches
+  std::vector<std::vector<int4>> waves(pl->n_waves);
+  for (int i = 0; i < n_groups; ++i) {
+    const GroupPlan& g = pl->groups[i];
+    for (int r = 0; r < g.n_real; ++r)
+      for (int64_t pp = 0; pp < g.n_patches; ++pp) {
+        const int ix = (int)(pp % g.np[0]), iy = (int)((pp / g.np[0]) % g.np[1]),
+                  iz = (int)(pp / ((int64_t)g.np[0] * g.np[1]));
+        waves[ix + 2 * iy + 4 * iz].push_back(make_int4(i, r, (int)pp, 0));
+      }
+  }
+  std::vector<int4> items;
   pl->wave_off.assign(pl->n_waves + 1, 0);
   pl->max_items = 0;
   for (int w = 0; w < pl->n_waves; ++w) {
     pl->wave_off[w] = (int64_t)items.size();
-    for (int r = 0; r < pl->n_real; ++r)
-      for (int pp : wave_patches[w]) items.push_back(make_int2(r, pp));
-    pl->max_items = std::max<int>(pl->max_items, (int)(items.size() - pl->wave_off[w]));
+    items.insert(items.end(), waves[w].begin(), waves[w].end());
+    pl->max_items = std::max<int>(pl->max_items, (int)waves[w].size());
   }
   pl->wave_off[pl->n_waves] = (int64_t)items.size();
   const int nch = p->score_mode == 0 ? t->F - 1 : 1;
@@ -923,19 +956,25 @@ int build_plan(ccw_ti* t, const ccw_params* p, SimPlan*& out) {
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
   plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp);
-  cudaError_t e;
-  if ((e = cudaMalloc(&pl->sg, (size_t)pl->gp_vol * pl->n_real)) != cudaSuccess ||
-      (e = cudaMalloc(&pl->overlay, (size_t)align_up(pl->g_vol, 4))) != cudaSuccess ||
-      (e = cudaMalloc(&pl->items, sizeof(int2) * items.size())) != cudaSuccess ||
+  cudaError_t e = cudaSuccess;
+  for (auto& g : pl->groups) {
+    if ((e = cudaMalloc(&g.sg, (size_t)g.gp_vol * g.n_real)) != cudaSuccess ||
+        (e = cudaMalloc(&g.overlay, (size_t)align_up(g.g_vol, 4))) != cudaSuccess)
+      break;
+  }
+  if (e != cudaSuccess ||
+      (e = cudaMalloc(&pl->items, sizeof(int4) * std::max<size_t>(items.size(), 1))) !=
+          cudaSuccess ||
       (e = cudaMalloc(&pl->ev, (size_t)cp->ev_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&pl->part, (size_t)cp->part_bytes)) != cudaSuccess ||
       (cp->bmat_bytes && (e = cudaMalloc(&pl->bmat, (size_t)cp->bmat_bytes)) != cudaSuccess) ||
-      (e = cudaMalloc((void**)&pl->call, sizeof(CallDev))) != cudaSuccess) {
+      (e = cudaMalloc((void**)&pl->call, sizeof(CallDev))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&pl->dgroups, sizeof(SimGroup) * n_groups)) != cudaSuccess) {
     delete pl;
     return fail(CCW_ENOMEM, "simulation workspace: %s", cudaGetErrorString(e));
   }
   pl->evl.base = (unsigned char*)pl->ev;
-  if ((e = cudaMemcpy(pl->items, items.data(), sizeof(int2) * items.size(),
+  if ((e = cudaMemcpy(pl->items, items.data(), sizeof(int4) * items.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     delete pl;
@@ -951,16 +990,8 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
   WaveArgs a;
   fill_ti(t, pl->score_mode, a);
   a.ev = pl->evl;
-  a.sim.sg = (uint8_t*)pl->sg;
-  a.sim.overlay = (const uint8_t*)pl->overlay;
-  for (int i = 0; i < 3; ++i) {
-    a.sim.G[i] = pl->g[i];
-    a.sim.Gp[i] = pl->gp[i];
-    a.sim.np[i] = pl->np[i];
-  }
-  a.sim.S = t->T - t->O;
-  a.sim.gp_vol = pl->gp_vol;
-  a.sim.n_patches = pl->n_patches;
+  a.groups = pl->dgroups;
+  a.S = t->T - t->O;
   a.call = pl->call;
   a.K = pl->K;
   a.part = (unsigned long long*)pl->part;
@@ -969,7 +1000,7 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
   for (int w = 0; w < pl->n_waves; ++w) {
     for (int64_t i0 = pl->wave_off[w]; i0 < pl->wave_off[w + 1]; i0 += 65535) {
       WaveArgs c = a;
-      c.items = (const int2*)pl->items + i0;
+      c.items = (const int4*)pl->items + i0;
       c.n_items = (int)std::min<int64_t>(65535, pl->wave_off[w + 1] - i0);
       apply_ccf(t, cp, pl->bmat, c);
       cudaError_t e = launch_events(kModeSim, c, true, st);
@@ -1011,40 +1042,39 @@ int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
   return CCW_OK;
 }
 
-}  // namespace
-
-extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t* hd_cells_dev,
-                            const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed,
-                            uint8_t* out_dev, int32_t* patch_log_dev, void* stream) {
-  if (!tc || !p || !out_dev) return fail(CCW_EINVAL, "NULL argument");
-  ccw_ti* t = const_cast<ccw_ti*>(tc);
+int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_groups,
+                    uint64_t seed, void* stream) {
   const int d = t->ndim;
   if (p->ndim != d) return fail(CCW_EINVAL, "params ndim %d != TI ndim %d", p->ndim, d);
   if (p->topk < 1 || p->topk > CCW_MAX_TOPK)
     return fail(CCW_EINVAL, "topk must be in [1, %d]", CCW_MAX_TOPK);
-  if (p->n_real < 1) return fail(CCW_EINVAL, "n_real must be >= 1");
-  if (p->real_base < 0) return fail(CCW_EINVAL, "real_base must be >= 0");
   if (p->score_mode != 0 && p->score_mode != 1) return fail(CCW_EINVAL, "bad score_mode");
   if (int rc = check_precision(t, p->precision, p->score_mode)) return rc;
   if (p->path_random != 0 && p->path_random != 1) return fail(CCW_EINVAL, "bad path_random");
   for (int i = 0; i < 4; ++i)
     if (p->reserved[i]) return fail(CCW_EINVAL, "reserved fields must be 0");
-  if (n_hd < 0 || (n_hd > 0 && (!hd_cells_dev || !hd_vals_dev)))
-    return fail(CCW_EINVAL, "bad hard data");
   if (int rc = check_score_bound(t, p->score_mode)) return rc;
-  for (int a = 0; a < 3; ++a)
-    if (p->grid[a] <= 0 || (a >= d && p->grid[a] != 1)) return fail(CCW_EINVAL, "bad grid dims");
+  if (n_groups < 1 || !groups) return fail(CCW_EINVAL, "at least one grid group is needed");
+  for (int i = 0; i < n_groups; ++i) {
+    const ccw_group& g = groups[i];
+    if (g.n_real < 1) return fail(CCW_EINVAL, "group %d: n_real must be >= 1", i);
+    if (g.real_base < 0) return fail(CCW_EINVAL, "group %d: real_base must be >= 0", i);
+    if (!g.out_dev) return fail(CCW_EINVAL, "group %d: out_dev is NULL", i);
+    if (g.n_hd < 0 || (g.n_hd > 0 && (!g.hd_cells_dev || !g.hd_vals_dev)))
+      return fail(CCW_EINVAL, "group %d: bad hard data", i);
+    for (int a = 0; a < 3; ++a)
+      if (g.grid[a] <= 0 || (a >= d && g.grid[a] != 1))
+        return fail(CCW_EINVAL, "group %d: bad grid dims", i);
+  }
 
   std::lock_guard<std::mutex> lock(t->mu);
   cudaStream_t st = (cudaStream_t)stream;
   SimPlan* pl = t->plan;
-  if (!pl || pl->grid[0] != p->grid[0] || pl->grid[1] != p->grid[1] ||
-      pl->grid[2] != p->grid[2] || pl->n_real != p->n_real || pl->K != p->topk ||
-      pl->score_mode != p->score_mode || pl->precision != p->precision) {
+  if (!plan_matches(pl, p, groups, n_groups)) {
     cudaDeviceSynchronize();
     delete t->plan;
     t->plan = nullptr;
-    if (int rc = build_plan(t, p, pl)) return rc;
+    if (int rc = build_plan(t, p, groups, n_groups, pl)) return rc;
     t->plan = pl;
   }
   bool prof;
@@ -1056,28 +1086,48 @@ extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t
   }
   CallDev call;
   call.seed = seed;
-  call.real_base = p->real_base;
   call.path_random = p->path_random;
-  call.log = patch_log_dev;
   call.log_stride = 4 + p->topk;
   call.work = work;
+  std::vector<SimGroup> hg(n_groups);
+  for (int i = 0; i < n_groups; ++i) {
+    const GroupPlan& g = pl->groups[i];
+    SimGroup& s = hg[i];
+    s.sg = (uint8_t*)g.sg;
+    s.overlay = (const uint8_t*)g.overlay;
+    for (int a = 0; a < 3; ++a) {
+      s.G[a] = g.g[a];
+      s.Gp[a] = g.gp[a];
+      s.np[a] = g.np[a];
+    }
+    s.gp_vol = g.gp_vol;
+    s.n_patches = g.n_patches;
+    s.real_base = groups[i].real_base;
+    s.log = groups[i].patch_log_dev;
+  }
   cudaError_t e;
   if ((e = cudaMemcpyAsync(pl->call, &call, sizeof(call), cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
-      (e = cudaMemsetAsync(pl->sg, 0xFF, (size_t)pl->gp_vol * pl->n_real, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(pl->overlay, 0xFF, (size_t)align_up(pl->g_vol, 4), st)) !=
-          cudaSuccess ||
+      (e = cudaMemcpyAsync(pl->dgroups, hg.data(), sizeof(SimGroup) * n_groups,
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(t->d_status, 0, sizeof(int), st)) != cudaSuccess)
     return cuda_fail(e, "simulation setup");
-  if ((e = launch_hd_overlay(hd_cells_dev, hd_vals_dev, n_hd, d, pl->g, t->F,
-                             (uint8_t*)pl->overlay, t->d_status, st)) != cudaSuccess)
-    return cuda_fail(e, "hard-data kernel");
-  if (n_hd > 0) ++g_launches;
-  if (patch_log_dev &&
-      (e = cudaMemsetAsync(patch_log_dev, 0xFF,
-                           sizeof(int32_t) * (size_t)pl->n_real * pl->n_patches * (4 + p->topk),
-                           st)) != cudaSuccess)
-    return cuda_fail(e, "log clear");
+  for (int i = 0; i < n_groups; ++i) {
+    const GroupPlan& g = pl->groups[i];
+    const ccw_group& u = groups[i];
+    if ((e = cudaMemsetAsync(g.sg, 0xFF, (size_t)g.gp_vol * g.n_real, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(g.overlay, 0xFF, (size_t)align_up(g.g_vol, 4), st)) != cudaSuccess)
+      return cuda_fail(e, "simulation setup");
+    if ((e = launch_hd_overlay(u.hd_cells_dev, u.hd_vals_dev, u.n_hd, d, g.g, t->F,
+                               (uint8_t*)g.overlay, t->d_status, st)) != cudaSuccess)
+      return cuda_fail(e, "hard-data kernel");
+    if (u.n_hd > 0) ++g_launches;
+    if (u.patch_log_dev &&
+        (e = cudaMemsetAsync(u.patch_log_dev, 0xFF,
+                             sizeof(int32_t) * (size_t)g.n_real * g.n_patches * (4 + p->topk),
+                             st)) != cudaSuccess)
+      return cuda_fail(e, "log clear");
+  }
   const int gi = prof ? 1 : 0;
   if (!pl->exec[gi])
     if (int rc = capture_waves(t, pl, prof)) return rc;
@@ -1086,10 +1136,14 @@ extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t
   for (int w = 0; w < pl->n_waves; ++w)
     wave_launches += 3 * ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
   g_launches += wave_launches;
-  if ((e = launch_crop_out((const uint8_t*)pl->sg, pl->gp_vol, pl->gp, out_dev, pl->g, d,
-                           pl->n_real, p->path_random, seed, p->real_base, st)) != cudaSuccess)
-    return cuda_fail(e, "crop kernel");
-  ++g_launches;
+  for (int i = 0; i < n_groups; ++i) {
+    const GroupPlan& g = pl->groups[i];
+    if ((e = launch_crop_out((const uint8_t*)g.sg, g.gp_vol, g.gp, groups[i].out_dev, g.g, d,
+                             g.n_real, p->path_random, seed, groups[i].real_base, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "crop kernel");
+    ++g_launches;
+  }
   int status = 0;
   if ((e = cudaMemcpyAsync(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
           cudaSuccess ||
@@ -1111,4 +1165,31 @@ extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t
     return fail(CCW_EINVAL, "more than %d hard data in one template window", kMaxHd);
   if (status & kStatusTimeout) return fail(CCW_ETIMEOUT, "a bounded device wait gave up");
   return CCW_OK;
+}
+
+}  // namespace
+
+extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t* hd_cells_dev,
+                            const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed,
+                            uint8_t* out_dev, int32_t* patch_log_dev, void* stream) {
+  if (!tc || !p || !out_dev) return fail(CCW_EINVAL, "NULL argument");
+  if (p->n_real < 1) return fail(CCW_EINVAL, "n_real must be >= 1");
+  if (p->real_base < 0) return fail(CCW_EINVAL, "real_base must be >= 0");
+  ccw_group g;
+  for (int a = 0; a < 3; ++a) g.grid[a] = p->grid[a];
+  g.n_real = p->n_real;
+  g.real_base = p->real_base;
+  g.hd_cells_dev = hd_cells_dev;
+  g.hd_vals_dev = hd_vals_dev;
+  g.n_hd = n_hd;
+  g.out_dev = out_dev;
+  g.patch_log_dev = patch_log_dev;
+  return simulate_groups(const_cast<ccw_ti*>(tc), p, &g, 1, seed, stream);
+}
+
+extern "C" int ccw_simulate_groups(const ccw_ti* tc, const ccw_params* p,
+                                   const ccw_group* groups, int32_t n_groups, uint64_t seed,
+                                   void* stream) {
+  if (!tc || !p) return fail(CCW_EINVAL, "NULL argument");
+  return simulate_groups(const_cast<ccw_ti*>(tc), p, groups, n_groups, seed, stream);
 }

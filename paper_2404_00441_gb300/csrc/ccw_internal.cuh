@@ -124,19 +124,21 @@ struct EvDev {
   int mask_off, hd_off, w_off, hd_cap;
 };
 
-struct SimDev {
+// One grid size of a simulation batch (device array, rewritten every call).
+struct SimGroup {
   uint8_t* sg;             // [n_real][Gp] padded grids, 255 = not simulated
-  const uint8_t* overlay;  // [G] hard data, 255 = none
-  int G[3], Gp[3], np[3], S;
+  const uint8_t* overlay;  // [G] hard data of this group, 255 = none
+  int G[3], Gp[3], np[3];
   int64_t gp_vol, n_patches;
+  int real_base;           // id of the group's first realization
+  int32_t* log;            // [n_real][n_patches][log_stride] or NULL
 };
 
 // Per-call values of a simulation, read from device memory so that a
 // captured wave graph can be replayed with another seed or output.
 struct CallDev {
   uint64_t seed;
-  int real_base, path_random;
-  int32_t* log;
+  int path_random;
   int log_stride;
   unsigned long long* work;  // profiling counters [2] or NULL
 };
@@ -144,9 +146,10 @@ struct CallDev {
 struct WaveArgs {
   TiDev ti;
   EvDev ev;
-  SimDev sim;
+  const SimGroup* groups;   // simulation mode
+  int S;                    // patch stride T - OR
   const CallDev* call;      // simulation mode
-  const int2* items;        // simulation: (realization slot, patch)
+  const int4* items;        // simulation: (group, realization slot, patch, 0)
   int n_items;
   int nb;                   // items per CTA in the CCF kernel
   // explicit data events (search / map)

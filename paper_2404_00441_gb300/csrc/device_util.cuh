@@ -248,36 +248,46 @@ __device__ void paste_hard_data(const PasteGeom& p, const int2* hdl, int n_hd, i
 // Position of a simulation item (realization slot, patch) in its padded
 // grid, with the path mirroring of its realization (Algorithm 1, line 3).
 struct ItemPos {
-  int slot, patch;
+  int group, slot, patch;
   uint32_t r, p;
   int o[3], off[3];
+  uint8_t* sg;              // this realization's padded grid
+  const uint8_t* overlay;   // the group's hard data
+  int G[3], Gp[3];
+  int32_t* log;             // this patch's log record, or NULL
 };
 
 template <int D>
 __device__ __forceinline__ ItemPos decode_sim_item(const WaveArgs& a, int item) {
   ItemPos it;
-  const int2 v = a.items[item];
-  it.slot = v.x;
-  it.patch = v.y;
+  const int4 v = a.items[item];
+  it.group = v.x;
+  it.slot = v.y;
+  it.patch = v.z;
+  const SimGroup& s = a.groups[it.group];
   const CallDev* c = a.call;
-  it.r = (uint32_t)(c->real_base + it.slot);
+  it.r = (uint32_t)(s.real_base + it.slot);
   it.p = (uint32_t)it.patch;
   const uint32_t flips =
       c->path_random ? (draw_word(c->seed, it.r, 0u, 1u) & ((1u << D) - 1u)) : 0u;
-  const SimDev& s = a.sim;
-  const int ip[3] = {it.patch % s.np[0], (it.patch / s.np[0]) % s.np[1],
-                     it.patch / (s.np[0] * s.np[1])};
+  const int np0 = s.np[0], np1 = s.np[1];
+  const int ip[3] = {it.patch % np0, (it.patch / np0) % np1, it.patch / (np0 * np1)};
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
+    it.G[ax] = s.G[ax];
+    it.Gp[ax] = s.Gp[ax];
     const bool f = (flips >> ax) & 1u;
     if (ax < D) {
-      it.o[ax] = f ? s.Gp[ax] - a.ti.T - s.S * ip[ax] : s.S * ip[ax];
-      it.off[ax] = f ? s.Gp[ax] - s.G[ax] : 0;
+      it.o[ax] = f ? it.Gp[ax] - a.ti.T - a.S * ip[ax] : a.S * ip[ax];
+      it.off[ax] = f ? it.Gp[ax] - it.G[ax] : 0;
     } else {
       it.o[ax] = 0;
       it.off[ax] = 0;
     }
   }
+  it.sg = s.sg + (int64_t)it.slot * s.gp_vol;
+  it.overlay = s.overlay;
+  it.log = s.log ? s.log + ((int64_t)it.slot * s.n_patches + it.patch) * c->log_stride : nullptr;
   return it;
 }
 
@@ -290,10 +300,10 @@ __device__ __forceinline__ PasteGeom sim_paste_geom(const WaveArgs& a, const Ite
   g.cd0 = a.ti.cd[0];
   g.cd1 = a.ti.cd[1];
   g.Tj = a.ti.Tj;
-  g.grid = a.sim.sg + (int64_t)it.slot * a.sim.gp_vol;
+  g.grid = it.sg;
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    g.g[ax] = a.sim.Gp[ax];
+    g.g[ax] = it.Gp[ax];
     g.o[ax] = it.o[ax];
   }
   return g;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   const uint8_t* hdw = nullptr;
   if (MODE == kModeSim) {
     it = decode_sim_item<D>(a, item);
-    sg = a.sim.sg + (int64_t)it.slot * a.sim.gp_vol;
+    sg = it.sg;
   } else {
     const int64_t tv = (D == 3) ? (int64_t)T * T * T : (int64_t)T * T;
     de = a.de + (int64_t)item * tv;
@@ -67,9 +67,9 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     if (MODE == kModeSim) {
       const int gx = it.o[0] + qx, gy = it.o[1] + qy, gz = it.o[2] + qz;
       const int hx = gx - it.off[0], hy = gy - it.off[1], hz = gz - it.off[2];
-      if (hx >= 0 && hy >= 0 && hz >= 0 && hx < a.sim.G[0] && hy < a.sim.G[1] && hz < a.sim.G[2])
-        h = __ldg(a.sim.overlay + hx + (int64_t)a.sim.G[0] * (hy + (int64_t)a.sim.G[1] * hz));
-      v = sg[gx + (int64_t)a.sim.Gp[0] * (gy + (int64_t)a.sim.Gp[1] * gz)];
+      if (hx >= 0 && hy >= 0 && hz >= 0 && hx < it.G[0] && hy < it.G[1] && hz < it.G[2])
+        h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
+      v = sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
       if (h != CCW_UNKNOWN) v = h;
     } else {
       const int q = qx + T * (qy + T * qz);
@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     return;
   }
   const CallDev* c = a.call;
-  if (c->log && tid < c->log_stride) {
-    int32_t* e = c->log + ((int64_t)it.slot * a.sim.n_patches + it.patch) * c->log_stride;
+  if (it.log && tid < c->log_stride) {
+    int32_t* e = it.log;
     e[tid] = (tid == 0) ? pk
                         : (tid == 3 ? (CCW_LOG_FLAG_UNIFORM | CCW_LOG_FLAG_DONE)
                                     : (tid < 3 ? 0 : -1));

@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     return;
   }
   const CallDev* c = a.call;
-  if (c->log && tid < c->log_stride) {
-    int32_t* e = c->log + ((int64_t)it.slot * a.sim.n_patches + it.patch) * c->log_stride;
+  if (it.log && tid < c->log_stride) {
+    int32_t* e = it.log;
     int val;
     if (tid == 0) val = pk;
     else if (tid == 1) val = key_score(sel);

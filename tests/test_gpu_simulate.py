@@ -137,3 +137,35 @@ def test_full_size_c2_sampled(ccw):
         pat = o.reconstruct(T, int(log[p, 0]))
         state[win] = np.where(hw != 255, hw, pat)
     assert np.array_equal(state[:grid[1], :grid[0]], out)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mixed_grid_sizes_in_one_batch(ccw, precision):
+    """Several grid sizes advance in one batch (ccw_simulate_groups); every
+    realization equals the oracle's simulation of its own grid."""
+    if precision == 0:
+        ti = synth.tube_lobe_ti_3d(60, 50, 40, seed=5)
+        F, J, T, Ov, K = 4, 1, 12, 2, 5
+        grids = [(50, 44, 30), (30, 26, 22)]
+        fields = [synth.tube_lobe_ti_3d(*g, seed=6 + i) for i, g in enumerate(grids)]
+    else:
+        ti = configs.channel_lens_ti_1000()
+        F, J, T, Ov, K = 3, 2, 64, 16, 5
+        grids = [(300, 260), (150, 120)]
+        fields = [synth.channel_lens_ti(*g, seed=6 + i, tol=0.3) for i, g in enumerate(grids)]
+    hds = [synth.sample_hard_data(f, 30, seed=9 + i) for i, f in enumerate(fields)]
+    g = ccw.TI(dev(ti), F, J, T, Ov)
+    groups = [dict(grid=grids[0], n_real=2, real_base=0, hd_cells=dev(hds[0][0]),
+                   hd_vals=dev(hds[0][1])),
+              dict(grid=grids[1], n_real=3, real_base=10, hd_cells=dev(hds[1][0]),
+                   hd_vals=dev(hds[1][1]))]
+    res = ccw.simulate_groups(g, groups, topk=K, seed=4, path_random=1, precision=precision,
+                              want_log=True)
+    o = O.OracleTI(ti, F, J)
+    for gi, (out, log) in enumerate(res):
+        out, log = out.cpu().numpy(), log.cpu().numpy()
+        for i in range(groups[gi]["n_real"]):
+            ref, rlog = o.simulate(grids[gi], T, Ov, K=K, path_random=1, hd_cells=hds[gi][0],
+                                   hd_vals=hds[gi][1], seed=4, r=groups[gi]["real_base"] + i)
+            assert np.array_equal(log[i], rlog), f"group {gi} realization {i} log"
+            assert np.array_equal(out[i], ref), f"group {gi} realization {i}"
