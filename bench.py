@@ -56,6 +56,8 @@ WORKLOAD_TEXT = {
            "data; K=5",
     "c4b": "3D 4-facies TI 180x150x120; 8 realizations 100x100x100; T24 OR6 J1; 1000 hard "
            "data; K=5",
+    "c4": "3D 4-facies TI 180x150x120; one batch of 8 realizations 200x200x100 and 8 of "
+          "100x100x100; T24 OR6 J1; 1000 hard data per grid size; K=5",
     "c5": "2D binary ribbon TI 250x250; 256 realizations 512x512; T48 OR12 J2; K=1",
 }
 
@@ -166,6 +168,8 @@ def run_reference(args, rank, world):
         return
     from workloads import configs
     w = configs.workload(args.workload)
+    if w.get("groups"):
+        w = dict(w, grid=w["groups"][0]["grid"], hd=w["groups"][0]["hd"])
     per_step = max(1.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(w, per_step / 4)
@@ -208,25 +212,43 @@ def run_ours(args, rank, world, local_rank):
     w = configs.workload(args.workload)
     ti_t = torch.from_numpy(w["ti"]).cuda()
     g = ccw.TI(ti_t, w["F"], w["J"], w["T"], w["O"])
-    hd = w["hd"]
-    hc = hv = None
-    if hd is not None:
-        hc = torch.from_numpy(hd[0]).cuda()
-        hv = torch.from_numpy(hd[1]).cuda()
-    n_real = w["n_real"]
-    grid = w["grid"]
-    precision = args.precision if args.precision is not None else (1 if len(grid) == 2 else 0)
-    base = rank * n_real             # each rank simulates its own realizations
-    out = torch.empty((n_real,) + tuple(grid)[::-1], dtype=torch.uint8, device="cuda")
+    # one or several grid sizes; each rank simulates its own realizations
+    specs = w.get("groups") or [dict(grid=w["grid"], n_real=w["n_real"], hd=w["hd"],
+                                     real_base=0)]
+    total_real = sum(s["n_real"] for s in specs)
+    groups = []
+    for s in specs:
+        hd = s["hd"]
+        groups.append(dict(
+            grid=tuple(s["grid"]), n_real=s["n_real"],
+            real_base=rank * total_real + s.get("real_base", 0),
+            hd_cells=None if hd is None else torch.from_numpy(hd[0]).cuda(),
+            hd_vals=None if hd is None else torch.from_numpy(hd[1]).cuda(),
+            hd_host=hd))
+    ndim = len(groups[0]["grid"])
+    precision = args.precision if args.precision is not None else (1 if ndim == 2 else 0)
+    cells_per_step = sum(gr["n_real"] * cells_of(gr["grid"]) for gr in groups)
+    outs = [torch.empty((gr["n_real"],) + gr["grid"][::-1], dtype=torch.uint8, device="cuda")
+            for gr in groups]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        ccw.simulate(g, grid, n_real=n_real, topk=w["K"], seed=w["seed"], hd_cells=hc,
-                     hd_vals=hv, real_base=base, out=out, precision=precision)
+    def run(hd_dev=None):
+        hd_dev = hd_dev or [(gr["hd_cells"], gr["hd_vals"]) for gr in groups]
+        if len(groups) == 1:
+            gr = groups[0]
+            ccw.simulate(g, gr["grid"], n_real=gr["n_real"], topk=w["K"], seed=w["seed"],
+                         hd_cells=hd_dev[0][0], hd_vals=hd_dev[0][1],
+                         real_base=gr["real_base"], out=outs[0], precision=precision)
+            return outs
+        res = ccw.simulate_groups(
+            g, [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
+                     hd_cells=h[0], hd_vals=h[1]) for gr, h in zip(groups, hd_dev)],
+            topk=w["K"], seed=w["seed"], precision=precision)
+        return [r[0] for r in res]
 
     for _ in range(max(args.warmup, 0)):
-        step()
+        run()
     torch.cuda.synchronize()
 
     def barrier():
@@ -245,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        run()
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
@@ -255,20 +277,25 @@ def run_ours(args, rank, world, local_rank):
     n_launch, kern_ms, cand_evals, macs = ccw.profile_read()
     clk = clocks.stop()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the hard data come
+    # in from pinned host memory and the realizations go back to it
     e2e_ms = None
     h2d = d2h = 0
     if not args.no_e2e:
-        host_out = torch.empty(out.shape, dtype=torch.uint8).pin_memory()
-        hpc = hpv = None
-        dc = dv = None
-        if hd is not None:
-            hpc = torch.from_numpy(hd[0]).pin_memory()
-            hpv = torch.from_numpy(hd[1]).pin_memory()
-            dc = torch.empty_like(hpc, device="cuda")
-            dv = torch.empty_like(hpv, device="cuda")
-            h2d = hpc.numel() * 4 + hpv.numel()
-        d2h = out.numel()
+        host_outs = [torch.empty(o.shape, dtype=torch.uint8).pin_memory() for o in outs]
+        pinned, dev_hd = [], []
+        for gr in groups:
+            hd = gr["hd_host"]
+            if hd is None:
+                pinned.append(None)
+                dev_hd.append((None, None))
+                continue
+            pc = torch.from_numpy(hd[0]).pin_memory()
+            pv = torch.from_numpy(hd[1]).pin_memory()
+            pinned.append((pc, pv))
+            dev_hd.append((torch.empty_like(pc, device="cuda"), torch.empty_like(pv, device="cuda")))
+            h2d += pc.numel() * 4 + pv.numel()
+        d2h = sum(o.numel() for o in outs)
         barrier()
         e2e_ms = 0.0
         for _ in range(args.steps):
@@ -276,12 +303,13 @@ def run_ours(args, rank, world, local_rank):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            if hd is not None:
-                dc.copy_(hpc, non_blocking=True)
-                dv.copy_(hpv, non_blocking=True)
-            ccw.simulate(g, grid, n_real=n_real, topk=w["K"], seed=w["seed"], hd_cells=dc,
-                         hd_vals=dv, real_base=base, out=out, precision=precision)
-            host_out.copy_(out, non_blocking=True)
+            for p, dv in zip(pinned, dev_hd):
+                if p is not None:
+                    dv[0].copy_(p[0], non_blocking=True)
+                    dv[1].copy_(p[1], non_blocking=True)
+            res = run(dev_hd)
+            for ho, o in zip(host_outs, res):
+                ho.copy_(o, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
             e2e_ms += e0.elapsed_time(e1)
@@ -293,7 +321,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms, e2e_ms_max, kern_ms_max = (float(v) for v in t.tolist())
     if rank != 0:
         return
-    cells = cells_of(grid) * n_real * world * args.steps
+    cells = cells_per_step * world * args.steps
     value = cells / (total_ms / 1e3)
     flops = 2.0 * macs
     achieved = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
@@ -313,7 +341,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "cand_evals_per_s": cand_evals * world / (total_ms / 1e3),
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
-                   "realizations_per_gpu": n_real, "precision": precision,
+                   "realizations_per_gpu": total_real, "precision": precision,
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
         "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
@@ -329,7 +357,9 @@ def run_ours(args, rank, world, local_rank):
         line["e2e"] = {"value": cells / (e2e_ms_max / 1e3), "unit": "cells/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     if not args.no_cpu_baseline:
-        n, dt, ce = oracle_sample(w, args.cpu_seconds)
+        w0 = dict(w, grid=groups[0]["grid"], hd=groups[0]["hd_host"])
+        n, dt, ce = oracle_sample(w0, args.cpu_seconds)
+        grid = groups[0]["grid"]
         n_tot = n_patches_of(grid, w["T"], w["O"])
         line["cpu_baseline"] = {"value": n * cells_of(grid) / n_tot / dt, "unit": "cells/s",
                                 "cores": 1, "kind": "oracle",

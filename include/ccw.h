@@ -54,6 +54,8 @@ extern "C" {
 #define CCW_MAX_TOPK 64
 #define CCW_LOG_FLAG_UNIFORM 1  /* patch log: empty data event, uniform pick */
 #define CCW_LOG_FLAG_DONE 2     /* patch log: the patch was simulated */
+#define CCW_LOG_FLAG_PROPOSAL 4 /* patch log: the learned proposal settled the
+                                   patch (no full search) */
 
 /* Opaque TI state, owned by the library (device buffers on the device that
  * was current at ccw_ti_prepare). */
@@ -79,7 +81,11 @@ typedef struct {
                           integer range (2048 for FP16, 256 for BF16; the
                           operands are at most 2^(d J) in the one-hot score,
                           (F - 1) 2^(d J) in the literal one). */
-  int32_t reserved[4]; /* must be 0 */
+  int32_t learned;     /* 0: full search for every patch; 1: learned proposal
+                          first (an addition of this library, see
+                          ccw_ti_attach_proposal): 2D, one-hot score only,
+                          topk <= the attached n_prop */
+  int32_t reserved[3]; /* must be 0 */
 } ccw_params;
 
 /* Shape information of a prepared TI. */
@@ -170,6 +176,10 @@ typedef struct {
   int32_t n_hd;
   uint8_t* out_dev;             /* uint8 [n_real][grid] realizations */
   int32_t* patch_log_dev;       /* int32 [n_real][n_patches][4 + topk], or NULL */
+  uint8_t* event_counts_dev;    /* uint8 [n_real][n_patches][F][(T/2^J)^d] or NULL:
+                                   the facies counts of every level-J block of each
+                                   patch's data event, as searched (needs 2^(d J) <=
+                                   255); the learned proposal trains on them */
 } ccw_group;
 
 /*
@@ -273,6 +283,100 @@ int ccw_idwt_paste(const ccw_ti* ti, int32_t B, const int32_t* pick_dev,
  * 2 (more than 1024 hard data in one template), 4 (a bounded wait gave up).
  */
 int ccw_ti_status(const ccw_ti* ti, void* stream, int32_t* status_out);
+
+/* ------------------------------------------------------------------------
+ * Learned proposal (not in the paper; an addition of this library). A small
+ * encoder maps a level-J data event, or a TI window under the same mask, to
+ * a unit 64-vector; nearest neighbours of a data event's vector among the TI
+ * windows' vectors are proposals that the exact CCF of Eq. CCW re-ranks.
+ * Network on inputs C x tj x tj (facies counts of the level-J blocks
+ * divided by 2^(d J)): conv 3x3 C->32 (pad 1) + ReLU, conv 3x3 32->32
+ * stride 2 + ReLU, conv 3x3 32->32 stride 2 + ReLU, linear -> 64, L2
+ * normalisation. Parameters are FP32 masters (layout: conv weights
+ * [out][in][3][3] then biases, layer by layer, then the linear weight
+ * [64][in] and bias). With bf16 = 1 the passes use BF16-rounded weights and
+ * activations.
+ * ------------------------------------------------------------------------ */
+typedef struct ccw_net ccw_net;
+
+/* ccw_net_create -- new encoder for in_ch channels of tj x tj, He-normal
+ * weights from `seed` (deterministic), zero biases. */
+int ccw_net_create(int32_t in_ch, int32_t tj, uint64_t seed, ccw_net** out);
+void ccw_net_free(ccw_net* net);
+int64_t ccw_net_param_count(const ccw_net* net);
+/* what = 0 copies the parameters, 1 the gradients of the last train step,
+ * to host memory of ccw_net_param_count floats. */
+int ccw_net_get(const ccw_net* net, int32_t what, float* host);
+int ccw_net_set(ccw_net* net, const float* host);
+/* ccw_net_embed -- unit embeddings float [n][64] of inputs float [n][C][tj][tj]
+ * (device pointers). */
+int ccw_net_embed(ccw_net* net, const float* x_dev, int32_t n, int32_t bf16, float* emb_dev,
+                  void* stream);
+/* ccw_net_train_step -- one InfoNCE step: anchors [B][C][tj][tj], candidates
+ * [M][C][tj][tj] (M >= B; candidate i is the positive of anchor i, all others
+ * negatives), logits a . c / tau, mean loss written to loss_dev (float, may
+ * be NULL). Gradients are recomputed; with apply = 1 an AdamW step
+ * (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay wd) follows. */
+int ccw_net_train_step(ccw_net* net, const float* anchors_dev, int32_t B,
+                       const float* cands_dev, int32_t M, float tau, float lr, float wd,
+                       int32_t bf16, int32_t apply, float* loss_dev, void* stream);
+const char* ccw_net_last_error(void);
+
+/*
+ * Inference of the learned proposal inside ccw_simulate (params.learned = 1).
+ * Per patch: the data event's block counts are embedded; its overlap mask
+ * type m (which of the four level-J overlap strips of width OR / 2^J are
+ * fully known: bit 0 low x, 1 high x, 2 low y, 3 high y) selects the table of
+ * TI-window embeddings under mask m; the n_prop windows with the largest dot
+ * product are proposals; their exact Eq. CCW score and hard-data mismatch
+ * (Sec. 4.4) rank them as the full search would, K best kept. When the
+ * relative embedding gap (e_1 - e_nprop) / max(|e_1|, 1e-6) is at least
+ * gap_theta the patch takes its pick from those K (log flag
+ * CCW_LOG_FLAG_PROPOSAL); otherwise, and for patches without a full strip,
+ * with both strips of an axis, or empty, the full search runs.
+ *
+ * ccw_ti_attach_proposal -- embeds every candidate window of `ti` under each
+ * mask type with `net` (BF16 passes) and keeps the tables and a copy of the
+ * parameters in the handle (16 x P_c x 64 BF16). The network must have
+ * in_ch = F and tj = T / 2^J; 2D TIs only; 1 <= n_prop <= CCW_MAX_TOPK.
+ * net = NULL detaches. Synchronizes `stream`. Later changes of `net` do not
+ * affect the handle. Errors: CCW_EINVAL, CCW_ENOMEM, CCW_ECUDA.
+ */
+int ccw_ti_attach_proposal(ccw_ti* ti, const ccw_net* net, int32_t n_prop, float gap_theta,
+                           void* stream);
+
+/*
+ * ccw_proposal_query -- the proposal step alone for n data events given by
+ * their block counts counts_dev uint8 [n][F][tj^2] (as ccw_group's
+ * event_counts_dev records them). Writes prop_dev int32 [n][n_prop]
+ * (proposals by embedding score, best first), gap_dev float [n] (relative
+ * gap, -1 when the event has no usable mask type) and type_dev int32 [n]
+ * (mask type), device buffers owned by the caller. Needs an attached
+ * proposal. Asynchronous on `stream`.
+ */
+int ccw_proposal_query(const ccw_ti* ti, const uint8_t* counts_dev, int32_t n, int32_t* prop_dev,
+                       float* gap_dev, int32_t* type_dev, void* stream);
+
+/*
+ * ccw_proposal_inputs -- encoder inputs float [n][F][tj][tj] for training.
+ *  what = 0: from data-event block counts counts_dev uint8 [n][F][tj^2]
+ *            (counts / 2^(d J)); type_dev int32 [n] receives the mask types.
+ *  what = 1: TI window of candidate cand_dev[i] under mask type type_dev[i]
+ *            (facies counts of the blocks inside the mask, / 2^(d J); zero
+ *            outside), the form the attached tables are built from.
+ * 2D TIs only. Asynchronous on `stream`.
+ */
+int ccw_proposal_inputs(const ccw_ti* ti, int32_t what, const uint8_t* counts_dev,
+                        const int32_t* cand_dev, int32_t* type_dev, int32_t n, float* out_dev,
+                        void* stream);
+
+/*
+ * ccw_proposal_stats -- counters of the learned simulations on `ti` since
+ * the last read (synchronizes `stream`, then resets them): out[0] patches
+ * with a non-empty data event, out[1] patches that had proposals (a usable
+ * mask type), out[2] patches settled by the proposal.
+ */
+int ccw_proposal_stats(const ccw_ti* ti, int64_t out[3], void* stream);
 
 /* ccw_last_error -- text of the last failure on the calling host thread. */
 const char* ccw_last_error(void);

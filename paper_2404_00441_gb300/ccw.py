@@ -18,6 +18,9 @@ _lib = None
 
 CCW_UNKNOWN = 255
 CCW_MAX_TOPK = 64
+LOG_FLAG_UNIFORM = 1
+LOG_FLAG_DONE = 2
+LOG_FLAG_PROPOSAL = 4
 
 
 class CCWError(RuntimeError):
@@ -27,14 +30,15 @@ class CCWError(RuntimeError):
 class _Params(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("grid", C.c_int32 * 3), ("topk", C.c_int32),
                 ("n_real", C.c_int32), ("real_base", C.c_int32), ("path_random", C.c_int32),
-                ("score_mode", C.c_int32), ("precision", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("score_mode", C.c_int32), ("precision", C.c_int32), ("learned", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class _Group(C.Structure):
     _fields_ = [("grid", C.c_int32 * 3), ("n_real", C.c_int32), ("real_base", C.c_int32),
                 ("hd_cells_dev", C.c_void_p), ("hd_vals_dev", C.c_void_p), ("n_hd", C.c_int32),
-                ("out_dev", C.c_void_p), ("patch_log_dev", C.c_void_p)]
+                ("out_dev", C.c_void_p), ("patch_log_dev", C.c_void_p),
+                ("event_counts_dev", C.c_void_p)]
 
 
 class _Desc(C.Structure):
@@ -74,6 +78,21 @@ def load():
     lib.ccw_profile_read.argtypes = [C.POINTER(i64), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.ccw_launch_count.restype = i64
+    f32 = C.c_float
+    lib.ccw_net_create.argtypes = [i32, i32, u64, C.POINTER(P)]
+    lib.ccw_net_free.argtypes = [P]
+    lib.ccw_net_free.restype = None
+    lib.ccw_net_param_count.argtypes = [P]
+    lib.ccw_net_param_count.restype = i64
+    lib.ccw_net_get.argtypes = [P, i32, P]
+    lib.ccw_net_set.argtypes = [P, P]
+    lib.ccw_net_embed.argtypes = [P, P, i32, i32, P, P]
+    lib.ccw_net_train_step.argtypes = [P, P, i32, P, i32, f32, f32, f32, i32, i32, P, P]
+    lib.ccw_net_last_error.restype = C.c_char_p
+    lib.ccw_ti_attach_proposal.argtypes = [P, P, i32, f32, P]
+    lib.ccw_proposal_query.argtypes = [P, P, i32, P, P, P, P]
+    lib.ccw_proposal_inputs.argtypes = [P, i32, P, P, P, i32, P, P]
+    lib.ccw_proposal_stats.argtypes = [P, C.POINTER(i64), P]
     _lib = lib
     return lib
 
@@ -172,6 +191,47 @@ class TI:
         _check(self._lib.ccw_ti_export(self._h, what, _ptr(out), _stream(stream)))
         return out
 
+    def attach_proposal(self, net, n_prop=64, gap_theta=0.0, stream=None):
+        """``ccw_ti_attach_proposal``: tables of the TI windows under every mask
+        type; ``net`` None detaches."""
+        _check(self._lib.ccw_ti_attach_proposal(self._h, None if net is None else net.handle,
+                                                n_prop, float(gap_theta), _stream(stream)))
+        self.n_prop = n_prop if net is not None else 0
+
+    def proposal_query(self, counts: torch.Tensor, stream=None):
+        """``ccw_proposal_query`` on block counts uint8 [n, F, tj*tj]:
+        (proposals int32 [n, n_prop], gaps float [n], mask types int32 [n])."""
+        n = counts.shape[0]
+        prop = torch.full((n, self.n_prop), -1, dtype=torch.int32, device=counts.device)
+        gap = torch.empty((n,), dtype=torch.float32, device=counts.device)
+        typ = torch.empty((n,), dtype=torch.int32, device=counts.device)
+        _check(self._lib.ccw_proposal_query(self._h, _ptr(counts), n, _ptr(prop), _ptr(gap),
+                                            _ptr(typ), _stream(stream)))
+        return prop, gap, typ
+
+    def proposal_inputs(self, what, counts=None, cand=None, types=None, stream=None):
+        """``ccw_proposal_inputs``: encoder inputs float [n, F, tj, tj] from
+        block counts (what 0; returns (x, mask types)) or from TI windows of
+        candidates under mask types (what 1; returns x)."""
+        tj = self.templ // self.scale
+        if what == 0:
+            n = counts.shape[0]
+            types = torch.empty((n,), dtype=torch.int32, device=counts.device)
+        else:
+            n = cand.shape[0]
+        dev = (counts if what == 0 else cand).device
+        out = torch.empty((n, self.n_facies, tj, tj), dtype=torch.float32, device=dev)
+        _check(self._lib.ccw_proposal_inputs(self._h, what, _ptr(counts), _ptr(cand),
+                                             _ptr(types), n, _ptr(out), _stream(stream)))
+        return (out, types) if what == 0 else out
+
+    def proposal_stats(self, stream=None):
+        """``ccw_proposal_stats``: (non-empty patches, patches with proposals,
+        patches settled by the proposal) since the last read."""
+        v = (C.c_int64 * 3)()
+        _check(self._lib.ccw_proposal_stats(self._h, v, _stream(stream)))
+        return tuple(int(x) for x in v)
+
     def status(self, stream=None) -> int:
         v = C.c_int32()
         _check(self._lib.ccw_ti_status(self._h, _stream(stream), C.byref(v)))
@@ -180,7 +240,7 @@ class TI:
 
 def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None, real_base=0,
              path_random=0, score_mode=0, precision=0, want_log=False, out=None, log=None,
-             stream=None):
+             learned=0, stream=None):
     """``ccw_simulate``: returns (realizations uint8 [n_real, *grid[::-1]], log or None)."""
     lib = load()
     p = _Params()
@@ -192,6 +252,7 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
     p.path_random = path_random
     p.score_mode = score_mode
     p.precision = precision
+    p.learned = learned
     shape = (n_real,) + tuple(grid)[::-1]
     if out is None:
         out = torch.empty(shape, dtype=torch.uint8, device="cuda")
@@ -209,7 +270,7 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
 
 
 def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0, precision=0,
-                    want_log=False, stream=None):
+                    want_log=False, want_counts=False, learned=0, stream=None):
     """``ccw_simulate_groups``: several grid sizes in one batch. ``groups`` is
     a list of dicts with keys grid, n_real, real_base and optionally hd_cells,
     hd_vals (CUDA tensors). Returns a list of (realizations, log or None)."""
@@ -222,6 +283,7 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
     p.path_random = path_random
     p.score_mode = score_mode
     p.precision = precision
+    p.learned = learned
     arr = (_Group * len(groups))()
     results = []
     keep = []
@@ -235,6 +297,9 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
             n_patches *= v
         log = (torch.empty((n_real, n_patches, 4 + topk), dtype=torch.int32, device="cuda")
                if want_log else None)
+        tjd = (ti.templ // ti.scale) ** ti.ndim
+        counts = (torch.empty((n_real, n_patches, ti.n_facies, tjd), dtype=torch.uint8,
+                              device="cuda") if want_counts else None)
         hc, hv = g.get("hd_cells"), g.get("hd_vals")
         n_hd = 0 if hv is None else int(hv.numel())
         arr[i].grid = _i3(grid)
@@ -245,8 +310,9 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
         arr[i].n_hd = n_hd
         arr[i].out_dev = _ptr(out)
         arr[i].patch_log_dev = _ptr(log) if want_log else None
+        arr[i].event_counts_dev = _ptr(counts) if want_counts else None
         keep.append((hc, hv))
-        results.append((out, log))
+        results.append((out, log, counts) if want_counts else (out, log))
     _check(lib.ccw_simulate_groups(ti.handle, C.byref(p), arr, len(groups), seed & (2 ** 64 - 1),
                                    _stream(stream)))
     return results
@@ -305,3 +371,58 @@ def profile_read():
 
 def launch_count() -> int:
     return int(load().ccw_launch_count())
+
+
+class Net:
+    """The learned proposal's encoder (``ccw_net_*``)."""
+
+    def __init__(self, in_ch: int, tj: int, seed: int = 0):
+        lib = load()
+        h = C.c_void_p()
+        rc = lib.ccw_net_create(in_ch, tj, seed & (2 ** 64 - 1), C.byref(h))
+        if rc != 0:
+            raise CCWError(lib.ccw_net_last_error().decode())
+        self._h, self._lib = h, lib
+        self.in_ch, self.tj = in_ch, tj
+        self.n_params = int(lib.ccw_net_param_count(h))
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                self._lib.ccw_net_free(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _chk(self, rc):
+        if rc != 0:
+            raise CCWError(self._lib.ccw_net_last_error().decode())
+
+    def get(self, what=0):
+        import numpy as np
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._chk(self._lib.ccw_net_get(self._h, what, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._chk(self._lib.ccw_net_set(self._h, p.ctypes.data_as(C.c_void_p)))
+
+    def embed(self, x: torch.Tensor, bf16=0, stream=None) -> torch.Tensor:
+        n = x.shape[0]
+        out = torch.empty((n, 64), dtype=torch.float32, device=x.device)
+        self._chk(self._lib.ccw_net_embed(self._h, _ptr(x), n, bf16, _ptr(out), _stream(stream)))
+        return out
+
+    def train_step(self, anchors, cands, tau=0.1, lr=1e-3, wd=1e-4, bf16=1, apply=1,
+                   stream=None) -> torch.Tensor:
+        loss = torch.zeros(1, dtype=torch.float32, device=anchors.device)
+        self._chk(self._lib.ccw_net_train_step(self._h, _ptr(anchors), anchors.shape[0],
+                                               _ptr(cands), cands.shape[0], tau, lr, wd, bf16,
+                                               apply, _ptr(loss), _stream(stream)))
+        return loss

@@ -44,6 +44,20 @@ cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3],
                               int Tj, int64_t P, int B, const int32_t* picks,
                               const int32_t* origins, uint8_t* grid, const int gdim[3],
                               int* status, cudaStream_t st);
+// proposal.cu
+int encode_smem_bytes(int C, int tj);
+cudaError_t encode_set_smem(int smem);
+cudaError_t launch_encode_items(const WaveArgs& a, bool pdl, cudaStream_t st);
+cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables,
+                                 cudaStream_t st);
+cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st);
+cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st);
+cudaError_t launch_records_from_counts(const WaveArgs& a, const uint8_t* counts,
+                                      int32_t* type_out, cudaStream_t st);
+cudaError_t launch_inputs(const WaveArgs& a, int what, const uint8_t* counts, const int32_t* cand,
+                          int32_t* type, int n, float* out, cudaStream_t st);
+// learned.cu
+void net_view(const ccw_net* n, int* C, int* tj, const float** params, int64_t* count);
 }  // namespace ccw
 
 using namespace ccw;
@@ -95,14 +109,16 @@ unsigned long long* profiling_counters() {
 }
 
 // Event-record layout (see EvDev).
-void event_layout(int nch, int rows, int TjP, int hd_cap, EvDev& ev) {
+void event_layout(int nch, int rows, int TjP, int hd_cap, int F, int ncells, EvDev& ev) {
   int64_t off = 64;
   ev.mask_off = (int)off;
   off = align_up(off + 4LL * rows, 16);
   ev.hd_off = (int)off;
   off = align_up(off + 8LL * hd_cap, 16);
   ev.w_off = (int)off;
-  off = align_up(off + 4LL * nch * rows * TjP, 256);
+  off = align_up(off + 4LL * nch * rows * TjP, 16);
+  ev.counts_off = (int)off;
+  off = align_up(off + (int64_t)F * ncells, 256);
   ev.stride = off;
   ev.hd_cap = hd_cap;
   ev.base = nullptr;
@@ -126,12 +142,16 @@ struct SimPlan {
   int n_groups = 0;
   std::vector<GroupPlan> groups;
   int K, score_mode, precision;
+  int learned = 0, n_prop = 0;
   int n_waves, max_items;
   std::vector<int64_t> wave_off;
   void* items = nullptr;
   void* ev = nullptr;
   void* part = nullptr;
   void* bmat = nullptr;
+  void* emb = nullptr;       // learned proposal: [max_items][64] item embeddings
+  void* prop = nullptr;      // [max_items][n_prop] proposals
+  void* prop_gap = nullptr;  // [max_items] relative embedding gaps
   CallDev* call = nullptr;
   SimGroup* dgroups = nullptr;
   EvDev evl;
@@ -155,6 +175,9 @@ struct SimPlan {
     cudaFree(ev);
     cudaFree(part);
     cudaFree(bmat);
+    cudaFree(emb);
+    cudaFree(prop);
+    cudaFree(prop_gap);
     cudaFree(call);
     cudaFree(dgroups);
     release_cp();
@@ -180,6 +203,12 @@ struct ccw_ti {
   int64_t z8_nq = 0;
   void* z8_f16 = nullptr;
   void* z8_bf16 = nullptr;
+  // learned proposal (2D): encoder parameters, window tables per mask type
+  float* d_net = nullptr;
+  __nv_bfloat16* d_tables = nullptr;   // [16][P][64]
+  unsigned long long* d_learn_stats = nullptr;   // [3]
+  int n_prop = 0;
+  float gap_theta = 0.f;
   std::mutex mu;
   SimPlan* plan = nullptr;
 };
@@ -219,6 +248,7 @@ void fill_ti(const ccw_ti* t, int score_mode, WaveArgs& a) {
   d.P = t->P;
   d.n_tiles = t->n_tiles;
   a.status = t->d_status;
+  a.Oj = t->O / t->s;
 }
 
 int check_score_bound(const ccw_ti* t, int score_mode) {
@@ -459,7 +489,7 @@ int search_common(const ccw_ti* t, int mode, int32_t B, const uint8_t* de, const
   cudaStream_t st = (cudaStream_t)stream;
   WaveArgs a;
   fill_ti(t, score_mode, a);
-  event_layout(a.ti.nch, t->rows, t->TjP, hd_capacity(t), a.ev);
+  event_layout(a.ti.nch, t->rows, t->TjP, hd_capacity(t), t->F, t->rows * t->Tj, a.ev);
   a.de = de;
   a.hd = hd;
   a.ctr = ctr;
@@ -750,6 +780,9 @@ void ccw_ti_free(ccw_ti* t) {
   cudaFree(t->d_planes);
   cudaFree(t->d_pyr);
   cudaFree(t->d_status);
+  cudaFree(t->d_net);
+  cudaFree(t->d_tables);
+  cudaFree(t->d_learn_stats);
   delete t;
 }
 
@@ -824,7 +857,7 @@ int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
     return fail(CCW_EINVAL, "NULL input, output or counter");
   WaveArgs a;
   fill_ti(t, sm, a);
-  event_layout(a.ti.nch, t->rows, t->TjP, hd_capacity(t), a.ev);
+  event_layout(a.ti.nch, t->rows, t->TjP, hd_capacity(t), t->F, t->rows * t->Tj, a.ev);
   CcfPlan cp;
   plan_ccf(t, precision, a.ti.nch, k, B, a.ev, cp);
   const int64_t part_off = align_up(cp.ev_bytes, 256);
@@ -887,7 +920,7 @@ namespace {
 
 bool plan_matches(const SimPlan* pl, const ccw_params* p, const ccw_group* groups, int n_groups) {
   if (!pl || pl->n_groups != n_groups || pl->K != p->topk || pl->score_mode != p->score_mode ||
-      pl->precision != p->precision)
+      pl->precision != p->precision || pl->learned != p->learned)
     return false;
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
@@ -908,6 +941,8 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   pl->K = p->topk;
   pl->score_mode = p->score_mode;
   pl->precision = p->precision;
+  pl->learned = p->learned;
+  pl->n_prop = p->learned ? t->n_prop : 0;
   pl->n_waves = 0;
   for (int i = 0; i < n_groups; ++i) {
     GroupPlan& g = pl->groups[i];
@@ -952,7 +987,7 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   }
   pl->wave_off[pl->n_waves] = (int64_t)items.size();
   const int nch = p->score_mode == 0 ? t->F - 1 : 1;
-  event_layout(nch, t->rows, t->TjP, hd_capacity(t), pl->evl);
+  event_layout(nch, t->rows, t->TjP, hd_capacity(t), t->F, t->rows * t->Tj, pl->evl);
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
   plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp);
@@ -968,6 +1003,12 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
       (e = cudaMalloc(&pl->ev, (size_t)cp->ev_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&pl->part, (size_t)cp->part_bytes)) != cudaSuccess ||
       (cp->bmat_bytes && (e = cudaMalloc(&pl->bmat, (size_t)cp->bmat_bytes)) != cudaSuccess) ||
+      (pl->learned &&
+       ((e = cudaMalloc(&pl->emb, sizeof(float) * 64 * (size_t)pl->max_items)) != cudaSuccess ||
+        (e = cudaMalloc(&pl->prop, sizeof(int) * (size_t)pl->n_prop * pl->max_items)) !=
+            cudaSuccess ||
+        (e = cudaMalloc(&pl->prop_gap, sizeof(float) * (size_t)pl->max_items)) !=
+            cudaSuccess)) ||
       (e = cudaMalloc((void**)&pl->call, sizeof(CallDev))) != cudaSuccess ||
       (e = cudaMalloc((void**)&pl->dgroups, sizeof(SimGroup) * n_groups)) != cudaSuccess) {
     delete pl;
@@ -995,6 +1036,15 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
   a.call = pl->call;
   a.K = pl->K;
   a.part = (unsigned long long*)pl->part;
+  if (pl->learned) {
+    a.learned = 1;
+    a.net = t->d_net;
+    a.tables = t->d_tables;
+    a.n_prop = pl->n_prop;
+    a.emb = (float*)pl->emb;
+    a.prop = (int*)pl->prop;
+    a.prop_gap = (float*)pl->prop_gap;
+  }
   const CcfPlan& cp = *static_cast<const CcfPlan*>(pl->cp);
   size_t pe = 0;
   for (int w = 0; w < pl->n_waves; ++w) {
@@ -1005,6 +1055,14 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
       apply_ccf(t, cp, pl->bmat, c);
       cudaError_t e = launch_events(kModeSim, c, true, st);
       if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
+      if (pl->learned) {
+        // learned proposal: embed, nearest windows, exact re-rank; the CCF
+        // kernel then skips the items the proposal settled
+        if ((e = launch_encode_items(c, true, st)) != cudaSuccess ||
+            (e = launch_nnsel(c, true, st)) != cudaSuccess ||
+            (e = launch_rerank(c, true, st)) != cudaSuccess)
+          return cuda_fail(e, "proposal kernel launch");
+      }
       if (prof) {
         if (pe >= pl->prof_events.size()) {
           cudaEvent_t e0, e1;
@@ -1051,7 +1109,13 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if (p->score_mode != 0 && p->score_mode != 1) return fail(CCW_EINVAL, "bad score_mode");
   if (int rc = check_precision(t, p->precision, p->score_mode)) return rc;
   if (p->path_random != 0 && p->path_random != 1) return fail(CCW_EINVAL, "bad path_random");
-  for (int i = 0; i < 4; ++i)
+  if (p->learned != 0 && p->learned != 1) return fail(CCW_EINVAL, "bad learned flag");
+  if (p->learned) {
+    if (!t->d_tables) return fail(CCW_EINVAL, "learned = 1 needs an attached proposal");
+    if (p->score_mode != 0) return fail(CCW_EINVAL, "learned = 1 needs the one-hot score");
+    if (p->topk > t->n_prop) return fail(CCW_EINVAL, "topk > the proposal's n_prop");
+  }
+  for (int i = 0; i < 3; ++i)
     if (p->reserved[i]) return fail(CCW_EINVAL, "reserved fields must be 0");
   if (int rc = check_score_bound(t, p->score_mode)) return rc;
   if (n_groups < 1 || !groups) return fail(CCW_EINVAL, "at least one grid group is needed");
@@ -1062,6 +1126,8 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
     if (!g.out_dev) return fail(CCW_EINVAL, "group %d: out_dev is NULL", i);
     if (g.n_hd < 0 || (g.n_hd > 0 && (!g.hd_cells_dev || !g.hd_vals_dev)))
       return fail(CCW_EINVAL, "group %d: bad hard data", i);
+    if (g.event_counts_dev && t->sd > 255)
+      return fail(CCW_EINVAL, "group %d: block counts need 2^(d J) <= 255", i);
     for (int a = 0; a < 3; ++a)
       if (g.grid[a] <= 0 || (a >= d && g.grid[a] != 1))
         return fail(CCW_EINVAL, "group %d: bad grid dims", i);
@@ -1089,6 +1155,8 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   call.path_random = p->path_random;
   call.log_stride = 4 + p->topk;
   call.work = work;
+  call.gap_theta = t->gap_theta;
+  call.learn_stats = t->d_learn_stats;
   std::vector<SimGroup> hg(n_groups);
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
@@ -1104,6 +1172,7 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
     s.n_patches = g.n_patches;
     s.real_base = groups[i].real_base;
     s.log = groups[i].patch_log_dev;
+    s.counts = groups[i].event_counts_dev;
   }
   cudaError_t e;
   if ((e = cudaMemcpyAsync(pl->call, &call, sizeof(call), cudaMemcpyHostToDevice, st)) !=
@@ -1134,7 +1203,8 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if ((e = cudaGraphLaunch(pl->exec[gi], st)) != cudaSuccess) return cuda_fail(e, "graph launch");
   int64_t wave_launches = 0;
   for (int w = 0; w < pl->n_waves; ++w)
-    wave_launches += 3 * ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
+    wave_launches += (pl->learned ? 6 : 3) *
+                     ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
   g_launches += wave_launches;
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
@@ -1169,6 +1239,172 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Learned proposal (an addition of this library; the paper has no
+// counterpart).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kEncMaxSmem = 200 * 1024;
+
+bool usable_mask_type(int type) { return type != 0 && (type & 3) != 3 && (type & 12) != 12; }
+
+// Minimal event records for the query entry point: meta and block counts.
+EvDev query_records(const ccw_ti* t, void* base) {
+  EvDev ev;
+  memset(&ev, 0, sizeof(ev));
+  ev.base = (unsigned char*)base;
+  ev.counts_off = 64;
+  ev.stride = align_up(64 + (int64_t)t->F * t->Tj * t->Tj, 16);
+  return ev;
+}
+}  // namespace
+
+extern "C" int ccw_ti_attach_proposal(ccw_ti* t, const ccw_net* net, int32_t n_prop,
+                                      float gap_theta, void* stream) {
+  if (!t) return fail(CCW_EINVAL, "NULL TI");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(t->mu);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "attach proposal");
+  // a captured plan holds the old table pointers
+  delete t->plan;
+  t->plan = nullptr;
+  cudaFree(t->d_net);
+  cudaFree(t->d_tables);
+  t->d_net = nullptr;
+  t->d_tables = nullptr;
+  t->n_prop = 0;
+  if (!net) return CCW_OK;
+  if (t->ndim != 2) return fail(CCW_EINVAL, "the learned proposal is 2D only");
+  if (n_prop < 1 || n_prop > CCW_MAX_TOPK)
+    return fail(CCW_EINVAL, "n_prop must be in [1, %d]", CCW_MAX_TOPK);
+  if (!(gap_theta == gap_theta)) return fail(CCW_EINVAL, "gap_theta is NaN");
+  if (t->sd > 255) return fail(CCW_EINVAL, "the proposal needs 2^(d J) <= 255");
+  int C, tj;
+  const float* params;
+  int64_t count;
+  net_view(net, &C, &tj, &params, &count);
+  if (C != t->F || tj != t->Tj)
+    return fail(CCW_EINVAL, "network shape (%d ch, %d) != TI (F %d, T/2^J %d)", C, tj, t->F, t->Tj);
+  const int smem = encode_smem_bytes(C, tj);
+  if (smem > kEncMaxSmem) return fail(CCW_EINVAL, "template too large for the encoder");
+  if ((e = encode_set_smem(smem)) != cudaSuccess) return cuda_fail(e, "encoder attributes");
+  const size_t tab_bytes = sizeof(__nv_bfloat16) * 16 * 64 * (size_t)t->P;
+  if ((e = cudaMalloc((void**)&t->d_net, sizeof(float) * count)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&t->d_tables, tab_bytes)) != cudaSuccess ||
+      (!t->d_learn_stats &&
+       (e = cudaMalloc((void**)&t->d_learn_stats, 3 * sizeof(unsigned long long))) !=
+           cudaSuccess)) {
+    cudaFree(t->d_net);
+    cudaFree(t->d_tables);
+    t->d_net = nullptr;
+    t->d_tables = nullptr;
+    return fail(CCW_ENOMEM, "proposal tables: %s", cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpyAsync(t->d_net, params, sizeof(float) * count, cudaMemcpyDeviceToDevice,
+                           st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(t->d_tables, 0, tab_bytes, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(t->d_learn_stats, 0, 3 * sizeof(unsigned long long), st)) !=
+          cudaSuccess)
+    return cuda_fail(e, "attach proposal");
+  WaveArgs a;
+  fill_ti(t, 0, a);
+  a.net = t->d_net;
+  for (int type = 1; type < 16; ++type) {
+    if (!usable_mask_type(type)) continue;
+    if ((e = launch_encode_tables(a, type, t->d_tables, st)) != cudaSuccess)
+      return cuda_fail(e, "proposal table kernel");
+    g_launches += (t->P + 65534) / 65535;
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "proposal tables");
+  t->n_prop = n_prop;
+  t->gap_theta = gap_theta;
+  return CCW_OK;
+}
+
+extern "C" int ccw_proposal_query(const ccw_ti* tc, const uint8_t* counts_dev, int32_t n,
+                                  int32_t* prop_dev, float* gap_dev, int32_t* type_dev,
+                                  void* stream) {
+  if (!tc) return fail(CCW_EINVAL, "NULL TI");
+  ccw_ti* t = const_cast<ccw_ti*>(tc);
+  if (!t->d_tables) return fail(CCW_EINVAL, "no proposal attached");
+  if (n < 0) return fail(CCW_EINVAL, "n must be >= 0");
+  if (n == 0) return CCW_OK;
+  if (!counts_dev || !prop_dev || !gap_dev) return fail(CCW_EINVAL, "NULL buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = std::min(n, 65535);
+  EvDev ev = query_records(t, nullptr);
+  void* rec = nullptr;
+  void* emb = nullptr;
+  cudaError_t e;
+  if ((e = cudaMallocAsync(&rec, (size_t)ev.stride * chunk, st)) != cudaSuccess ||
+      (e = cudaMallocAsync(&emb, sizeof(float) * 64 * (size_t)chunk, st)) != cudaSuccess) {
+    if (rec) cudaFreeAsync(rec, st);
+    return fail(CCW_ENOMEM, "query workspace: %s", cudaGetErrorString(e));
+  }
+  ev.base = (unsigned char*)rec;
+  const int64_t nc = (int64_t)t->F * t->Tj * t->Tj;
+  int rc = CCW_OK;
+  for (int i0 = 0; i0 < n && rc == CCW_OK; i0 += chunk) {
+    WaveArgs a;
+    fill_ti(t, 0, a);
+    a.ev = ev;
+    a.n_items = std::min(chunk, n - i0);
+    a.net = t->d_net;
+    a.tables = t->d_tables;
+    a.n_prop = t->n_prop;
+    a.emb = (float*)emb;
+    a.prop = prop_dev + (int64_t)i0 * t->n_prop;
+    a.prop_gap = gap_dev + i0;
+    if ((e = launch_records_from_counts(a, counts_dev + i0 * nc, type_dev ? type_dev + i0 : nullptr,
+                                        st)) != cudaSuccess ||
+        (e = launch_encode_items(a, false, st)) != cudaSuccess ||
+        (e = launch_nnsel(a, false, st)) != cudaSuccess)
+      rc = cuda_fail(e, "proposal query kernels");
+    g_launches += 3;
+  }
+  cudaFreeAsync(emb, st);
+  cudaFreeAsync(rec, st);
+  return rc;
+}
+
+extern "C" int ccw_proposal_inputs(const ccw_ti* tc, int32_t what, const uint8_t* counts_dev,
+                                   const int32_t* cand_dev, int32_t* type_dev, int32_t n,
+                                   float* out_dev, void* stream) {
+  if (!tc) return fail(CCW_EINVAL, "NULL TI");
+  ccw_ti* t = const_cast<ccw_ti*>(tc);
+  if (t->ndim != 2) return fail(CCW_EINVAL, "the learned proposal is 2D only");
+  if (n < 0) return fail(CCW_EINVAL, "n must be >= 0");
+  if (what == 0 && !counts_dev) return fail(CCW_EINVAL, "what 0 needs counts_dev");
+  if (what == 1 && (!cand_dev || !type_dev)) return fail(CCW_EINVAL, "what 1 needs cand and type");
+  if (what != 0 && what != 1) return fail(CCW_EINVAL, "bad what");
+  if (n == 0) return CCW_OK;
+  if (!out_dev) return fail(CCW_EINVAL, "NULL output");
+  WaveArgs a;
+  fill_ti(t, 0, a);
+  cudaError_t e = launch_inputs(a, what, counts_dev, cand_dev, type_dev, n, out_dev,
+                                (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal input kernel");
+  g_launches += (n + 65534) / 65535;
+  return CCW_OK;
+}
+
+extern "C" int ccw_proposal_stats(const ccw_ti* tc, int64_t out[3], void* stream) {
+  if (!tc || !out) return fail(CCW_EINVAL, "NULL argument");
+  ccw_ti* t = const_cast<ccw_ti*>(tc);
+  out[0] = out[1] = out[2] = 0;
+  if (!t->d_learn_stats) return CCW_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long h[3];
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess ||
+      (e = cudaMemcpy(h, t->d_learn_stats, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemset(t->d_learn_stats, 0, sizeof(h))) != cudaSuccess)
+    return cuda_fail(e, "proposal stats");
+  for (int i = 0; i < 3; ++i) out[i] = (int64_t)h[i];
+  return CCW_OK;
+}
+
 extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t* hd_cells_dev,
                             const uint8_t* hd_vals_dev, int32_t n_hd, uint64_t seed,
                             uint8_t* out_dev, int32_t* patch_log_dev, void* stream) {
@@ -1184,6 +1420,7 @@ extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t
   g.n_hd = n_hd;
   g.out_dev = out_dev;
   g.patch_log_dev = patch_log_dev;
+  g.event_counts_dev = nullptr;
   return simulate_groups(const_cast<ccw_ti*>(tc), p, &g, 1, seed, stream);
 }
 

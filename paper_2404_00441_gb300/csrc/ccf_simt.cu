@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kThreads)
       m[kMConst] = em[kEvConst];
       m[kMNHd] = em[kEvNHd];
       m[kMMask] = em[kEvMaskCells];
-      m[kMActive] = (MODE == kModeMap) ? 1 : (em[kEvKnown] > 0);
+      // items settled by the learned proposal need no full search
+      m[kMActive] = (MODE == kModeMap) ? 1 : (em[kEvKnown] > 0 && !em[kEvResolved]);
     } else {
       m[kMKnown] = 0;
       m[kMConst] = 0;
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThreads)
   if (work && tid == 0 && tile_id == 0) {
 #pragma unroll
     for (int nb = 0; nb < NB; ++nb)
-      if (meta[nb * 8 + kMKnown] > 0 && MODE != kModeMap) {
+      if (meta[nb * 8 + kMActive] && MODE != kModeMap) {
         atomicAdd(&work[0], (unsigned long long)t.P);
         atomicAdd(&work[1], (unsigned long long)t.P * meta[nb * 8 + kMMask] * t.nch);
       }

@@ -2,6 +2,7 @@
 // public ABI; see include/ccw.h for that).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -116,12 +117,17 @@ struct TiDev {
 //   holds a non-zero weight in some channel), int2 hd[hd_cap] (.x: offset of
 //   the hard datum in the cropped fine TI relative to a candidate's first
 //   cell; .y: (offset in the template window << 8) | code),
-//   float w[nch][rows][TjP].
-enum { kEvKnown = 0, kEvConst = 1, kEvMaskCells = 2, kEvNHd = 3 };
+//   float w[nch][rows][TjP], uint8 counts[F][Tj^d] (facies counts of the
+//   level-J blocks, saturated at 255).
+// meta[kEvMaskType]: overlap strips fully known in 2D (bit 0 low x, 1 high x,
+// 2 low y, 3 high y); meta[kEvResolved]: 1 when the learned proposal settled
+// the item (the full CCF then skips it).
+enum { kEvKnown = 0, kEvConst = 1, kEvMaskCells = 2, kEvNHd = 3, kEvMaskType = 4,
+       kEvResolved = 5 };
 struct EvDev {
   unsigned char* base;
   int64_t stride;
-  int mask_off, hd_off, w_off, hd_cap;
+  int mask_off, hd_off, w_off, counts_off, hd_cap;
 };
 
 // One grid size of a simulation batch (device array, rewritten every call).
@@ -132,6 +138,7 @@ struct SimGroup {
   int64_t gp_vol, n_patches;
   int real_base;           // id of the group's first realization
   int32_t* log;            // [n_real][n_patches][log_stride] or NULL
+  uint8_t* counts;         // [n_real][n_patches][F][Tj^d] data-event block counts or NULL
 };
 
 // Per-call values of a simulation, read from device memory so that a
@@ -141,6 +148,8 @@ struct CallDev {
   int path_random;
   int log_stride;
   unsigned long long* work;  // profiling counters [2] or NULL
+  float gap_theta;           // learned proposal: relative gap that settles a patch
+  unsigned long long* learn_stats;  // learned proposal counters [3] or NULL
 };
 
 struct WaveArgs {
@@ -183,6 +192,15 @@ struct WaveArgs {
   int32_t* map_mis;
   int* status;
   unsigned long long* work;     // profiling counters for search/map mode (or NULL)
+  // learned proposal (simulation mode)
+  int learned;
+  const float* net;         // encoder parameters (FP32)
+  const __nv_bfloat16* tables;  // [16 mask types][P][64] unit embeddings of TI windows
+  float* emb;               // [n_items][64] item embeddings
+  int* prop;                // [n_items][n_prop] proposals
+  float* prop_gap;          // [n_items] relative embedding gap of the proposals
+  int n_prop;
+  int Oj;                   // overlap in level-J blocks
 };
 
 }  // namespace ccw

@@ -255,6 +255,7 @@ struct ItemPos {
   const uint8_t* overlay;   // the group's hard data
   int G[3], Gp[3];
   int32_t* log;             // this patch's log record, or NULL
+  uint8_t* counts;          // this patch's block-count record, or NULL
 };
 
 template <int D>
@@ -288,6 +289,9 @@ __device__ __forceinline__ ItemPos decode_sim_item(const WaveArgs& a, int item) 
   it.sg = s.sg + (int64_t)it.slot * s.gp_vol;
   it.overlay = s.overlay;
   it.log = s.log ? s.log + ((int64_t)it.slot * s.n_patches + it.patch) * c->log_stride : nullptr;
+  it.counts = s.counts ? s.counts + ((int64_t)it.slot * s.n_patches + it.patch) * a.ti.F *
+                                        ((D == 3) ? a.ti.Tj * a.ti.Tj * a.ti.Tj : a.ti.Tj * a.ti.Tj)
+                       : nullptr;
   return it;
 }
 

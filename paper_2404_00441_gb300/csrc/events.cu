@@ -118,6 +118,27 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   if (my_known) atomicAdd(&cnt[0], my_known);
   if (my_const) atomicAdd(&cnt[1], my_const);
   if (my_mask) atomicAdd(&cnt[2], my_mask);
+  if (MODE == kModeSim && it.counts)
+    for (int i = tid; i < t.F * ncells; i += kThreads) it.counts[i] = (uint8_t)counts[i];
+  {
+    uint8_t* rc = rec + a.ev.counts_off;
+    for (int i = tid; i < t.F * ncells; i += kThreads) rc[i] = (uint8_t)min(counts[i], 255);
+  }
+  __syncthreads();
+  // overlap strips fully known (2D): the mask type of the learned proposal
+  if (D == 2 && tid < 4) {
+    const int Oj = a.Oj;
+    bool full = Oj > 0;
+    for (int k = 0; k < Oj * Tj && full; ++k) {
+      const int along = k / Tj, across = k % Tj;
+      const int ux = (tid == 0) ? along : (tid == 1) ? Tj - 1 - along : across;
+      const int uy = (tid == 2) ? along : (tid == 3) ? Tj - 1 - along : across;
+      int c = 0;
+      for (int f = 0; f < t.F; ++f) c += counts[f * ncells + ux + Tj * uy];
+      full = (c == t.sd);
+    }
+    if (full) atomicOr(&cnt[5], 1 << tid);
+  }
   __syncthreads();
   // chunk masks of the template rows and the weights, to the record
   for (int row = tid; row < rows; row += kThreads) {
@@ -173,6 +194,8 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     meta[kEvConst] = cnt[1];
     meta[kEvMaskCells] = cnt[2];
     meta[kEvNHd] = min(cnt[3], a.ev.hd_cap);
+    meta[kEvMaskType] = cnt[5];
+    meta[kEvResolved] = 0;
     const int bad = cnt[4] | (cnt[3] > a.ev.hd_cap ? kStatusHdOverflow : 0);
     if (bad) atomicOr(a.status, bad);
   }
@@ -247,7 +270,7 @@ cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3],
 }
 
 int events_smem_bytes(int nch, int rows, int TjP, int F, int ncells) {
-  return nch * rows * TjP * 4 + 32 + F * ncells * 4;
+  return nch * rows * TjP * 4 + 32 + F * ncells * 4;   // cnt[8] then the counts
 }
 
 template <int D, int MODE>

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     if (tid == 0) val = pk;
     else if (tid == 1) val = key_score(sel);
     else if (tid == 2) val = key_mis(sel);
-    else if (tid == 3) val = CCW_LOG_FLAG_DONE;
+    else if (tid == 3) val = CCW_LOG_FLAG_DONE | (em[kEvResolved] ? CCW_LOG_FLAG_PROPOSAL : 0);
     else val = (tid - 4 < Kp) ? key_index(topk[tid - 4]) : -1;
     e[tid] = val;
   }

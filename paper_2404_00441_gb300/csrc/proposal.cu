@@ -1,0 +1,499 @@
+// proposal.cu -- inference of the learned proposal (not part of the paper):
+// embed each data event with the encoder, propose the n_prop TI candidates
+// whose embedding (under the same overlap mask type) is nearest, re-rank the
+// proposals with the exact masked CCF of Eq. CCW and the hard-data
+// mismatches, and settle the item when the proposals' embedding scores are
+// well separated; otherwise the item falls back to the full search.
+#include <algorithm>
+
+#include "device_util.cuh"
+
+namespace ccw {
+
+constexpr int kEncThreads = 256;
+constexpr int kEncMaxTj = 16;
+
+struct EncShape {
+  int C, tj, h2, h3, flat;
+  int o_w1, o_b1, o_w2, o_b2, o_w3, o_b3, o_wf, o_bf;
+};
+
+__host__ __device__ inline EncShape enc_shape(int C, int tj) {
+  EncShape s;
+  s.C = C;
+  s.tj = tj;
+  s.h2 = (tj - 1) / 2 + 1;
+  s.h3 = (s.h2 - 1) / 2 + 1;
+  s.flat = 32 * s.h3 * s.h3;
+  int o = 0;
+  s.o_w1 = o; o += 32 * C * 9;
+  s.o_b1 = o; o += 32;
+  s.o_w2 = o; o += 32 * 32 * 9;
+  s.o_b2 = o; o += 32;
+  s.o_w3 = o; o += 32 * 32 * 9;
+  s.o_b3 = o; o += 32;
+  s.o_wf = o; o += 64 * s.flat;
+  s.o_bf = o;
+  return s;
+}
+
+// Is level-J cell (ux, uy) inside the overlap strips of mask type `type`?
+__device__ __forceinline__ bool in_mask(int type, int ux, int uy, int Tj, int Oj) {
+  return ((type & 1) && ux < Oj) || ((type & 2) && ux >= Tj - Oj) || ((type & 4) && uy < Oj) ||
+         ((type & 8) && uy >= Tj - Oj);
+}
+
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Overlap mask type of a data event from its block counts (2D): bit k set
+// when strip k (0 low x, 1 high x, 2 low y, 3 high y; Oj blocks wide) is
+// fully known, i.e. every block holds 2^(2J) known cells.
+__device__ inline int mask_type_of(const uint8_t* cnt, int F, int Tj, int Oj, int sd) {
+  if (Oj <= 0) return 0;
+  int type = 0;
+  for (int k = 0; k < 4; ++k) {
+    bool full = true;
+    for (int i = 0; i < Oj * Tj && full; ++i) {
+      const int along = i / Tj, across = i % Tj;
+      const int ux = (k == 0) ? along : (k == 1) ? Tj - 1 - along : across;
+      const int uy = (k == 2) ? along : (k == 3) ? Tj - 1 - along : across;
+      int c = 0;
+      for (int f = 0; f < F; ++f) c += cnt[f * Tj * Tj + ux + Tj * uy];
+      full = (c == sd);
+    }
+    if (full) type |= 1 << k;
+  }
+  return type;
+}
+
+// Proposals exist only for a non-empty mask of strips with at most one
+// strip per axis (the shapes a raster or mirrored raster path produces).
+__device__ __forceinline__ bool usable_type(int type) {
+  return type != 0 && (type & 3) != 3 && (type & 12) != 12;
+}
+
+// Encoder input of TI candidate c under mask type `type`: facies counts of
+// the level-J blocks inside the mask divided by 2^(d J), zero outside.
+__device__ inline void window_input(const TiDev& t, int Oj, int type, int64_t c, float* x,
+                                    int tid, int nthreads, bool round) {
+  const int C = t.F, tj = t.Tj;
+  const int cx = (int)(c % t.cd[0]), cy = (int)(c / t.cd[0]);
+  const float inv = 1.f / (float)t.sd;
+  for (int u = tid; u < tj * tj; u += nthreads) {
+    const int ux = u % tj, uy = u / tj;
+    const bool m = in_mask(type, ux, uy, tj, Oj);
+    float rest = (float)t.sd;
+    for (int f = 0; f < C - 1; ++f) {
+      const float v =
+          m ? t.planes[(int64_t)f * t.plane_vol + (cx + ux) + (int64_t)t.px * (cy + uy)] : 0.f;
+      x[f * tj * tj + u] = round ? bf(v * inv) : v * inv;
+      rest -= v;
+    }
+    x[(C - 1) * tj * tj + u] = m ? (round ? bf(rest * inv) : rest * inv) : 0.f;
+  }
+}
+
+// One CTA per sample: conv1, conv2, conv3, linear, L2 normalisation in
+// shared memory, BF16-rounded weights and activations as in training.
+// Source: the data events of the step's items (SRC 0) or the candidate
+// windows of the TI under mask type `type` (SRC 1, sample = candidate).
+template <int SRC>
+__global__ void __launch_bounds__(kEncThreads)
+    k_encode(const __grid_constant__ WaveArgs a, int type, int64_t c0, int n,
+             float* __restrict__ out_f32, __nv_bfloat16* __restrict__ out_bf16) {
+  extern __shared__ float sh[];
+  const TiDev& t = a.ti;
+  const int C = t.F, tj = t.Tj;
+  const EncShape s = enc_shape(C, tj);
+  float* x = sh;                                   // [C][tj][tj]
+  float* a1 = x + C * tj * tj;                     // [32][tj][tj]
+  float* a2 = a1 + 32 * tj * tj;                   // [32][h2][h2]
+  float* a3 = a2 + 32 * s.h2 * s.h2;               // [32][h3][h3]
+  float* z = a3 + s.flat;                          // [64]
+  __shared__ float red[2];
+  const int tid = threadIdx.x;
+  const int sample = blockIdx.x;
+  if (sample >= n) return;
+  const float inv = 1.f / (float)t.sd;
+  if (SRC == 0) {
+    pdl_trigger();
+    pdl_wait();
+    const unsigned char* rec = a.ev.base + (int64_t)sample * a.ev.stride;
+    const int* meta = reinterpret_cast<const int*>(rec);
+    if (meta[kEvKnown] == 0) return;
+    const uint8_t* cnt = rec + a.ev.counts_off;
+    for (int i = tid; i < C * tj * tj; i += kEncThreads) x[i] = bf(cnt[i] * inv);
+  } else {
+    window_input(t, a.Oj, type, c0 + sample, x, tid, kEncThreads, true);
+  }
+  __syncthreads();
+  const float* P = a.net;
+  // conv1 (stride 1), conv2, conv3 (stride 2), ReLU
+  auto conv = [&](const float* in, int Ci, int H, float* outp, int Ho, int stride, int ow,
+                  int ob) {
+    for (int o = tid; o < 32 * Ho * Ho; o += kEncThreads) {
+      const int ox = o % Ho, oy = (o / Ho) % Ho, co = o / (Ho * Ho);
+      float acc = P[ob + co];
+      for (int ci = 0; ci < Ci; ++ci)
+        for (int ky = 0; ky < 3; ++ky) {
+          const int iy = oy * stride + ky - 1;
+          if (iy < 0 || iy >= H) continue;
+          for (int kx = 0; kx < 3; ++kx) {
+            const int ix = ox * stride + kx - 1;
+            if (ix < 0 || ix >= H) continue;
+            acc += bf(__ldg(P + ow + ((co * Ci + ci) * 3 + ky) * 3 + kx)) * in[(ci * H + iy) * H + ix];
+          }
+        }
+      outp[o] = bf(fmaxf(acc, 0.f));
+    }
+    __syncthreads();
+  };
+  conv(x, C, tj, a1, tj, 1, s.o_w1, s.o_b1);
+  conv(a1, 32, tj, a2, s.h2, 2, s.o_w2, s.o_b2);
+  conv(a2, 32, s.h2, a3, s.h3, 2, s.o_w3, s.o_b3);
+  for (int j = tid; j < 64; j += kEncThreads) {
+    float acc = P[s.o_bf + j];
+    for (int k = 0; k < s.flat; ++k) acc += bf(__ldg(P + s.o_wf + j * s.flat + k)) * a3[k];
+    z[j] = acc;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    float q = z[tid] * z[tid] + z[tid + 32] * z[tid + 32];
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (tid == 0) red[0] = sqrtf(fmaxf(q, 1e-24f));
+  }
+  __syncthreads();
+  if (tid < 64) {
+    const float e = z[tid] / red[0];
+    if (SRC == 0) out_f32[(int64_t)sample * 64 + tid] = e;
+    else out_bf16[((int64_t)type * t.P + c0 + sample) * 64 + tid] = __float2bfloat16_rn(e);
+  }
+}
+
+int encode_smem_bytes(int C, int tj) {
+  const EncShape s = enc_shape(C, tj);
+  return 4 * (C * tj * tj + 32 * tj * tj + 32 * s.h2 * s.h2 + s.flat + 64);
+}
+
+// ---------------------------------------------------------------------------
+// Nearest neighbours: scores s_c = table[type][c] . e over every candidate,
+// the n_prop best by (score desc, index asc), and the relative gap
+// (s_1 - s_nprop) / max(|s_1|, eps). A two-level histogram over [-1, 1]
+// finds a threshold that keeps at least n_prop and at most kCollect
+// candidates; those are ranked exactly.
+// ---------------------------------------------------------------------------
+constexpr int kNnThreads = 256;
+constexpr int kBins = 1024;
+constexpr int kCollect = 512;
+
+__device__ __forceinline__ float nn_score(const __nv_bfloat16* row, const float* e) {
+  float s = 0.f;
+#pragma unroll 8
+  for (int k = 0; k < 64; k += 2) {
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(row + k);
+    s = fmaf(__bfloat162float(v.x), e[k], s);
+    s = fmaf(__bfloat162float(v.y), e[k + 1], s);
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ WaveArgs a) {
+  __shared__ float e[64];
+  __shared__ int hist[kBins];
+  __shared__ float cs[kCollect];
+  __shared__ int ci[kCollect];
+  __shared__ int sh_i[4];
+  __shared__ float sh_f[4];
+  const TiDev& t = a.ti;
+  const int tid = threadIdx.x;
+  const int item = blockIdx.x;
+  pdl_trigger();
+  pdl_wait();
+  const int* meta = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+  const int type = meta[kEvMaskType];
+  const bool known = meta[kEvKnown] > 0;
+  unsigned long long* stats = a.call ? a.call->learn_stats : nullptr;
+  if (!known || !usable_type(type)) {
+    if (tid == 0) {
+      a.prop_gap[item] = -1.f;   // no proposals: full search
+      if (stats && known) atomicAdd(&stats[0], 1ull);
+    }
+    return;
+  }
+  if (tid == 0 && stats) {
+    atomicAdd(&stats[0], 1ull);
+    atomicAdd(&stats[1], 1ull);
+  }
+  if (tid < 64) e[tid] = a.emb[(int64_t)item * 64 + tid];
+  for (int b = tid; b < kBins; b += kNnThreads) hist[b] = 0;
+  __syncthreads();
+  const __nv_bfloat16* tab = a.tables + (int64_t)type * t.P * 64;
+  const int np = (int)min((int64_t)a.n_prop, t.P);
+  // Threshold search: a histogram of the scores over [lo, hi] (two levels)
+  // gives a score thr with at least np candidates at or above it and, when
+  // possible, at most kCollect. The exact ranking below checks both counts,
+  // so rounding in the binning can only cost a fallback, never a wrong list.
+  float lo = -1.5f, hi = 1.5f;
+  int above_prev = 0;
+  float thr = lo;
+  for (int level = 0; level < 2; ++level) {
+    const float scale = kBins / (hi - lo);
+    for (int64_t c = tid; c < t.P; c += kNnThreads) {
+      const float sc = nn_score(tab + c * 64, e);
+      if (sc < lo || sc >= hi) continue;
+      const int b = min(kBins - 1, max(0, (int)((sc - lo) * scale)));
+      atomicAdd(&hist[b], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int above = above_prev;
+      int b = kBins - 1;
+      for (; b > 0; --b) {
+        if (above + hist[b] >= np) break;
+        above += hist[b];
+      }
+      sh_i[0] = b;
+      sh_i[1] = above;   // scores in bins above b (and above the window)
+      sh_i[2] = hist[b];
+    }
+    __syncthreads();
+    const int bsel = sh_i[0], above = sh_i[1], inbin = sh_i[2];
+    thr = lo + bsel / scale;
+    if (above + inbin <= kCollect || level == 1) break;
+    // refine inside the selected bin
+    const float nlo = thr, nhi = lo + (bsel + 1) / scale;
+    above_prev = above;
+    __syncthreads();
+    for (int bb = tid; bb < kBins; bb += kNnThreads) hist[bb] = 0;
+    __syncthreads();
+    lo = nlo;
+    hi = nhi;
+  }
+  if (tid == 0) sh_i[3] = 0;
+  __syncthreads();
+  for (int64_t c = tid; c < t.P; c += kNnThreads) {
+    const float sc = nn_score(tab + c * 64, e);
+    if (sc >= thr) {
+      const int k = atomicAdd(&sh_i[3], 1);
+      if (k < kCollect) {
+        cs[k] = sc;
+        ci[k] = (int)c;
+      }
+    }
+  }
+  __syncthreads();
+  const int total = sh_i[3];
+  const int ncoll = min(total, kCollect);
+  if (total > kCollect || ncoll < np) {
+    if (tid == 0) a.prop_gap[item] = -1.f;   // threshold not usable: full search
+    return;
+  }
+  // exact rank of each collected candidate: score desc, index asc
+  for (int k = tid; k < ncoll; k += kNnThreads) {
+    int rank = 0;
+    for (int j = 0; j < ncoll; ++j)
+      rank += (cs[j] > cs[k]) || (cs[j] == cs[k] && ci[j] < ci[k]);
+    if (rank < np) a.prop[(int64_t)item * a.n_prop + rank] = ci[k];
+    if (rank == 0) sh_f[1] = cs[k];
+    if (rank == np - 1) sh_f[2] = cs[k];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const float s1 = sh_f[1], sn = sh_f[2];
+    a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+  }
+}
+
+// Event records from explicit block counts (the query entry point): known
+// cells, mask type and counts, as the event kernel writes them.
+__global__ void k_records_from_counts(const __grid_constant__ WaveArgs a, const uint8_t* counts,
+                                      int32_t* type_out) {
+  __shared__ int red[kWarps];
+  const TiDev& t = a.ti;
+  const int tid = threadIdx.x, item = blockIdx.x;
+  const int nc = t.F * t.Tj * t.Tj;
+  const uint8_t* src = counts + (int64_t)item * nc;
+  unsigned char* rec = a.ev.base + (int64_t)item * a.ev.stride;
+  int known = 0;
+  for (int i = tid; i < nc; i += blockDim.x) {
+    const uint8_t v = src[i];
+    rec[a.ev.counts_off + i] = v;
+    known += v;
+  }
+  for (int o = 16; o > 0; o >>= 1) known += __shfl_xor_sync(0xffffffffu, known, o);
+  if ((tid & 31) == 0) red[tid >> 5] = known;
+  __syncthreads();
+  if (tid == 0) {
+    int k = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) k += red[w];
+    int* meta = reinterpret_cast<int*>(rec);
+    const int type = mask_type_of(src, t.F, t.Tj, a.Oj, t.sd);
+    meta[kEvKnown] = k;
+    meta[kEvMaskType] = type;
+    meta[kEvResolved] = 0;
+    if (type_out) type_out[item] = type;
+  }
+}
+
+// Encoder inputs for training: what 0 from block counts, 1 TI windows.
+__global__ void k_inputs(const __grid_constant__ WaveArgs a, int what, const uint8_t* counts,
+                         const int32_t* cand, int32_t* type, int n, float* out) {
+  const TiDev& t = a.ti;
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int nc = t.F * t.Tj * t.Tj;
+  float* x = out + (int64_t)i * nc;
+  if (what == 0) {
+    const uint8_t* src = counts + (int64_t)i * nc;
+    const float inv = 1.f / (float)t.sd;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) x[k] = src[k] * inv;
+    if (threadIdx.x == 0 && type) type[i] = mask_type_of(src, t.F, t.Tj, a.Oj, t.sd);
+  } else {
+    const int ty = type[i];
+    const int64_t c = cand[i];
+    if (c < 0 || c >= t.P || ty < 0 || ty > 15) {   // out of range: zeros
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) x[k] = 0.f;
+      return;
+    }
+    window_input(t, a.Oj, ty, c, x, threadIdx.x, blockDim.x, false);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-rank of the proposals (Eq. CCW on the level-J weights of the
+// event record, hard-data mismatches of Sec. 4.4), K best by the ranking
+// key. Settles the item (per-part lists for the finish kernel, resolved
+// flag) when the embedding gap is at least gap_theta.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_rerank(const __grid_constant__ WaveArgs a) {
+  __shared__ uint64_t keys[CCW_MAX_TOPK];
+  __shared__ uint64_t red[9];
+  const TiDev& t = a.ti;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int item = blockIdx.x;
+  pdl_trigger();
+  pdl_wait();
+  unsigned char* rec = a.ev.base + (int64_t)item * a.ev.stride;
+  int* meta = reinterpret_cast<int*>(rec);
+  const float gap = a.prop_gap[item];
+  // gap < 0: no proposals were written for this item
+  if (meta[kEvKnown] == 0 || gap < 0.f || gap < a.call->gap_theta) return;
+  const int np = (int)min((int64_t)a.n_prop, t.P);
+  const int K = a.K;
+  const int Kp = (int)min((int64_t)K, (int64_t)np);
+  const float* W = reinterpret_cast<const float*>(rec + a.ev.w_off);
+  const int2* hdl = reinterpret_cast<const int2*>(rec + a.ev.hd_off);
+  const int nhd = meta[kEvNHd], cons = meta[kEvConst];
+  // 4 threads per proposal, rows split among them
+  const int pi = tid >> 2, part = tid & 3;
+  uint64_t key = kNoKey;
+  float acc = 0.f;
+  int c = -1;
+  if (pi < np) {
+    c = a.prop[(int64_t)item * a.n_prop + pi];
+    const int cx = c % t.cd[0], cy = c / t.cd[0];
+    for (int ch = 0; ch < t.nch; ++ch) {
+      const float* plane = t.planes + (int64_t)(t.plane0 + ch) * t.plane_vol;
+      for (int row = part; row < t.rows; row += 4) {
+        const float* wr = W + (ch * t.rows + row) * t.TjP;
+        const float* pr = plane + (cx) + (int64_t)t.px * (cy + row);
+        for (int ux = 0; ux < t.Tj; ++ux) acc = fmaf(wr[ux], __ldg(pr + ux), acc);
+      }
+    }
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (pi < np && part == 0) {
+    const uint8_t* tb = t.ti + (int64_t)t.s * (c % t.cd[0]) +
+                        (int64_t)t.n[0] * ((int64_t)t.s * (c / t.cd[0]));
+    int mis = 0;
+    for (int k = 0; k < nhd; ++k) {
+      const int2 e = hdl[k];
+      mis += (__ldg(tb + e.x) != (uint8_t)(e.y & 0xFF));
+    }
+    key = make_key(mis, __float2int_rn(acc) + cons, c);
+  }
+  // K smallest keys of the proposals
+  uint64_t prev = 0;
+  for (int r = 0; r < Kp; ++r) {
+    uint64_t m = (r == 0 || key > prev) ? key : kNoKey;
+    m = warp_min_u64(m);
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = lane < 8 ? red[lane] : kNoKey;
+      w = warp_min_u64(w);
+      if (lane == 0) red[8] = w;
+    }
+    __syncthreads();
+    prev = red[8];
+    if (tid == 0) keys[r] = prev;
+    __syncthreads();
+  }
+  // the item's lists: the proposals' K best in the first part, empty others
+  unsigned long long* dst = a.part + (int64_t)item * a.n_parts * K;
+  for (int i = tid; i < a.n_parts * K; i += 256) {
+    const int p = i / K, r = i % K;
+    dst[i] = (p == 0 && r < Kp) ? keys[r] : kNoKey;
+  }
+  if (tid == 0) {
+    meta[kEvResolved] = 1;
+    if (a.call->learn_stats) atomicAdd(&a.call->learn_stats[2], 1ull);
+  }
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t encode_set_smem(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_encode<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_encode<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_encode_items(const WaveArgs& a, bool pdl, cudaStream_t st) {
+  const int smem = encode_smem_bytes(a.ti.F, a.ti.Tj);
+  return launch_pdl(k_encode<0>, dim3(a.n_items), dim3(kEncThreads), smem, st, pdl, a, 0,
+                    (int64_t)0, a.n_items, a.emb, (__nv_bfloat16*)nullptr);
+}
+
+cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables,
+                                 cudaStream_t st) {
+  const int smem = encode_smem_bytes(a.ti.F, a.ti.Tj);
+  for (int64_t c0 = 0; c0 < a.ti.P; c0 += 65535) {
+    const int n = (int)std::min<int64_t>(65535, a.ti.P - c0);
+    k_encode<1><<<n, kEncThreads, smem, st>>>(a, type, c0, n, nullptr, tables);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st) {
+  return launch_pdl(k_nnsel, dim3(a.n_items), dim3(kNnThreads), 0, st, pdl, a);
+}
+
+cudaError_t launch_records_from_counts(const WaveArgs& a, const uint8_t* counts,
+                                      int32_t* type_out, cudaStream_t st) {
+  k_records_from_counts<<<a.n_items, 256, 0, st>>>(a, counts, type_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inputs(const WaveArgs& a, int what, const uint8_t* counts, const int32_t* cand,
+                          int32_t* type, int n, float* out, cudaStream_t st) {
+  for (int i0 = 0; i0 < n; i0 += 65535) {
+    const int c = std::min(65535, n - i0);
+    const int nc = a.ti.F * a.ti.Tj * a.ti.Tj;
+    k_inputs<<<c, 128, 0, st>>>(a, what, counts ? counts + (int64_t)i0 * nc : nullptr,
+                                cand ? cand + i0 : nullptr, type ? type + i0 : nullptr, c,
+                                out + (int64_t)i0 * nc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st) {
+  return launch_pdl(k_rerank, dim3(a.n_items), dim3(256), 0, st, pdl, a);
+}
+
+}  // namespace ccw

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       m.x = em[kEvKnown];
       m.y = em[kEvConst];
       m.z = em[kEvNHd];
-      m.w = (MODE == kModeMap) ? 1 : (m.x > 0);
+      m.w = (MODE == kModeMap) ? 1 : (m.x > 0 && !em[kEvResolved]);
     }
     meta[i] = m;
   }
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       const int item = ntile * nt + i;
       if (item >= a.n_items) continue;
       const int* em = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
-      if (em[kEvKnown] <= 0) continue;
+      if (em[kEvKnown] <= 0 || em[kEvResolved]) continue;
       atomicAdd(&work[0], (unsigned long long)t.P);
       atomicAdd(&work[1], (unsigned long long)t.P * em[kEvMaskCells] * nch);
     }

@@ -71,6 +71,13 @@ def workload(name: str) -> dict:
         cells, vals = synth.sample_hard_data(hd_field_3d(100, 100, 100), 1000, seed=8)
         return dict(name="c4b", ti=tube_ti_3d(), F=4, J=1, T=24, O=6, K=5,
                     grid=(100, 100, 100), n_real=8, hd=(cells, vals), seed=4)
+    if name == "c4":
+        # the mixed-size batch: both grid sizes advance in one call
+        a, b = workload("c4a"), workload("c4b")
+        b["real_base"] = a["n_real"]
+        a["real_base"] = 0
+        return dict(name="c4", ti=a["ti"], F=4, J=1, T=24, O=6, K=5, groups=[a, b], seed=4,
+                    grid=None, n_real=a["n_real"] + b["n_real"], hd=None)
     if name == "c5":
         return dict(name="c5", ti=ribbon_ti_250(), F=2, J=2, T=48, O=12, K=1,
                     grid=(512, 512), n_real=256, hd=None, seed=5)
