@@ -76,7 +76,32 @@ def parse_args():
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP32 FMA lanes, 1 FP16 tensor cores, 2 BF16 tensor cores "
                          "(default: 1 for 2D workloads, 0 for 3D)")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned proposal (2D): train the encoder on pairs from plain runs "
+                         "before timing, calibrate the gap threshold on held-out pairs")
+    ap.add_argument("--train-real", type=int, default=1024,
+                    help="plain realizations that generate the training pairs")
+    ap.add_argument("--train-steps", type=int, default=600)
+    ap.add_argument("--target-miss", type=float, default=0.02)
     return ap.parse_args()
+
+
+def shard_real_base(rank: int, total_real: int, group_base: int) -> int:
+    """First realization id of a group on `rank`: ranks own disjoint id
+    ranges [rank * total_real, (rank + 1) * total_real), so every rank draws
+    different Philox streams and no exchange is needed."""
+    return rank * total_real + group_base
+
+
+def max_over_ranks(values, world: int, device: str):
+    """Element-wise max of a list of floats over all ranks (the job's time is
+    that of its slowest rank)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
 
 
 def n_patches_of(grid, T, O):
@@ -201,6 +226,35 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ ours ---
+def train_proposal(args, ti, w, grid):
+    """Trains the proposal encoder on the GPU from plain runs of the same
+    geometry (not timed) and attaches it with a calibrated gap threshold."""
+    import torch
+
+    import paper_2404_00441_gb300 as ccw
+    from paper_2404_00441_gb300 import proposal as PR
+    t0 = time.time()
+    tj = w["T"] // (2 ** w["J"])
+    cnt_tr, best_tr = PR.generate_pairs(ti, grid, args.train_real, seed=1000)
+    cnt_te, best_te = PR.generate_pairs(ti, grid, max(args.train_real // 16, 8), seed=2000)
+    net = ccw.Net(w["F"], tj, seed=1)
+    losses = PR.train(ti, net, cnt_tr, best_tr, args.train_steps, log_every=max(
+        args.train_steps // 4, 1))
+    ti.attach_proposal(net, 64, 0.0)
+    hit, gap, _ = PR.proposal_hits(ti, cnt_te, best_te)
+    theta = PR.calibrate_gap(hit, gap, args.target_miss)
+    ti.attach_proposal(net, 64, theta)
+    ok = gap >= 0
+    settled = ok & (gap >= theta)
+    miss = float((~hit[settled]).float().mean().item()) if settled.any() else 0.0
+    torch.cuda.synchronize()
+    return {"train_pairs": int(cnt_tr.shape[0]), "train_steps": args.train_steps,
+            "loss_first_last": [losses[0], losses[-1]], "n_prop": 64, "theta": theta,
+            "target_miss": args.target_miss, "held_out_miss_of_settled": miss,
+            "held_out_settled_frac": float(settled.float().mean().item()),
+            "prep_s": time.time() - t0}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -221,13 +275,16 @@ def run_ours(args, rank, world, local_rank):
         hd = s["hd"]
         groups.append(dict(
             grid=tuple(s["grid"]), n_real=s["n_real"],
-            real_base=rank * total_real + s.get("real_base", 0),
+            real_base=shard_real_base(rank, total_real, s.get("real_base", 0)),
             hd_cells=None if hd is None else torch.from_numpy(hd[0]).cuda(),
             hd_vals=None if hd is None else torch.from_numpy(hd[1]).cuda(),
             hd_host=hd))
     ndim = len(groups[0]["grid"])
     precision = args.precision if args.precision is not None else (1 if ndim == 2 else 0)
     cells_per_step = sum(gr["n_real"] * cells_of(gr["grid"]) for gr in groups)
+    learned_info = None
+    if args.learned:
+        learned_info = train_proposal(args, g, w, groups[0]["grid"])
     outs = [torch.empty((gr["n_real"],) + gr["grid"][::-1], dtype=torch.uint8, device="cuda")
             for gr in groups]
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -239,12 +296,14 @@ def run_ours(args, rank, world, local_rank):
             gr = groups[0]
             ccw.simulate(g, gr["grid"], n_real=gr["n_real"], topk=w["K"], seed=w["seed"],
                          hd_cells=hd_dev[0][0], hd_vals=hd_dev[0][1],
-                         real_base=gr["real_base"], out=outs[0], precision=precision)
+                         real_base=gr["real_base"], out=outs[0], precision=precision,
+                         learned=1 if args.learned else 0)
             return outs
         res = ccw.simulate_groups(
             g, [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
                      hd_cells=h[0], hd_vals=h[1]) for gr, h in zip(groups, hd_dev)],
-            topk=w["K"], seed=w["seed"], precision=precision)
+            topk=w["K"], seed=w["seed"], precision=precision,
+            learned=1 if args.learned else 0)
         return [r[0] for r in res]
 
     for _ in range(max(args.warmup, 0)):
@@ -273,6 +332,10 @@ def run_ours(args, rank, world, local_rank):
         total_ms += e0.elapsed_time(e1)
     barrier()
     launches = ccw.launch_count() - launches0
+    if learned_info is not None:
+        n_known, n_prop, n_settled = g.proposal_stats()
+        learned_info["settled_frac"] = n_settled / max(n_known, 1)
+        learned_info["with_proposals_frac"] = n_prop / max(n_known, 1)
     ccw.profile_enable(False)
     n_launch, kern_ms, cand_evals, macs = ccw.profile_read()
     clk = clocks.stop()
@@ -315,10 +378,8 @@ def run_ours(args, rank, world, local_rank):
             e2e_ms += e0.elapsed_time(e1)
         barrier()
 
-    t = torch.tensor([total_ms, e2e_ms or 0.0, kern_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms_max, kern_ms_max = (float(v) for v in t.tolist())
+    total_ms, e2e_ms_max, kern_ms_max = max_over_ranks([total_ms, e2e_ms or 0.0, kern_ms], world,
+                                                       "cuda")
     if rank != 0:
         return
     cells = cells_per_step * world * args.steps
@@ -353,6 +414,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if learned_info is not None:
+        line["config"]["learned"] = learned_info
     if e2e_ms:
         line["e2e"] = {"value": cells / (e2e_ms_max / 1e3), "unit": "cells/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}

@@ -45,11 +45,11 @@ cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3],
                               const int32_t* origins, uint8_t* grid, const int gdim[3],
                               int* status, cudaStream_t st);
 // proposal.cu
-int encode_smem_bytes(int C, int tj);
-cudaError_t encode_set_smem(int smem);
-cudaError_t launch_encode_items(const WaveArgs& a, bool pdl, cudaStream_t st);
-cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables,
-                                 cudaStream_t st);
+cudaError_t launch_round_weights(float* p, int C, int tj, cudaStream_t st);
+cudaError_t launch_encode_items(const WaveArgs& a, float* x, float* act, bool pdl,
+                                cudaStream_t st);
+cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables, float* x,
+                                 float* act, float* emb, int chunk, cudaStream_t st);
 cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st);
 cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st);
 cudaError_t launch_records_from_counts(const WaveArgs& a, const uint8_t* counts,
@@ -58,6 +58,7 @@ cudaError_t launch_inputs(const WaveArgs& a, int what, const uint8_t* counts, co
                           int32_t* type, int n, float* out, cudaStream_t st);
 // learned.cu
 void net_view(const ccw_net* n, int* C, int* tj, const float** params, int64_t* count);
+int64_t infer_act_floats(int C, int tj);
 }  // namespace ccw
 
 using namespace ccw;
@@ -152,6 +153,8 @@ struct SimPlan {
   void* emb = nullptr;       // learned proposal: [max_items][64] item embeddings
   void* prop = nullptr;      // [max_items][n_prop] proposals
   void* prop_gap = nullptr;  // [max_items] relative embedding gaps
+  void* enc_x = nullptr;     // encoder inputs and activations of a step
+  void* enc_act = nullptr;
   CallDev* call = nullptr;
   SimGroup* dgroups = nullptr;
   EvDev evl;
@@ -178,6 +181,8 @@ struct SimPlan {
     cudaFree(emb);
     cudaFree(prop);
     cudaFree(prop_gap);
+    cudaFree(enc_x);
+    cudaFree(enc_act);
     cudaFree(call);
     cudaFree(dgroups);
     release_cp();
@@ -1008,7 +1013,11 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
         (e = cudaMalloc(&pl->prop, sizeof(int) * (size_t)pl->n_prop * pl->max_items)) !=
             cudaSuccess ||
         (e = cudaMalloc(&pl->prop_gap, sizeof(float) * (size_t)pl->max_items)) !=
-            cudaSuccess)) ||
+            cudaSuccess ||
+        (e = cudaMalloc(&pl->enc_x, sizeof(float) * (size_t)t->F * t->Tj * t->Tj *
+                                        pl->max_items)) != cudaSuccess ||
+        (e = cudaMalloc(&pl->enc_act, sizeof(float) * (size_t)infer_act_floats(t->F, t->Tj) *
+                                          pl->max_items)) != cudaSuccess)) ||
       (e = cudaMalloc((void**)&pl->call, sizeof(CallDev))) != cudaSuccess ||
       (e = cudaMalloc((void**)&pl->dgroups, sizeof(SimGroup) * n_groups)) != cudaSuccess) {
     delete pl;
@@ -1044,6 +1053,8 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
     a.emb = (float*)pl->emb;
     a.prop = (int*)pl->prop;
     a.prop_gap = (float*)pl->prop_gap;
+    a.enc_x = (float*)pl->enc_x;
+    a.enc_act = (float*)pl->enc_act;
   }
   const CcfPlan& cp = *static_cast<const CcfPlan*>(pl->cp);
   size_t pe = 0;
@@ -1058,7 +1069,7 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
       if (pl->learned) {
         // learned proposal: embed, nearest windows, exact re-rank; the CCF
         // kernel then skips the items the proposal settled
-        if ((e = launch_encode_items(c, true, st)) != cudaSuccess ||
+        if ((e = launch_encode_items(c, c.enc_x, c.enc_act, true, st)) != cudaSuccess ||
             (e = launch_nnsel(c, true, st)) != cudaSuccess ||
             (e = launch_rerank(c, true, st)) != cudaSuccess)
           return cuda_fail(e, "proposal kernel launch");
@@ -1203,7 +1214,7 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if ((e = cudaGraphLaunch(pl->exec[gi], st)) != cudaSuccess) return cuda_fail(e, "graph launch");
   int64_t wave_launches = 0;
   for (int w = 0; w < pl->n_waves; ++w)
-    wave_launches += (pl->learned ? 6 : 3) *
+    wave_launches += (pl->learned ? 11 : 3) *
                      ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
   g_launches += wave_launches;
   for (int i = 0; i < n_groups; ++i) {
@@ -1244,8 +1255,6 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
 // counterpart).
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kEncMaxSmem = 200 * 1024;
-
 bool usable_mask_type(int type) { return type != 0 && (type & 3) != 3 && (type & 12) != 12; }
 
 // Minimal event records for the query entry point: meta and block counts.
@@ -1286,9 +1295,6 @@ extern "C" int ccw_ti_attach_proposal(ccw_ti* t, const ccw_net* net, int32_t n_p
   net_view(net, &C, &tj, &params, &count);
   if (C != t->F || tj != t->Tj)
     return fail(CCW_EINVAL, "network shape (%d ch, %d) != TI (F %d, T/2^J %d)", C, tj, t->F, t->Tj);
-  const int smem = encode_smem_bytes(C, tj);
-  if (smem > kEncMaxSmem) return fail(CCW_EINVAL, "template too large for the encoder");
-  if ((e = encode_set_smem(smem)) != cudaSuccess) return cuda_fail(e, "encoder attributes");
   const size_t tab_bytes = sizeof(__nv_bfloat16) * 16 * 64 * (size_t)t->P;
   if ((e = cudaMalloc((void**)&t->d_net, sizeof(float) * count)) != cudaSuccess ||
       (e = cudaMalloc((void**)&t->d_tables, tab_bytes)) != cudaSuccess ||
@@ -1303,20 +1309,36 @@ extern "C" int ccw_ti_attach_proposal(ccw_ti* t, const ccw_net* net, int32_t n_p
   }
   if ((e = cudaMemcpyAsync(t->d_net, params, sizeof(float) * count, cudaMemcpyDeviceToDevice,
                            st)) != cudaSuccess ||
+      (e = launch_round_weights(t->d_net, C, tj, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(t->d_tables, 0, tab_bytes, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(t->d_learn_stats, 0, 3 * sizeof(unsigned long long), st)) !=
           cudaSuccess)
     return cuda_fail(e, "attach proposal");
+  ++g_launches;   // weight rounding
   WaveArgs a;
   fill_ti(t, 0, a);
   a.net = t->d_net;
-  for (int type = 1; type < 16; ++type) {
-    if (!usable_mask_type(type)) continue;
-    if ((e = launch_encode_tables(a, type, t->d_tables, st)) != cudaSuccess)
-      return cuda_fail(e, "proposal table kernel");
-    g_launches += (t->P + 65534) / 65535;
+  // scratch of the table passes, freed at the end
+  const int chunk = (int)std::min<int64_t>(t->P, 16384);
+  float *x = nullptr, *act = nullptr, *emb = nullptr;
+  if ((e = cudaMalloc((void**)&x, sizeof(float) * (size_t)C * tj * tj * chunk)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&act, sizeof(float) * (size_t)infer_act_floats(C, tj) * chunk)) !=
+          cudaSuccess ||
+      (e = cudaMalloc((void**)&emb, sizeof(float) * 64 * (size_t)chunk)) != cudaSuccess) {
+    cudaFree(x);
+    cudaFree(act);
+    return fail(CCW_ENOMEM, "proposal table scratch: %s", cudaGetErrorString(e));
   }
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "proposal tables");
+  for (int type = 1; type < 16 && e == cudaSuccess; ++type) {
+    if (!usable_mask_type(type)) continue;
+    e = launch_encode_tables(a, type, t->d_tables, x, act, emb, chunk, st);
+    g_launches += 7 * ((t->P + chunk - 1) / chunk);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(x);
+  cudaFree(act);
+  cudaFree(emb);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal tables");
   t->n_prop = n_prop;
   t->gap_theta = gap_theta;
   return CCW_OK;
@@ -1336,10 +1358,18 @@ extern "C" int ccw_proposal_query(const ccw_ti* tc, const uint8_t* counts_dev, i
   EvDev ev = query_records(t, nullptr);
   void* rec = nullptr;
   void* emb = nullptr;
+  void* x = nullptr;
+  void* act = nullptr;
   cudaError_t e;
   if ((e = cudaMallocAsync(&rec, (size_t)ev.stride * chunk, st)) != cudaSuccess ||
-      (e = cudaMallocAsync(&emb, sizeof(float) * 64 * (size_t)chunk, st)) != cudaSuccess) {
+      (e = cudaMallocAsync(&emb, sizeof(float) * 64 * (size_t)chunk, st)) != cudaSuccess ||
+      (e = cudaMallocAsync(&x, sizeof(float) * (size_t)t->F * t->Tj * t->Tj * chunk, st)) !=
+          cudaSuccess ||
+      (e = cudaMallocAsync(&act, sizeof(float) * (size_t)infer_act_floats(t->F, t->Tj) * chunk,
+                           st)) != cudaSuccess) {
     if (rec) cudaFreeAsync(rec, st);
+    if (emb) cudaFreeAsync(emb, st);
+    if (x) cudaFreeAsync(x, st);
     return fail(CCW_ENOMEM, "query workspace: %s", cudaGetErrorString(e));
   }
   ev.base = (unsigned char*)rec;
@@ -1358,11 +1388,13 @@ extern "C" int ccw_proposal_query(const ccw_ti* tc, const uint8_t* counts_dev, i
     a.prop_gap = gap_dev + i0;
     if ((e = launch_records_from_counts(a, counts_dev + i0 * nc, type_dev ? type_dev + i0 : nullptr,
                                         st)) != cudaSuccess ||
-        (e = launch_encode_items(a, false, st)) != cudaSuccess ||
+        (e = launch_encode_items(a, (float*)x, (float*)act, false, st)) != cudaSuccess ||
         (e = launch_nnsel(a, false, st)) != cudaSuccess)
       rc = cuda_fail(e, "proposal query kernels");
-    g_launches += 3;
+    g_launches += 8;
   }
+  cudaFreeAsync(act, st);
+  cudaFreeAsync(x, st);
   cudaFreeAsync(emb, st);
   cudaFreeAsync(rec, st);
   return rc;

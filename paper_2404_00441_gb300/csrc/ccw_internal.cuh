@@ -197,6 +197,8 @@ struct WaveArgs {
   const float* net;         // encoder parameters (FP32)
   const __nv_bfloat16* tables;  // [16 mask types][P][64] unit embeddings of TI windows
   float* emb;               // [n_items][64] item embeddings
+  float* enc_x;             // [n_items][F][Tj^2] encoder inputs
+  float* enc_act;           // encoder activations of the step's items
   int* prop;                // [n_items][n_prop] proposals
   float* prop_gap;          // [n_items] relative embedding gap of the proposals
   int n_prop;

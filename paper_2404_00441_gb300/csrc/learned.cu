@@ -595,3 +595,36 @@ void net_view(const ccw_net* n, int* C, int* tj, const float** params, int64_t* 
   *count = n->s.n;
 }
 }  // namespace ccw
+
+namespace ccw {
+// Inference forward pass of the encoder on N samples x [N][C][tj][tj]
+// (BF16 weights and activations, the passes of training with bf16 = 1):
+// act holds N * infer_act_floats(C, tj) floats of scratch, emb receives the
+// unit embeddings [N][64]. Batched over all samples of a step: every layer
+// is one grid-wide launch.
+int64_t infer_act_floats(int C, int tj) {
+  const NetShape s = net_shape(C, tj);
+  return 32LL * tj * tj + 32LL * s.h2 * s.h2 + s.flat + 64 + 1;
+}
+
+cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
+                      float* emb, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const NetShape s = net_shape(C, tj);
+  float* a1 = act;
+  float* a2 = a1 + (int64_t)N * 32 * tj * tj;
+  float* a3 = a2 + (int64_t)N * 32 * s.h2 * s.h2;
+  float* z = a3 + (int64_t)N * s.flat;
+  float* nrm = z + (int64_t)N * 64;
+  k_conv_fwd<<<grid_for((int64_t)N * 32 * tj * tj), 256, 0, st>>>(
+      x, P + s.o_w1, P + s.o_b1, a1, N, C, tj, tj, 32, tj, tj, 1, 1, 1);
+  k_conv_fwd<<<grid_for((int64_t)N * 32 * s.h2 * s.h2), 256, 0, st>>>(
+      a1, P + s.o_w2, P + s.o_b2, a2, N, 32, tj, tj, 32, s.h2, s.h2, 2, 1, 1);
+  k_conv_fwd<<<grid_for((int64_t)N * 32 * s.h3 * s.h3), 256, 0, st>>>(
+      a2, P + s.o_w3, P + s.o_b3, a3, N, 32, s.h2, s.h2, 32, s.h3, s.h3, 2, 1, 1);
+  k_linear_fwd<<<grid_for((int64_t)N * 64), 256, 0, st>>>(a3, P + s.o_wf, P + s.o_bf, z, N,
+                                                          s.flat, 64, 1);
+  k_l2norm_fwd<<<(N + 7) / 8, 256, 0, st>>>(z, emb, nrm, N, 64);
+  return cudaGetLastError();
+}
+}  // namespace ccw

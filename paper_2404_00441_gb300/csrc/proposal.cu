@@ -10,8 +10,9 @@
 
 namespace ccw {
 
-constexpr int kEncThreads = 256;
-constexpr int kEncMaxTj = 16;
+// learned.cu
+cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
+                      float* emb, cudaStream_t st);
 
 struct EncShape {
   int C, tj, h2, h3, flat;
@@ -93,86 +94,51 @@ __device__ inline void window_input(const TiDev& t, int Oj, int type, int64_t c,
   }
 }
 
-// One CTA per sample: conv1, conv2, conv3, linear, L2 normalisation in
-// shared memory, BF16-rounded weights and activations as in training.
-// Source: the data events of the step's items (SRC 0) or the candidate
-// windows of the TI under mask type `type` (SRC 1, sample = candidate).
-template <int SRC>
-__global__ void __launch_bounds__(kEncThreads)
-    k_encode(const __grid_constant__ WaveArgs a, int type, int64_t c0, int n,
-             float* __restrict__ out_f32, __nv_bfloat16* __restrict__ out_bf16) {
-  extern __shared__ float sh[];
+// Encoder inputs of the step's items: the block counts of the event record
+// divided by 2^(d J) (zero for an empty event, which is never searched).
+__global__ void k_event_inputs(const __grid_constant__ WaveArgs a, float* __restrict__ x) {
   const TiDev& t = a.ti;
-  const int C = t.F, tj = t.Tj;
-  const EncShape s = enc_shape(C, tj);
-  float* x = sh;                                   // [C][tj][tj]
-  float* a1 = x + C * tj * tj;                     // [32][tj][tj]
-  float* a2 = a1 + 32 * tj * tj;                   // [32][h2][h2]
-  float* a3 = a2 + 32 * s.h2 * s.h2;               // [32][h3][h3]
-  float* z = a3 + s.flat;                          // [64]
-  __shared__ float red[2];
-  const int tid = threadIdx.x;
-  const int sample = blockIdx.x;
-  if (sample >= n) return;
+  const int item = blockIdx.x;
+  const int nc = t.F * t.Tj * t.Tj;
+  pdl_trigger();
+  pdl_wait();   // the event records of this step are complete
+  const unsigned char* rec = a.ev.base + (int64_t)item * a.ev.stride;
+  const uint8_t* cnt = rec + a.ev.counts_off;
+  const bool known = reinterpret_cast<const int*>(rec)[kEvKnown] > 0;
   const float inv = 1.f / (float)t.sd;
-  if (SRC == 0) {
-    pdl_trigger();
-    pdl_wait();
-    const unsigned char* rec = a.ev.base + (int64_t)sample * a.ev.stride;
-    const int* meta = reinterpret_cast<const int*>(rec);
-    if (meta[kEvKnown] == 0) return;
-    const uint8_t* cnt = rec + a.ev.counts_off;
-    for (int i = tid; i < C * tj * tj; i += kEncThreads) x[i] = bf(cnt[i] * inv);
-  } else {
-    window_input(t, a.Oj, type, c0 + sample, x, tid, kEncThreads, true);
-  }
-  __syncthreads();
-  const float* P = a.net;
-  // conv1 (stride 1), conv2, conv3 (stride 2), ReLU
-  auto conv = [&](const float* in, int Ci, int H, float* outp, int Ho, int stride, int ow,
-                  int ob) {
-    for (int o = tid; o < 32 * Ho * Ho; o += kEncThreads) {
-      const int ox = o % Ho, oy = (o / Ho) % Ho, co = o / (Ho * Ho);
-      float acc = P[ob + co];
-      for (int ci = 0; ci < Ci; ++ci)
-        for (int ky = 0; ky < 3; ++ky) {
-          const int iy = oy * stride + ky - 1;
-          if (iy < 0 || iy >= H) continue;
-          for (int kx = 0; kx < 3; ++kx) {
-            const int ix = ox * stride + kx - 1;
-            if (ix < 0 || ix >= H) continue;
-            acc += bf(__ldg(P + ow + ((co * Ci + ci) * 3 + ky) * 3 + kx)) * in[(ci * H + iy) * H + ix];
-          }
-        }
-      outp[o] = bf(fmaxf(acc, 0.f));
-    }
-    __syncthreads();
-  };
-  conv(x, C, tj, a1, tj, 1, s.o_w1, s.o_b1);
-  conv(a1, 32, tj, a2, s.h2, 2, s.o_w2, s.o_b2);
-  conv(a2, 32, s.h2, a3, s.h3, 2, s.o_w3, s.o_b3);
-  for (int j = tid; j < 64; j += kEncThreads) {
-    float acc = P[s.o_bf + j];
-    for (int k = 0; k < s.flat; ++k) acc += bf(__ldg(P + s.o_wf + j * s.flat + k)) * a3[k];
-    z[j] = acc;
-  }
-  __syncthreads();
-  if (tid < 32) {
-    float q = z[tid] * z[tid] + z[tid + 32] * z[tid + 32];
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if (tid == 0) red[0] = sqrtf(fmaxf(q, 1e-24f));
-  }
-  __syncthreads();
-  if (tid < 64) {
-    const float e = z[tid] / red[0];
-    if (SRC == 0) out_f32[(int64_t)sample * 64 + tid] = e;
-    else out_bf16[((int64_t)type * t.P + c0 + sample) * 64 + tid] = __float2bfloat16_rn(e);
+  float* xi = x + (int64_t)item * nc;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) xi[i] = known ? cnt[i] * inv : 0.f;
+}
+
+// Encoder inputs of TI candidates c0 .. c0 + n - 1 under mask type `type`.
+__global__ void k_window_inputs(const __grid_constant__ WaveArgs a, int type, int64_t c0,
+                                float* __restrict__ x) {
+  const TiDev& t = a.ti;
+  const int nc = t.F * t.Tj * t.Tj;
+  window_input(t, a.Oj, type, c0 + blockIdx.x, x + (int64_t)blockIdx.x * nc, threadIdx.x,
+               blockDim.x, false);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                          int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Round the weights (not the biases) of an encoder to BF16 values in place.
+__global__ void k_round_weights(float* p, EncShape s) {
+  const int total = s.o_bf + 64;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const bool bias = (i >= s.o_b1 && i < s.o_b1 + 32) || (i >= s.o_b2 && i < s.o_b2 + 32) ||
+                      (i >= s.o_b3 && i < s.o_b3 + 32) || i >= s.o_bf;
+    if (!bias) p[i] = bf(p[i]);
   }
 }
 
-int encode_smem_bytes(int C, int tj) {
-  const EncShape s = enc_shape(C, tj);
-  return 4 * (C * tj * tj + 32 * tj * tj + 32 * s.h2 * s.h2 + s.flat + 64);
+cudaError_t launch_round_weights(float* p, int C, int tj, cudaStream_t st) {
+  k_round_weights<<<64, 256, 0, st>>>(p, enc_shape(C, tj));
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -185,16 +151,23 @@ int encode_smem_bytes(int C, int tj) {
 constexpr int kNnThreads = 256;
 constexpr int kBins = 1024;
 constexpr int kCollect = 512;
+constexpr int kScoreCache = 6144;   // candidates whose scores stay in shared memory
 
 __device__ __forceinline__ float nn_score(const __nv_bfloat16* row, const float* e) {
-  float s = 0.f;
-#pragma unroll 8
-  for (int k = 0; k < 64; k += 2) {
-    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(row + k);
-    s = fmaf(__bfloat162float(v.x), e[k], s);
-    s = fmaf(__bfloat162float(v.y), e[k + 1], s);
+  float s0 = 0.f, s1 = 0.f;
+  const uint4* r = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {   // 8 BF16 values per 16-byte load
+    const uint4 v = __ldg(r + q);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const float lo = __uint_as_float(w[h] << 16), hi = __uint_as_float(w[h] & 0xFFFF0000u);
+      s0 = fmaf(lo, e[8 * q + 2 * h], s0);
+      s1 = fmaf(hi, e[8 * q + 2 * h + 1], s1);
+    }
   }
-  return s;
+  return s0 + s1;
 }
 
 __global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ WaveArgs a) {
@@ -202,6 +175,7 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ Wa
   __shared__ int hist[kBins];
   __shared__ float cs[kCollect];
   __shared__ int ci[kCollect];
+  __shared__ float cache[kScoreCache];
   __shared__ int sh_i[4];
   __shared__ float sh_f[4];
   const TiDev& t = a.ti;
@@ -236,13 +210,26 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ Wa
   float lo = -1.5f, hi = 1.5f;
   int above_prev = 0;
   float thr = lo;
+  const bool cached = t.P <= kScoreCache;
   for (int level = 0; level < 2; ++level) {
     const float scale = kBins / (hi - lo);
-    for (int64_t c = tid; c < t.P; c += kNnThreads) {
-      const float sc = nn_score(tab + c * 64, e);
-      if (sc < lo || sc >= hi) continue;
-      const int b = min(kBins - 1, max(0, (int)((sc - lo) * scale)));
-      atomicAdd(&hist[b], 1);
+    // warp-uniform trip count; lanes of a warp that fall in the same bin
+    // add once (the scores cluster, so plain atomics would serialize)
+    for (int64_t cb = 0; cb < t.P; cb += kNnThreads) {
+      const int64_t c = cb + tid;
+      int b = -1;
+      if (c < t.P) {
+        float sc;
+        if (cached && level > 0) {
+          sc = cache[c];
+        } else {
+          sc = nn_score(tab + c * 64, e);
+          if (cached) cache[c] = sc;
+        }
+        if (sc >= lo && sc < hi) b = min(kBins - 1, max(0, (int)((sc - lo) * scale)));
+      }
+      const unsigned same = __match_any_sync(0xffffffffu, b);
+      if (b >= 0 && (tid & 31) == __ffs(same) - 1) atomicAdd(&hist[b], __popc(same));
     }
     __syncthreads();
     if (tid == 0) {
@@ -271,10 +258,20 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ Wa
   }
   if (tid == 0) sh_i[3] = 0;
   __syncthreads();
-  for (int64_t c = tid; c < t.P; c += kNnThreads) {
-    const float sc = nn_score(tab + c * 64, e);
-    if (sc >= thr) {
-      const int k = atomicAdd(&sh_i[3], 1);
+  for (int64_t cb = 0; cb < t.P; cb += kNnThreads) {
+    const int64_t c = cb + tid;
+    float sc = 0.f;
+    bool keep = false;
+    if (c < t.P) {
+      sc = cached ? cache[c] : nn_score(tab + c * 64, e);
+      keep = sc >= thr;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    int base = 0;
+    if ((tid & 31) == 0 && bal) base = atomicAdd(&sh_i[3], __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) {
+      const int k = base + __popc(bal & ((1u << (tid & 31)) - 1u));
       if (k < kCollect) {
         cs[k] = sc;
         ci[k] = (int)c;
@@ -443,27 +440,26 @@ __global__ void __launch_bounds__(256) k_rerank(const __grid_constant__ WaveArgs
 }
 
 // ---------------------------------------------------------------------------
-cudaError_t encode_set_smem(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_encode<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem);
+cudaError_t launch_encode_items(const WaveArgs& a, float* x, float* act, bool pdl,
+                                cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_event_inputs, dim3(a.n_items), dim3(128), 0, st, pdl, a, x);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_encode<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return net_infer(a.net, a.ti.F, a.ti.Tj, x, a.n_items, act, a.emb, st);
 }
 
-cudaError_t launch_encode_items(const WaveArgs& a, bool pdl, cudaStream_t st) {
-  const int smem = encode_smem_bytes(a.ti.F, a.ti.Tj);
-  return launch_pdl(k_encode<0>, dim3(a.n_items), dim3(kEncThreads), smem, st, pdl, a, 0,
-                    (int64_t)0, a.n_items, a.emb, (__nv_bfloat16*)nullptr);
-}
-
-cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables,
-                                 cudaStream_t st) {
-  const int smem = encode_smem_bytes(a.ti.F, a.ti.Tj);
-  for (int64_t c0 = 0; c0 < a.ti.P; c0 += 65535) {
-    const int n = (int)std::min<int64_t>(65535, a.ti.P - c0);
-    k_encode<1><<<n, kEncThreads, smem, st>>>(a, type, c0, n, nullptr, tables);
+// Table of mask type `type`: embeddings of every candidate window, in
+// chunks of `chunk` candidates through the scratch x, act, emb.
+cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables, float* x,
+                                 float* act, float* emb, int chunk, cudaStream_t st) {
+  for (int64_t c0 = 0; c0 < a.ti.P; c0 += chunk) {
+    const int n = (int)std::min<int64_t>(chunk, a.ti.P - c0);
+    k_window_inputs<<<n, 128, 0, st>>>(a, type, c0, x);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if ((e = net_infer(a.net, a.ti.F, a.ti.Tj, x, n, act, emb, st)) != cudaSuccess) return e;
+    k_to_bf16<<<256, 256, 0, st>>>(emb, tables + ((int64_t)type * a.ti.P + c0) * 64,
+                                   (int64_t)n * 64);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -1,0 +1,253 @@
+"""GPU tests of the learned proposal's inference path (the paper has no
+learned component; the full search of Algorithm 1 judges it).
+
+* encoder inputs are the level-J facies counts (Sec. 4.2) of the window;
+* the tables hold the embedding of every TI window under each mask type;
+* with the gap threshold at +inf nothing is settled by the proposal and the
+  simulation is bit-identical to the plain one;
+* every patch the proposal settles carries the exact Eq. CCW score of its
+  pick, the best among the proposals;
+* a trained encoder misses the full search's best match less often than an
+  untrained one and keeps the pattern statistics of the plain method.
+"""
+import numpy as np
+import pytest
+
+from workloads import configs, stats
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+F, J, T, O = 2, 2, 48, 12      # the 512x512 batched geometry on the ribbon TI
+S = 4
+TJ = T // S
+GRID = (512, 512)
+
+
+@pytest.fixture(scope="module")
+def ccw():
+    import paper_2404_00441_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ti(ccw):
+    return ccw.TI(torch.from_numpy(configs.ribbon_ti_250()).cuda(), F, J, T, O)
+
+
+def block_counts(ti_np):
+    """Facies counts of every s x s block of the cropped TI: [F, ny/s, nx/s]."""
+    ny, nx = (ti_np.shape[0] // S) * S, (ti_np.shape[1] // S) * S
+    b = ti_np[:ny, :nx].reshape(ny // S, S, nx // S, S)
+    return np.stack([(b == f).sum(axis=(1, 3)) for f in range(F)])
+
+
+def strip_mask(mtype):
+    m = np.zeros((TJ, TJ), bool)   # [uy, ux]
+    oj = O // S
+    if mtype & 1:
+        m[:, :oj] = True
+    if mtype & 2:
+        m[:, TJ - oj:] = True
+    if mtype & 4:
+        m[:oj, :] = True
+    if mtype & 8:
+        m[TJ - oj:, :] = True
+    return m
+
+
+def de_from_counts(c):
+    """A fine-resolution data event [n, T, T] whose level-J blocks hold the
+    facies counts c [n, F, TJ*TJ] (cells of a block filled in facies order;
+    the one-hot score depends on the counts only)."""
+    n = c.shape[0]
+    cum = np.cumsum(c.astype(np.int32), axis=1)
+    k = np.arange(S * S)[None, None, :]
+    val = np.full((n, TJ * TJ, S * S), 255, np.uint8)
+    prev = np.zeros((n, TJ * TJ, 1), np.int32)
+    for f in range(F):
+        cf = cum[:, f, :, None]
+        val[(k >= prev) & (k < cf)] = f
+        prev = cf
+    v = val.reshape(n, TJ, TJ, S, S)
+    return np.ascontiguousarray(v.transpose(0, 1, 3, 2, 4).reshape(n, T, T))
+
+
+def test_encoder_inputs_are_block_counts(ccw, ti):
+    bc = block_counts(configs.ribbon_ti_250())
+    cd = ti.cand
+    rng = np.random.default_rng(0)
+    n = 64
+    cand = rng.integers(0, ti.n_cand, n).astype(np.int32)
+    types = rng.choice([1, 2, 4, 5, 6, 8, 9, 10], n).astype(np.int32)
+    cand[3] = ti.n_cand          # out of range: zeros
+    cand[5] = -1
+    x = ti.proposal_inputs(1, cand=torch.from_numpy(cand).cuda(),
+                           types=torch.from_numpy(types).cuda()).cpu().numpy()
+    for i in range(n):
+        if cand[i] < 0 or cand[i] >= ti.n_cand:
+            assert not x[i].any()
+            continue
+        cy, cx = divmod(int(cand[i]), cd[0])
+        win = bc[:, cy:cy + TJ, cx:cx + TJ] / float(S * S)
+        ref = np.where(strip_mask(int(types[i]))[None], win, 0.0)
+        assert np.array_equal(x[i], ref.astype(np.float32)), i
+    # anchors: counts / s^d and the mask type of the fully known strips
+    _, _, counts = ccw.simulate_groups(ti, [dict(grid=(200, 160), n_real=2)], topk=1, seed=3,
+                                       want_log=True, want_counts=True)[0]
+    c = counts.reshape(-1, F, TJ * TJ).contiguous()
+    xa, ta = ti.proposal_inputs(0, counts=c)
+    cn = c.cpu().numpy().astype(np.float32)
+    assert np.array_equal(xa.cpu().numpy().reshape(cn.shape), cn / (S * S))
+    tot = cn.sum(1).reshape(-1, TJ, TJ)
+    for i in range(tot.shape[0]):
+        ref_t = 0
+        for bit in range(4):
+            if np.all(tot[i][strip_mask(1 << bit)] == S * S):
+                ref_t |= 1 << bit
+        assert ta[i].item() == ref_t
+
+
+def test_tables_hold_every_window(ccw, ti):
+    """A data event equal to a TI window under mask type m embeds like the
+    table entry of that window: the window, or a window identical under the
+    mask, is among its proposals."""
+    net = ccw.Net(F, TJ, seed=3)
+    ti.attach_proposal(net, 64, 0.0)
+    bc = block_counts(configs.ribbon_ti_250())
+    cd = ti.cand
+    rng = np.random.default_rng(1)
+    n = 48
+    cand = rng.integers(0, ti.n_cand, n)
+    types = rng.choice([1, 4, 5], n)
+    counts = np.zeros((n, F, TJ * TJ), np.uint8)
+    wins = []
+    for i in range(n):
+        cy, cx = divmod(int(cand[i]), cd[0])
+        m = strip_mask(int(types[i]))
+        win = np.where(m[None], bc[:, cy:cy + TJ, cx:cx + TJ], 0)
+        wins.append(win)
+        counts[i] = win.reshape(F, -1)
+    prop, gap, typ = ti.proposal_query(torch.from_numpy(counts).cuda())
+    prop, gap, typ = prop.cpu().numpy(), gap.cpu().numpy(), typ.cpu().numpy()
+    assert np.array_equal(typ, types)
+    # windows of the uniform background tie with many others; beyond the
+    # selector's capacity the event gets no proposals (gap -1)
+    assert np.mean(gap >= 0) >= 0.5
+    for i in range(n):
+        if gap[i] < 0 or cand[i] in prop[i]:
+            continue
+        # the window itself may lose its place to identical masked windows
+        m = strip_mask(int(types[i]))
+        same = False
+        for c in prop[i]:
+            cy, cx = divmod(int(c), cd[0])
+            same |= np.array_equal(np.where(m[None], bc[:, cy:cy + TJ, cx:cx + TJ], 0), wins[i])
+        assert same, i
+    ti.attach_proposal(None)
+
+
+def run(ccw, ti, n_real, learned, seed=5, base=0):
+    return ccw.simulate_groups(ti, [dict(grid=GRID, n_real=n_real, real_base=base)], topk=1,
+                               seed=seed, want_log=True, want_counts=True, learned=learned)[0]
+
+
+def test_infinite_gap_threshold_is_the_plain_method(ccw, ti):
+    net = ccw.Net(F, TJ, seed=1)
+    ti.attach_proposal(net, 64, float("inf"))
+    po, pl, pc = run(ccw, ti, 4, 0)
+    ti.proposal_stats()
+    lo, ll, lc = run(ccw, ti, 4, 1)
+    assert torch.equal(po, lo) and torch.equal(pl, ll) and torch.equal(pc, lc)
+    n_known, n_prop, n_settled = ti.proposal_stats()
+    searched = int(((pl[..., 3] & 1) == 0).sum().item())
+    assert n_known == searched and n_prop > 0 and n_settled == 0
+    ti.attach_proposal(None)
+
+
+def exact_scores(ccw, ti, counts):
+    de = de_from_counts(counts)
+    out = []
+    for i0 in range(0, len(de), 256):
+        sc, _ = ccw.ccf_map(ti, torch.from_numpy(de[i0:i0 + 256]).cuda())
+        out.append(sc.cpu().numpy())
+    return np.concatenate(out)
+
+
+def test_settled_patches_take_the_exact_best_proposal(ccw, ti):
+    net = ccw.Net(F, TJ, seed=1)
+    ti.attach_proposal(net, 64, -0.5)    # every patch with proposals is settled
+    out, log, counts = run(ccw, ti, 4, 1)
+    n_known, n_prop, n_settled = ti.proposal_stats()
+    flags = log[..., 3].cpu().numpy()
+    settled = (flags & ccw.LOG_FLAG_PROPOSAL) != 0
+    # patches whose nearest windows tie beyond the selector's capacity fall
+    # back to the full search
+    assert settled.sum() == n_settled and n_settled >= 0.9 * n_prop > 0
+    sel = torch.from_numpy(settled).cuda()
+    c = counts[sel].contiguous()
+    prop, gap, _ = ti.proposal_query(c)
+    prop = prop.cpu().numpy()
+    picks = log[..., 0].cpu().numpy()[settled]
+    scores = log[..., 1].cpu().numpy()[settled]
+    idx = np.random.default_rng(0).choice(len(picks), min(300, len(picks)), replace=False)
+    sc = exact_scores(ccw, ti, c.cpu().numpy()[idx])
+    for j, i in enumerate(idx):
+        p = prop[i]
+        s = sc[j][p]
+        best = np.lexsort((p, -s))[0]
+        assert picks[i] == p[best] and scores[i] == s[best]
+    # patches not settled were searched in full: their pick is the argmax
+    full = ((flags & ccw.LOG_FLAG_DONE) != 0) & ~settled & ((flags & 1) == 0)
+    if full.any():
+        cf = counts[torch.from_numpy(full).cuda()].cpu().numpy()[:64]
+        scf = exact_scores(ccw, ti, cf)
+        assert np.array_equal(scf.argmax(1), log[..., 0].cpu().numpy()[full][:64])
+    ti.attach_proposal(None)
+
+
+def test_trained_proposal_gains_and_keeps_statistics(ccw, ti):
+    from paper_2404_00441_gb300 import proposal as PR
+    cnt_tr, best_tr = PR.generate_pairs(ti, GRID, 32, seed=1000)
+    cnt_te, best_te = PR.generate_pairs(ti, GRID, 8, seed=2000)
+    untrained = ccw.Net(F, TJ, seed=7)
+    ti.attach_proposal(untrained, 64, 0.0)
+    hit0, gap0, _ = PR.proposal_hits(ti, cnt_te, best_te)
+    trained = ccw.Net(F, TJ, seed=7)
+    losses = PR.train(ti, trained, cnt_tr, best_tr, 250, log_every=50)
+    assert losses[-1] < 0.6 * losses[0]
+    ti.attach_proposal(trained, 64, 0.0)
+    hit1, gap1, _ = PR.proposal_hits(ti, cnt_te, best_te)
+    ok0, ok1 = gap0 >= 0, gap1 >= 0
+    miss0 = 1.0 - hit0[ok0].float().mean().item()
+    miss1 = 1.0 - hit1[ok1].float().mean().item()
+    assert miss1 < miss0 and miss1 <= 0.03, (miss0, miss1)
+    theta = PR.calibrate_gap(hit1, gap1, 0.02)
+    assert np.isfinite(theta)
+    ti.attach_proposal(trained, 64, theta)
+    lo, ll, lc = run(ccw, ti, 16, 1, seed=9)
+    n_known, n_prop, n_settled = ti.proposal_stats()
+    assert n_settled > 0.5 * n_known
+    # miss rate on the learned path's own data events
+    flags = ll[..., 3].cpu().numpy()
+    settled = (flags & ccw.LOG_FLAG_PROPOSAL) != 0
+    cs = lc[torch.from_numpy(settled).cuda()].cpu().numpy()
+    picks = ll[..., 0].cpu().numpy()[settled]
+    idx = np.random.default_rng(1).choice(len(picks), min(400, len(picks)), replace=False)
+    sc = exact_scores(ccw, ti, cs[idx])
+    miss = float(np.mean(sc.argmax(1) != picks[idx]))
+    assert miss <= 0.06, miss
+    # pattern statistics of the two ensembles agree
+    po, _, _ = run(ccw, ti, 16, 0, seed=9)
+    ti_np = configs.ribbon_ti_250()
+    sp = stats.summary(list(po.cpu().numpy()), ti_np, F)
+    sl = stats.summary(list(lo.cpu().numpy()), ti_np, F)
+    mp, hp = stats.ci95(sp["props"])
+    ml, hl = stats.ci95(sl["props"])
+    assert abs(mp[1] - ml[1]) <= 2 * max(hp[1], hl[1]) + 0.01
+    vp, vl = sp["vario_x"].mean(0), sl["vario_x"].mean(0)
+    assert np.all(np.abs(vp - vl) <= 0.1 * vp + 0.005)
+    assert np.all(np.abs(sp["js"] - sl["js"]) <= 0.02)
+    ti.attach_proposal(None)
