@@ -18,6 +18,8 @@
 
 namespace ccw {
 
+constexpr int kCntInts = 12;   // shared counters ahead of the block counts
+
 template <int D, int MODE>
 __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ WaveArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -27,8 +29,9 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   const int T = t.T, Tj = t.Tj, s = t.s, rows = t.rows, TjP = t.TjP;
   float* Ws = reinterpret_cast<float*>(smem);
   int* cnt = reinterpret_cast<int*>(smem + t.nch * rows * TjP * 4);
-  // cnt: 0 known, 1 const, 2 mask cells, 3 hd count, 4 bad
-  int* counts = cnt + 8;   // [F][Tj^d] facies counts of the level-J blocks
+  // cnt: 0 known, 1 const, 2 mask cells, 3 hd count, 4 bad, 8..11 overlap
+  // strip k holds an incomplete block
+  int* counts = cnt + kCntInts;   // [F][Tj^d] facies counts of the level-J blocks
   unsigned char* rec = a.ev.base + (int64_t)item * a.ev.stride;
   int* meta = reinterpret_cast<int*>(rec);
   uint32_t* rowmask = reinterpret_cast<uint32_t*>(rec + a.ev.mask_off);
@@ -54,60 +57,78 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
 
   const int ncells = (D == 3) ? Tj * Tj * Tj : Tj * Tj;
   for (int i = tid; i < t.nch * rows * TjP; i += kThreads) Ws[i] = 0.f;
-  for (int i = tid; i < t.F * ncells; i += kThreads) counts[i] = 0;
-  if (tid < 8) cnt[tid] = 0;
+  if (tid < kCntInts) cnt[tid] = 0;
   pdl_trigger();
   pdl_wait();   // the previous step's pastes and reads of the records are done
   __syncthreads();
-  // one thread per fine cell of the window (consecutive x on consecutive
-  // threads: coalesced reads), facies counts of every level-J block in
-  // shared memory
-  for_window<D>(T, kThreads, [&](int qx, int qy, int qz) {
-    uint8_t v, h = CCW_UNKNOWN;
-    if (MODE == kModeSim) {
-      const int gx = it.o[0] + qx, gy = it.o[1] + qy, gz = it.o[2] + qz;
-      const int hx = gx - it.off[0], hy = gy - it.off[1], hz = gz - it.off[2];
-      if (hx >= 0 && hy >= 0 && hz >= 0 && hx < it.G[0] && hy < it.G[1] && hz < it.G[2])
-        h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
-      v = sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
-      if (h != CCW_UNKNOWN) v = h;
-    } else {
-      const int q = qx + T * (qy + T * qz);
-      v = __ldg(de + q);
-      if (hdw) h = __ldg(hdw + q);
-    }
-    if (h != CCW_UNKNOWN) {
-      const int k = atomicAdd(&cnt[3], 1);
-      if (k < a.ev.hd_cap)
-        hdl[k] = make_int2(qx + t.n[0] * (qy + t.n[1] * qz),
-                           ((qx + T * (qy + T * qz)) << 8) | (int)h);
-      if (h >= t.F) atomicOr(&cnt[4], kStatusBadCode);
-    }
-    if (v != CCW_UNKNOWN) {
-      if (v >= t.F) {
-        atomicOr(&cnt[4], kStatusBadCode);
-      } else {
-        const int u = (qx >> t.J) + Tj * ((qy >> t.J) + Tj * (qz >> t.J));
-        atomicAdd(&counts[v * ncells + u], 1);
-      }
-    }
-  });
-  __syncthreads();
-  // level-J weights of every block (one thread per block)
-  int my_known = 0, my_const = 0, my_mask = 0;
+  // One thread per level-J block: it gathers the block's s^d cells (grid
+  // value, or the hard datum where there is one), counts the facies in
+  // registers, and writes the block's weights (Eq. CCW operand). Facies
+  // counts sit in 16-bit lanes: facies 0-3 in `lo`, 4-7 in `hi`.
+  int my_known = 0, my_const = 0, my_mask = 0, bad = 0;
+  const int Oj = a.Oj;
   for (int u = tid; u < ncells; u += kThreads) {
-    int c = 0, csum = 0, blast = 0;
-    for (int f = 0; f < t.F; ++f) {
-      const int b = counts[f * ncells + u];
+    const int ux = u % Tj, uy = (u / Tj) % Tj, uz = (D == 3) ? u / (Tj * Tj) : 0;
+    uint64_t lo = 0, hi = 0;
+    for (int cz = 0; cz < ((D == 3) ? s : 1); ++cz)
+      for (int cy = 0; cy < s; ++cy) {
+        const int qy = uy * s + cy, qz = uz * s + cz;
+#pragma unroll 4
+        for (int cx = 0; cx < s; ++cx) {
+          const int qx = ux * s + cx;
+          uint8_t v, h = CCW_UNKNOWN;
+          if (MODE == kModeSim) {
+            const int gx = it.o[0] + qx, gy = it.o[1] + qy, gz = it.o[2] + qz;
+            const int hx = gx - it.off[0], hy = gy - it.off[1], hz = gz - it.off[2];
+            if (hx >= 0 && hy >= 0 && hz >= 0 && hx < it.G[0] && hy < it.G[1] && hz < it.G[2])
+              h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
+            v = sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
+            if (h != CCW_UNKNOWN) v = h;
+          } else {
+            const int q = qx + T * (qy + T * qz);
+            v = __ldg(de + q);
+            if (hdw) h = __ldg(hdw + q);
+          }
+          if (h != CCW_UNKNOWN) {
+            const int k = atomicAdd(&cnt[3], 1);
+            if (k < a.ev.hd_cap)
+              hdl[k] = make_int2(qx + t.n[0] * (qy + t.n[1] * qz),
+                                 ((qx + T * (qy + T * qz)) << 8) | (int)h);
+            if (h >= t.F) bad |= kStatusBadCode;
+          }
+          if (v != CCW_UNKNOWN) {
+            if (v >= t.F) {
+              bad |= kStatusBadCode;
+            } else {
+              const uint64_t one = 1ull << (16 * (v & 3));
+              if (v < 4) lo += one;
+              else hi += one;
+            }
+          }
+        }
+      }
+    int c = 0, csum = 0;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f >= t.F) break;
+      const int b = (int)(((f < 4 ? lo : hi) >> (16 * (f & 3))) & 0xFFFF);
+      counts[f * ncells + u] = b;
       c += b;
       csum += f * b;
-      if (f == t.F - 1) blast = b;
+    }
+    if (D == 2 && a.learned && c != t.sd) {
+      // this block keeps every overlap strip it lies in from being full
+      if (ux < Oj) cnt[8] = 1;
+      if (ux >= Tj - Oj) cnt[9] = 1;
+      if (uy < Oj) cnt[10] = 1;
+      if (uy >= Tj - Oj) cnt[11] = 1;
     }
     if (!c) continue;
     my_known += c;
     ++my_mask;
-    const int ux = u % Tj, row = u / Tj;
+    const int row = u / Tj;
     if (t.score_mode == 0) {
+      const int blast = counts[(t.F - 1) * ncells + u];
       for (int f = 0; f < t.F - 1; ++f)
         Ws[(f * rows + row) * TjP + ux] = (float)(counts[f * ncells + u] - blast);
       my_const += t.sd * blast;
@@ -118,28 +139,14 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   if (my_known) atomicAdd(&cnt[0], my_known);
   if (my_const) atomicAdd(&cnt[1], my_const);
   if (my_mask) atomicAdd(&cnt[2], my_mask);
+  if (bad) atomicOr(&cnt[4], bad);
+  __syncthreads();
   if (MODE == kModeSim && it.counts)
     for (int i = tid; i < t.F * ncells; i += kThreads) it.counts[i] = (uint8_t)counts[i];
-  {
+  if (a.learned) {
     uint8_t* rc = rec + a.ev.counts_off;
     for (int i = tid; i < t.F * ncells; i += kThreads) rc[i] = (uint8_t)min(counts[i], 255);
   }
-  __syncthreads();
-  // overlap strips fully known (2D): the mask type of the learned proposal
-  if (D == 2 && tid < 4) {
-    const int Oj = a.Oj;
-    bool full = Oj > 0;
-    for (int k = 0; k < Oj * Tj && full; ++k) {
-      const int along = k / Tj, across = k % Tj;
-      const int ux = (tid == 0) ? along : (tid == 1) ? Tj - 1 - along : across;
-      const int uy = (tid == 2) ? along : (tid == 3) ? Tj - 1 - along : across;
-      int c = 0;
-      for (int f = 0; f < t.F; ++f) c += counts[f * ncells + ux + Tj * uy];
-      full = (c == t.sd);
-    }
-    if (full) atomicOr(&cnt[5], 1 << tid);
-  }
-  __syncthreads();
   // chunk masks of the template rows and the weights, to the record
   for (int row = tid; row < rows; row += kThreads) {
     uint32_t m = 0;
@@ -194,7 +201,12 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     meta[kEvConst] = cnt[1];
     meta[kEvMaskCells] = cnt[2];
     meta[kEvNHd] = min(cnt[3], a.ev.hd_cap);
-    meta[kEvMaskType] = cnt[5];
+    // overlap strips fully known (2D, learned proposal): bit k unless a
+    // block of strip k was incomplete
+    meta[kEvMaskType] = (D == 2 && a.learned && Oj > 0)
+                            ? ((cnt[8] ? 0 : 1) | (cnt[9] ? 0 : 2) | (cnt[10] ? 0 : 4) |
+                               (cnt[11] ? 0 : 8))
+                            : 0;
     meta[kEvResolved] = 0;
     const int bad = cnt[4] | (cnt[3] > a.ev.hd_cap ? kStatusHdOverflow : 0);
     if (bad) atomicOr(a.status, bad);
@@ -270,7 +282,7 @@ cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3],
 }
 
 int events_smem_bytes(int nch, int rows, int TjP, int F, int ncells) {
-  return nch * rows * TjP * 4 + 32 + F * ncells * 4;   // cnt[8] then the counts
+  return nch * rows * TjP * 4 + kCntInts * 4 + F * ncells * 4;   // cnt, then the counts
 }
 
 template <int D, int MODE>
