@@ -85,7 +85,15 @@ typedef struct {
                           first (an addition of this library, see
                           ccw_ti_attach_proposal): 2D, one-hot score only,
                           topk <= the attached n_prop */
-  int32_t reserved[3]; /* must be 0 */
+  int32_t ccf_tile;    /* CCF tiling (no counterpart in the paper; results do
+                          not depend on it): 0 = the library's choice; with
+                          precision 0 the data events per CTA (1, 2, 4 or 8
+                          in 2D; 1, 2 or 4 in 3D); with precision 1/2
+                          nt | (mt << 16): data events per N-tile nt in
+                          {16, 32, 64, 128}, 128-candidate M-tiles per CTA
+                          mt in [1, 4], mt * nt <= 512. An autotuner picks it
+                          by timing (paper_2404_00441_gb300.autotune). */
+  int32_t reserved[2]; /* must be 0 */
 } ccw_params;
 
 /* Shape information of a prepared TI. */

@@ -143,7 +143,7 @@ struct SimPlan {
   int n_groups = 0;
   std::vector<GroupPlan> groups;
   int K, score_mode, precision;
-  int learned = 0, n_prop = 0;
+  int learned = 0, n_prop = 0, ccf_tile = 0;
   int n_waves, max_items;
   std::vector<int64_t> wave_off;
   void* items = nullptr;
@@ -270,16 +270,18 @@ int check_score_bound(const ccw_ti* t, int score_mode) {
 }
 
 // Items per CTA and TI tile buffers of the CCF kernel.
-void choose_simt(const ccw_ti* t, int nch, int K, int n_items, int& nb, int& nbuf, int& smem) {
+void choose_simt(const ccw_ti* t, int nch, int K, int n_items, int& nb, int& nbuf, int& smem,
+                 int nb_hint = 0) {
   nb = (t->ndim == 3) ? 2 : 4;
   while (nb > 1 && n_items < nb / 2 + 1) nb /= 2;
+  if (nb_hint) nb = nb_hint;
   nbuf = 2;
   smem = simt_smem_bytes(t->ndim, nch, t->rows, t->chunks, t->Tj, t->TjP, nb, K, nbuf);
   if (smem > 110 * 1024) {
     nbuf = 1;
     smem = simt_smem_bytes(t->ndim, nch, t->rows, t->chunks, t->Tj, t->TjP, nb, K, nbuf);
   }
-  while (smem > 220 * 1024 && nb > 1) {
+  while (!nb_hint && smem > 220 * 1024 && nb > 1) {
     nb /= 2;
     smem = simt_smem_bytes(t->ndim, nch, t->rows, t->chunks, t->Tj, t->TjP, nb, K, nbuf);
   }
@@ -309,8 +311,10 @@ int tc_a_nq(const ccw_ti* t, int mt) {
 }
 
 // Tensor-core tiling: items per N-tile, M-tiles per CTA, shared memory.
-void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& smem) {
+void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& smem,
+               int hint = 0) {
   a.nt = n_items <= 16 ? 16 : n_items <= 32 ? 32 : n_items <= 64 ? 64 : 128;
+  if (hint) a.nt = hint & 0xFFFF;
   a.ks = t->ks;
   a.ksteps = nch * t->rows * (t->ks / 16);
   a.px8 = t->px8;
@@ -319,10 +323,11 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
   // M-tiles per CTA: about one CTA per SM, at most 4 (and mt * nt TMEM
   // columns <= 512)
   int mt = (int)std::max<int64_t>(1, std::min<int64_t>(4, ((int64_t)t->mtiles * n_ntiles + 151) / 152));
+  if (hint) mt = hint >> 16;
   while (mt * a.nt > 512) --mt;
   for (;;) {
     smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K);
-    if (smem <= 220 * 1024 || (mt == 1 && a.nt == 16)) break;
+    if (hint || smem <= 220 * 1024 || (mt == 1 && a.nt == 16)) break;
     if (mt > 1) --mt;
     else a.nt /= 2;
   }
@@ -361,17 +366,28 @@ void SimPlan::release_cp() { delete static_cast<CcfPlan*>(cp); }
 
 namespace {
 
+// Valid values of the `ccf_tile` hint (0 = the library's heuristic).
+bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
+  if (hint == 0) return true;
+  if (precision == 0)
+    return t->ndim == 2 ? (hint == 1 || hint == 2 || hint == 4 || hint == 8)
+                        : (hint == 1 || hint == 2 || hint == 4);
+  const int nt = hint & 0xFFFF, mt = hint >> 16;
+  return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
+         mt * nt <= 512;
+}
+
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
-              CcfPlan& cp) {
+              CcfPlan& cp, int hint = 0) {
   cp.precision = precision;
   const int64_t chunk = std::min(n_items, 65535);
   if (precision == 0) {
-    choose_simt(t, nch, K, (int)chunk, cp.nb, cp.nbuf, cp.smem);
+    choose_simt(t, nch, K, (int)chunk, cp.nb, cp.nbuf, cp.smem, hint);
     cp.n_parts = t->n_tiles;
     cp.bmat_bytes = 0;
   } else {
     memset(&cp.tc, 0, sizeof(cp.tc));
-    choose_tc(t, nch, K, (int)chunk, cp.tc, cp.smem);
+    choose_tc(t, nch, K, (int)chunk, cp.tc, cp.smem, hint);
     cp.n_parts = cp.tc.n_mgroups;
     cp.bmat_bytes = ((chunk + cp.tc.nt - 1) / cp.tc.nt) * (int64_t)cp.tc.ksteps * 32 * cp.tc.nt;
   }
@@ -925,7 +941,8 @@ namespace {
 
 bool plan_matches(const SimPlan* pl, const ccw_params* p, const ccw_group* groups, int n_groups) {
   if (!pl || pl->n_groups != n_groups || pl->K != p->topk || pl->score_mode != p->score_mode ||
-      pl->precision != p->precision || pl->learned != p->learned)
+      pl->precision != p->precision || pl->learned != p->learned ||
+      pl->ccf_tile != p->ccf_tile)
     return false;
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
@@ -947,6 +964,7 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   pl->score_mode = p->score_mode;
   pl->precision = p->precision;
   pl->learned = p->learned;
+  pl->ccf_tile = p->ccf_tile;
   pl->n_prop = p->learned ? t->n_prop : 0;
   pl->n_waves = 0;
   for (int i = 0; i < n_groups; ++i) {
@@ -995,7 +1013,12 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   event_layout(nch, t->rows, t->TjP, hd_capacity(t), t->F, t->rows * t->Tj, pl->evl);
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
-  plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp);
+  plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
+  if (cp->smem > 220 * 1024) {
+    delete pl;
+    return fail(CCW_EINVAL, "ccf_tile 0x%x needs %d bytes of shared memory", p->ccf_tile,
+                cp->smem);
+  }
   cudaError_t e = cudaSuccess;
   for (auto& g : pl->groups) {
     if ((e = cudaMalloc(&g.sg, (size_t)g.gp_vol * g.n_real)) != cudaSuccess ||
@@ -1121,12 +1144,15 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if (int rc = check_precision(t, p->precision, p->score_mode)) return rc;
   if (p->path_random != 0 && p->path_random != 1) return fail(CCW_EINVAL, "bad path_random");
   if (p->learned != 0 && p->learned != 1) return fail(CCW_EINVAL, "bad learned flag");
+  if (!valid_tile_hint(t, p->precision, p->ccf_tile))
+    return fail(CCW_EINVAL, "ccf_tile 0x%x is not a valid tiling for precision %d", p->ccf_tile,
+                p->precision);
   if (p->learned) {
     if (!t->d_tables) return fail(CCW_EINVAL, "learned = 1 needs an attached proposal");
     if (p->score_mode != 0) return fail(CCW_EINVAL, "learned = 1 needs the one-hot score");
     if (p->topk > t->n_prop) return fail(CCW_EINVAL, "topk > the proposal's n_prop");
   }
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (p->reserved[i]) return fail(CCW_EINVAL, "reserved fields must be 0");
   if (int rc = check_score_bound(t, p->score_mode)) return rc;
   if (n_groups < 1 || !groups) return fail(CCW_EINVAL, "at least one grid group is needed");

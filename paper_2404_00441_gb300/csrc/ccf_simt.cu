@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads)
       const int nb = i % NB;
       const int rest = i / NB;   // (ch * rows + row) * chunks + g
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (meta[nb * 8 + kMKnown] > 0) {
+      if (meta[nb * 8 + kMActive]) {
         const float4* src = reinterpret_cast<const float4*>(
             a.ev.base + (int64_t)(item0 + nb) * a.ev.stride + a.ev.w_off);
         w = src[rest];
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads)
     uint32_t m = 0;
 #pragma unroll
     for (int nb = 0; nb < NB; ++nb)
-      if (meta[nb * 8 + kMKnown] > 0)
+      if (meta[nb * 8 + kMActive])
         m |= reinterpret_cast<const uint32_t*>(a.ev.base + (int64_t)(item0 + nb) * a.ev.stride +
                                                a.ev.mask_off)[row];
     if (m) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads)
   const int n_spans = flag[1];
   bool any_known = false;
 #pragma unroll
-  for (int nb = 0; nb < NB; ++nb) any_known |= meta[nb * 8 + kMKnown] > 0;
+  for (int nb = 0; nb < NB; ++nb) any_known |= meta[nb * 8 + kMActive] != 0;
 
   // ---- masked CCF -----------------------------------------------------------
   const int ltx = tid % TS::TXT;
@@ -384,11 +384,13 @@ cudaError_t launch_ccf_simt(int mode, const WaveArgs& a, const CUtensorMap& tmap
     switch (a.nb) {
       case 1: return launch_nb<2, 1>(mode, a, tmap, nbuf, smem, pdl, st);
       case 2: return launch_nb<2, 2>(mode, a, tmap, nbuf, smem, pdl, st);
+      case 8: return launch_nb<2, 8>(mode, a, tmap, nbuf, smem, pdl, st);
       default: return launch_nb<2, 4>(mode, a, tmap, nbuf, smem, pdl, st);
     }
   }
   switch (a.nb) {
     case 1: return launch_nb<3, 1>(mode, a, tmap, nbuf, smem, pdl, st);
+    case 4: return launch_nb<3, 4>(mode, a, tmap, nbuf, smem, pdl, st);
     default: return launch_nb<3, 2>(mode, a, tmap, nbuf, smem, pdl, st);
   }
 }

@@ -23,6 +23,7 @@ constexpr int kRx = 4;            // consecutive x-candidates per thread
 constexpr int kMaxHd = 1024;      // hard data kept per template window
 constexpr int kMaxLevel2D = 4;
 constexpr int kMaxLevel3D = 2;
+constexpr int kTcMaxMt = 4;       // M-tiles per CTA of the tensor-core CCF
 constexpr int kMaxChunks = 32;    // 4-wide tap chunks per template row (Tj <= 128)
 
 // ---------------------------------------------------------------------------

@@ -123,7 +123,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 constexpr int kTcThreads = 256;   // 8 warps: TMEM lane quarter w % 4, item parity w / 4
-constexpr int kTcMaxMt = 4;
 
 struct TcSmem {
   int bar_off, meta_off, list_off, a_off, b_off, bytes;
