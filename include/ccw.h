@@ -89,10 +89,12 @@ typedef struct {
                           not depend on it): 0 = the library's choice; with
                           precision 0 the data events per CTA (1, 2, 4 or 8
                           in 2D; 1, 2 or 4 in 3D); with precision 1/2
-                          nt | (mt << 16): data events per N-tile nt in
-                          {16, 32, 64, 128}, 128-candidate M-tiles per CTA
-                          mt in [1, 4], mt * nt <= 512. An autotuner picks it
-                          by timing (paper_2404_00441_gb300.autotune). */
+                          nt | (mt << 16) | (e << 24): data events per N-tile
+                          nt in {16, 32, 64, 128}, 128-candidate M-tiles per
+                          CTA mt in [1, 4], mt * nt <= 512, epilogue e (0:
+                          per-thread K-lists when K <= 8, 1: lanes on
+                          candidates). An autotuner picks it by timing
+                          (paper_2404_00441_gb300.autotune). */
   int32_t reserved[2]; /* must be 0 */
 } ccw_params;
 

@@ -34,10 +34,11 @@ def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
             for nb in ((1, 2, 4, 8) if ti.ndim == 2 else (1, 2, 4)):
                 out.append((0, nb))
         elif ti.ndim == 2:
-            for nt in (16, 32, 64, 128):
-                for mt in (1, 2, 4):
-                    if mt * nt <= 512:
-                        out.append((p, nt | (mt << 16)))
+            for epi in (0, 1):
+                for nt in (16, 32, 64, 128):
+                    for mt in (1, 2, 4):
+                        if mt * nt <= 512:
+                            out.append((p, nt | (mt << 16) | (epi << 24)))
     return out
 
 

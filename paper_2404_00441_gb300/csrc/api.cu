@@ -24,7 +24,7 @@ void simt_tma_box(int d, int Tj, int TjP, int box[3]);
 cudaError_t launch_ccf_simt(int mode, const WaveArgs& a, const CUtensorMap& tmap, int nbuf,
                             int smem, bool pdl, cudaStream_t st);
 // tc.cu
-int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K);
+int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K, int lane_epi);
 cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // prepare.cu
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
@@ -314,7 +314,13 @@ int tc_a_nq(const ccw_ti* t, int mt) {
 void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& smem,
                int hint = 0) {
   a.nt = n_items <= 16 ? 16 : n_items <= 32 ? 32 : n_items <= 64 ? 64 : 128;
-  if (hint) a.nt = hint & 0xFFFF;
+  // epilogue: per-thread K-lists pay off for K = 1; lanes on candidates
+  // keep every lane busy when the item count is small and K > 1
+  a.tc_lane_epi = K > 1 ? 1 : 0;
+  if (hint) {
+    a.nt = hint & 0xFFFF;
+    a.tc_lane_epi = (hint >> 24) & 1;
+  }
   a.ks = t->ks;
   a.ksteps = nch * t->rows * (t->ks / 16);
   a.px8 = t->px8;
@@ -323,10 +329,10 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
   // M-tiles per CTA: about one CTA per SM, at most 4 (and mt * nt TMEM
   // columns <= 512)
   int mt = (int)std::max<int64_t>(1, std::min<int64_t>(4, ((int64_t)t->mtiles * n_ntiles + 151) / 152));
-  if (hint) mt = hint >> 16;
+  if (hint) mt = (hint >> 16) & 0xFF;
   while (mt * a.nt > 512) --mt;
   for (;;) {
-    smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K);
+    smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
     if (hint || smem <= 220 * 1024 || (mt == 1 && a.nt == 16)) break;
     if (mt > 1) --mt;
     else a.nt /= 2;
@@ -372,9 +378,9 @@ bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
   if (precision == 0)
     return t->ndim == 2 ? (hint == 1 || hint == 2 || hint == 4 || hint == 8)
                         : (hint == 1 || hint == 2 || hint == 4);
-  const int nt = hint & 0xFFFF, mt = hint >> 16;
+  const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, epi = hint >> 24;
   return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
-         mt * nt <= 512;
+         mt * nt <= 512 && (epi == 0 || epi == 1);
 }
 
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
@@ -411,6 +417,7 @@ void apply_ccf(const ccw_ti* t, const CcfPlan& cp, void* bmat, WaveArgs& c) {
     c.n_mgroups = cp.tc.n_mgroups;
     c.nt = cp.tc.nt;
     c.a_nq = cp.tc.a_nq;
+    c.tc_lane_epi = cp.tc.tc_lane_epi;
     c.bmat = bmat;
   }
 }

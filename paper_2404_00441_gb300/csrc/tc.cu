@@ -111,6 +111,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 8 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // One 32-bit TMEM column of this thread's lane (completion not awaited).
 __device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
   uint32_t v;
@@ -123,12 +133,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 constexpr int kTcThreads = 256;   // 8 warps: TMEM lane quarter w % 4, item parity w / 4
+constexpr int kTcRegK = 8;        // K up to this keeps per-thread lists in registers
 
 struct TcSmem {
-  int bar_off, meta_off, list_off, a_off, b_off, bytes;
+  int bar_off, meta_off, list_off, a_off, b_off, s_off, c_off, bytes;
 };
 
-__host__ __device__ inline TcSmem tc_smem(int nch, int a_nq, int ksteps, int nt, int K) {
+__host__ __device__ inline TcSmem tc_smem(int nch, int a_nq, int ksteps, int nt, int K,
+                                          int lane_epi) {
   TcSmem L;
   int off = 0;
   L.bar_off = off;
@@ -141,12 +153,22 @@ __host__ __device__ inline TcSmem tc_smem(int nch, int a_nq, int ksteps, int nt,
   off += nch * a_nq * 128;
   L.b_off = off;
   off += ksteps * 32 * nt;
+  L.s_off = L.c_off = off;
+  if (K <= kTcRegK && !lane_epi) {
+    // one M-tile of scores, [128][nt + 4] floats; later the thread lists
+    off = ((off + 127) / 128) * 128;
+    L.s_off = off;
+    const int s_bytes = 128 * (nt + 4) * 4, l_bytes = kTcThreads * kTcRegK * 8;
+    off += ((s_bytes > l_bytes ? s_bytes : l_bytes) + 127) / 128 * 128;
+    L.c_off = off;   // (candidate index, TI offset) of every row of the CTA's M-tiles
+    off += kTcMaxMt * 128 * 8;
+  }
   L.bytes = off + 128;   // slack for aligning the dynamic shared memory base
   return L;
 }
 
-int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K) {
-  return tc_smem(nch, a_nq, ksteps, nt, K).bytes;
+int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K, int lane_epi) {
+  return tc_smem(nch, a_nq, ksteps, nt, K, lane_epi).bytes;
 }
 
 enum { kTcBarA = 0, kTcBarB = 1, kTcBarMma = 2 };
@@ -158,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const TiDev& t = a.ti;
   const int nt = a.nt, K = a.K, nch = t.nch;
-  const TcSmem L = tc_smem(nch, a.a_nq, a.ksteps, nt, K);
+  const TcSmem L = tc_smem(nch, a.a_nq, a.ksteps, nt, K, a.tc_lane_epi);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.bar_off + 64);
   int* flag = reinterpret_cast<int*>(smem + L.bar_off + 72);
@@ -262,8 +284,111 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
     failed = flag[0] != 0;
   }
 
-  // ---- epilogue: lane = candidate of each M-tile, warps split the items ----
-  if (!failed) {
+  // ---- epilogue, K <= kTcRegK: scores move from tensor memory to shared
+  // memory one M-tile at a time; thread (item n, segment) then scans its
+  // item's column over a segment of candidates, turning scores into ranking
+  // keys (with the hard-data mismatches) and keeping its K best in
+  // registers; the segment lists of each item merge into the CTA's list.
+  const bool reg_lists = MODE != kModeMap && K <= kTcRegK && !a.tc_lane_epi;
+  if (!failed && reg_lists) {
+    mbar_try_wait(&bar[kTcBarMma], 0u);
+    tc_fence_after();
+    float* S = reinterpret_cast<float*>(smem + L.s_off);
+    int2* cand = reinterpret_cast<int2*>(smem + L.c_off);
+    const int sp = nt + 4;
+    for (int i = tid; i < n_mt * 128; i += kTcThreads) {
+      const int64_t Lpos = L_start + i;
+      const int cx = (int)(Lpos % a.px8), cy = (int)(Lpos / a.px8);
+      const bool valid = cx < t.cd[0] && cy < t.cd[1];
+      cand[i] = make_int2(valid ? cx + t.cd[0] * cy : -1,
+                          t.s * cx + t.n[0] * (t.s * cy));
+    }
+    const int n = tid % nt, nseg = kTcThreads / nt, seg = tid / nt;
+    const int seg_len = 128 / nseg;
+    const int4 mt4 = meta[n];
+    const int item = ntile * nt + n;
+    const int2* hdl = reinterpret_cast<const int2*>(
+        a.ev.base + (int64_t)(item < a.n_items ? item : 0) * a.ev.stride + a.ev.hd_off);
+    uint64_t lst[kTcRegK];
+#pragma unroll
+    for (int i = 0; i < kTcRegK; ++i) lst[i] = kNoKey;
+    uint64_t worst = kNoKey;
+    const int m = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int half = nt / 2;
+#pragma unroll 1
+    for (int j = 0; j < n_mt; ++j) {
+#pragma unroll 1
+      for (int c0 = parity * half; c0 < (parity + 1) * half; c0 += 8) {
+        uint32_t v[8];
+        tmem_ld8(lane_base + (uint32_t)(j * nt + c0), v);
+        float4* dst = reinterpret_cast<float4*>(S + m * sp + c0);
+        dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]),
+                             __uint_as_float(v[2]), __uint_as_float(v[3]));
+        dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
+                             __uint_as_float(v[6]), __uint_as_float(v[7]));
+      }
+      __syncthreads();
+      if (mt4.w) {
+#pragma unroll 2
+        for (int r = seg * seg_len; r < (seg + 1) * seg_len; ++r) {
+          const int2 ci = cand[j * 128 + r];
+          if (ci.x < 0) continue;
+          const int score = __float2int_rn(S[r * sp + n]) + mt4.y;
+          int mis = 0;
+#pragma unroll 1
+          for (int k = 0; k < mt4.z; ++k) {
+            const int2 e = __ldg(hdl + k);
+            mis += (__ldg(t.ti + ci.y + e.x) != (uint8_t)(e.y & 0xFF));
+          }
+          const uint64_t key = make_key(mis, score, ci.x);
+          if (key < worst) {
+            if (K == 1) {
+              lst[0] = key;
+              worst = key;
+            } else {
+              uint64_t x = key;
+#pragma unroll
+              for (int i = 0; i < kTcRegK; ++i) {
+                const uint64_t lo = lst[i] < x ? lst[i] : x;
+                x = lst[i] < x ? x : lst[i];
+                lst[i] = lo;
+              }
+              worst = lst[0];
+#pragma unroll
+              for (int i = 1; i < kTcRegK; ++i)
+                if (i < K) worst = lst[i];
+            }
+          }
+        }
+      }
+      __syncthreads();   // S is rewritten by the next M-tile
+    }
+    // segment lists -> shared memory (over S), then one warp per item merges
+    uint64_t* seglists = reinterpret_cast<uint64_t*>(S);
+#pragma unroll
+    for (int i = 0; i < kTcRegK; ++i)
+      if (i < K) seglists[(seg * nt + n) * kTcRegK + i] = lst[i];
+    __syncthreads();
+    for (int nn = warp; nn < nt; nn += 8) {
+      if (!meta[nn].w) continue;
+      const int item2 = ntile * nt + nn;
+      unsigned long long* part = a.part + ((int64_t)item2 * a.n_parts + mg) * K;
+      int head = 0;
+      const bool has = lane < nseg;
+      for (int r = 0; r < Kp; ++r) {
+        const uint64_t mine =
+            (has && head < Kp) ? seglists[(lane * nt + nn) * kTcRegK + head] : kNoKey;
+        const uint64_t best = warp_min_u64(mine);
+        if (has && best != kNoKey && mine == best) ++head;
+        if (lane == 0) part[r] = best;
+      }
+    }
+  }
+
+  // ---- epilogue (maps, K > kTcRegK): lane = candidate of each M-tile, warps
+  // split the items ----
+  if (!failed && !reg_lists) {
     mbar_try_wait(&bar[kTcBarMma], 0u);
     tc_fence_after();
     const int m = quarter * 32 + lane;
@@ -327,7 +452,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
   }
   tc_fence_before();
   __syncthreads();
-  if (!failed && MODE != kModeMap) {
+  if (!failed && !reg_lists && MODE != kModeMap) {
     // merge the lists of the 4 warps that saw each item into the CTA's list
     for (int n = warp; n < nt; n += 8) {
       if (!meta[n].w) continue;
