@@ -90,6 +90,27 @@ def parse_args():
     return ap.parse_args()
 
 
+def profiled_traffic(kernel: str, workload: str, tile: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.txt), if it was taken on this workload and tiling with
+    the current kernel source; None otherwise."""
+    import hashlib
+    src = {"k_ccf_tc": "tc.cu", "k_ccf_simt": "ccf_simt.cu"}[kernel]
+    path = os.path.join(ROOT, "paper_2404_00441_gb300", "csrc", src)
+    try:
+        with open(path, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 5 and not line.startswith("#") and parts[0] == kernel and \
+                        parts[1] == workload and int(parts[2], 0) == tile and parts[3] == sha:
+                    return int(parts[4])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def shard_real_base(rank: int, total_real: int, group_base: int) -> int:
     """First realization id of a group on `rank`: ranks own disjoint id
     ranges [rank * total_real, (rank + 1) * total_real), so every rank draws
@@ -439,7 +460,12 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
         "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "launches": n_launch,
+                     "traffic": profiled_traffic("k_ccf_simt" if precision == 0 else "k_ccf_tc",
+                                                 args.workload, tile),
+                     "traffic_note": "cold-cache DRAM bytes per launch from profiles/traffic.txt "
+                                     "(null unless taken on this workload, tiling and kernel "
+                                     "source)",
+                     "launches": n_launch,
                      "kernel_ms_per_step": kern_ms / args.steps,
                      "instrumented_ms_per_step": instr_ms / args.steps,
                      "timing": "CUDA events around every CCF launch on its stream, over a "

@@ -230,6 +230,78 @@ __device__ void paste_pixels(const PasteGeom& p, int pick, int J, int nthreads,
   });
 }
 
+// Inverse of the per-block scaled Haar analysis (Sec. 3.1) for a block of
+// S^D coefficients in registers, in the in-place layout (level j pairs
+// samples 2^(j-1) apart, sum at the lower, difference at the upper index,
+// axes x, y, z in turn): the levels and axes in reverse order, each pair
+// (l, d) back to ((l + d) / 2, (l - d) / 2), exact in integers.
+template <int D, int S>
+__device__ __forceinline__ void haar_block_inverse(int (&v)[(D == 3) ? S * S * S : S * S]) {
+  constexpr int SZ = (D == 3) ? S : 1;
+#pragma unroll
+  for (int h = S / 2; h >= 1; h /= 2) {
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      const int stride = (a == 0) ? 1 : (a == 1 ? S : S * S);
+      const int hx = (a == 0) ? 2 * h : h, hy = (a == 1) ? 2 * h : h,
+                hz = (D == 3) ? ((a == 2) ? 2 * h : h) : 1;
+#pragma unroll
+      for (int z = 0; z < SZ; z += hz)
+#pragma unroll
+        for (int y = 0; y < S; y += hy)
+#pragma unroll
+          for (int x = 0; x < S; x += hx) {
+            const int p = x + S * (y + S * z), q = p + h * stride;
+            const int l = v[p], d = v[q];
+            v[p] = (l + d) >> 1;   // l + d and l - d are even
+            v[q] = (l - d) >> 1;
+          }
+    }
+  }
+}
+
+// CTA-cooperative Inverse-DWT paste with one thread per level-J block of the
+// drawn pattern (Algorithm 1, lines 13-14): the block's S^D coefficients
+// from `staged` (stage_blocks), inverted in registers, written row by row
+// (S-byte words when `aligned`: window origin and grid pitch multiples of S).
+// For windows that lie inside the grid (simulation lattice).
+template <int D, int S>
+__device__ void paste_blocks(const PasteGeom& p, const int16_t* staged, int nthreads,
+                             bool aligned) {
+  constexpr int SD = (D == 3) ? S * S * S : S * S;
+  constexpr int SZ = (D == 3) ? S : 1;
+  const int Tj = p.Tj;
+  const int nblk = (D == 3) ? Tj * Tj * Tj : Tj * Tj;
+  for (int u = threadIdx.x; u < nblk; u += nthreads) {
+    const int ux = u % Tj, uy = (u / Tj) % Tj, uz = (D == 3) ? u / (Tj * Tj) : 0;
+    int v[SD];
+    const int16_t* blk = staged + u * SD;
+#pragma unroll
+    for (int i = 0; i < SD; ++i) v[i] = blk[i];
+    haar_block_inverse<D, S>(v);
+#pragma unroll
+    for (int cz = 0; cz < SZ; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < S; ++cy) {
+        const int gx = p.o[0] + ux * S, gy = p.o[1] + uy * S + cy, gz = p.o[2] + uz * S + cz;
+        uint8_t* row = p.grid + gx + (int64_t)p.g[0] * (gy + (int64_t)p.g[1] * gz);
+        const int* r = v + S * (cy + S * cz);
+        if (S == 4 && aligned) {
+          *reinterpret_cast<uint32_t*>(row) = (uint32_t)(r[0] & 0xFF) |
+                                              ((uint32_t)(r[1] & 0xFF) << 8) |
+                                              ((uint32_t)(r[2] & 0xFF) << 16) |
+                                              ((uint32_t)(r[3 % S] & 0xFF) << 24);
+        } else if (S == 2 && aligned) {
+          *reinterpret_cast<uint16_t*>(row) =
+              (uint16_t)((r[0] & 0xFF) | ((r[1 % S] & 0xFF) << 8));
+        } else {
+#pragma unroll
+          for (int cx = 0; cx < S; ++cx) row[cx] = (uint8_t)r[cx];
+        }
+      }
+  }
+}
+
 // Re-impose the hard data of a pasted window (event-record list, int2 .y =
 // (window offset << 8) | code). Call after a barrier that follows the paste.
 template <int D>

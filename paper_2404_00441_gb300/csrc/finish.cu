@@ -111,7 +111,14 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
   if (staged_bytes > 0) {
     stage_blocks<D>(g, pk, t.J, staged, kThreads);
     __syncthreads();
-    paste_pixels<D>(g, pk, t.J, kThreads, staged);
+    // block-wise inverse in registers for the common levels, else per cell
+    const bool aligned = (g.o[0] % t.s) == 0 && (g.g[0] % t.s) == 0;
+    if (D == 2 && t.J == 2)
+      paste_blocks<D, 4>(g, staged, kThreads, aligned);
+    else if (t.J == 1)
+      paste_blocks<D, 2>(g, staged, kThreads, aligned);
+    else
+      paste_pixels<D>(g, pk, t.J, kThreads, staged);
   } else {
     paste_pixels<D>(g, pk, t.J, kThreads);
   }

@@ -119,25 +119,33 @@ __global__ void k_hd_overlay(const int32_t* __restrict__ cells, const uint8_t* _
   atomicOr(status, kStatusTimeout);
 }
 
-// Crop the padded grids of n_real realizations into the caller's output.
+// Crop the padded grids of n_real realizations into the caller's output,
+// undoing each realization's path mirroring (Algorithm 1, line 3): one CTA
+// per output row at a time, 32-bit words when every row start is aligned.
 __global__ void k_crop_out(const uint8_t* __restrict__ sg, int64_t gp_vol, int gpx, int gpy,
                            uint8_t* __restrict__ out, int gx, int gy, int gz, int d, int gpz,
-                           int path_random, uint64_t seed, int real_base) {
+                           int path_random, uint64_t seed, int real_base, int vec) {
   const int slot = blockIdx.y;
   const uint32_t r = (uint32_t)(real_base + slot);
   const uint32_t flips = path_random ? (draw_word(seed, r, 0u, 1u) & ((1u << d) - 1u)) : 0u;
   const int ox = (flips & 1u) ? gpx - gx : 0;
   const int oy = (flips & 2u) ? gpy - gy : 0;
   const int oz = (flips & 4u) ? gpz - gz : 0;
-  const int64_t total = (int64_t)gx * gy * gz;
+  const int rows = gy * gz;
   const uint8_t* src = sg + (int64_t)slot * gp_vol;
-  uint8_t* dst = out + (int64_t)slot * total;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % gx);
-    const int y = (int)((i / gx) % gy);
-    const int z = (int)(i / ((int64_t)gx * gy));
-    dst[i] = src[(x + ox) + (int64_t)gpx * ((y + oy) + (int64_t)gpy * (z + oz))];
+  uint8_t* dst = out + (int64_t)slot * gx * rows;
+  const bool words = vec && ((ox & 3) == 0);
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int y = row % gy, z = row / gy;
+    const uint8_t* s = src + ox + (int64_t)gpx * ((y + oy) + (int64_t)gpy * (z + oz));
+    uint8_t* o = dst + (int64_t)row * gx;
+    if (words) {
+      const uint32_t* s4 = reinterpret_cast<const uint32_t*>(s);
+      uint32_t* o4 = reinterpret_cast<uint32_t*>(o);
+      for (int i = threadIdx.x; i < gx / 4; i += blockDim.x) o4[i] = __ldg(s4 + i);
+    } else {
+      for (int i = threadIdx.x; i < gx; i += blockDim.x) o[i] = __ldg(s + i);
+    }
   }
 }
 
@@ -218,14 +226,19 @@ cudaError_t launch_hd_overlay(const int32_t* cells, const uint8_t* vals, int n, 
 cudaError_t launch_crop_out(const uint8_t* sg, int64_t gp_vol, const int gp[3], uint8_t* out,
                             const int g[3], int d, int n_real, int path_random, uint64_t seed,
                             int real_base, cudaStream_t st) {
-  const int64_t total = (int64_t)g[0] * g[1] * g[2];
-  const int bx = (int)std::min<int64_t>((total + 255) / 256, 1024);
+  const int rows = g[1] * g[2];
+  // word copies need 4-aligned row starts in both arrays
+  const int vec = ((g[0] | gp[0]) & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 3) == 0 &&
+                  (reinterpret_cast<uintptr_t>(sg) & 3) == 0;
+  const int bx = std::min(rows, 64);
+  const int threads = vec ? std::min(256, std::max(32, (g[0] / 4 + 31) / 32 * 32))
+                          : std::min(256, std::max(32, (g[0] + 31) / 32 * 32));
   for (int r0 = 0; r0 < n_real; r0 += 65535) {
     const int nr = std::min(65535, n_real - r0);
     dim3 grid(bx, nr);
-    k_crop_out<<<grid, 256, 0, st>>>(sg + (int64_t)r0 * gp_vol, gp_vol, gp[0], gp[1],
-                                     out + (int64_t)r0 * total, g[0], g[1], g[2], d, gp[2],
-                                     path_random, seed, real_base + r0);
+    k_crop_out<<<grid, threads, 0, st>>>(sg + (int64_t)r0 * gp_vol, gp_vol, gp[0], gp[1],
+                                         out + (int64_t)r0 * g[0] * rows, g[0], g[1], g[2], d,
+                                         gp[2], path_random, seed, real_base + r0, vec);
   }
   return cudaGetLastError();
 }
