@@ -1206,7 +1206,7 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
     const GroupPlan& g = pl->groups[i];
     SimGroup& s = hg[i];
     s.sg = (uint8_t*)g.sg;
-    s.overlay = (const uint8_t*)g.overlay;
+    s.overlay = groups[i].n_hd > 0 ? (const uint8_t*)g.overlay : nullptr;
     for (int a = 0; a < 3; ++a) {
       s.G[a] = g.g[a];
       s.Gp[a] = g.gp[a];

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   extern __shared__ __align__(16) unsigned char smem[];
   const TiDev& t = a.ti;
   const int tid = threadIdx.x;
+  const int nth = blockDim.x;   // a multiple of 32, at most kThreads
   const int item = blockIdx.x;
   const int T = t.T, Tj = t.Tj, s = t.s, rows = t.rows, TjP = t.TjP;
   float* Ws = reinterpret_cast<float*>(smem);
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   }
 
   const int ncells = (D == 3) ? Tj * Tj * Tj : Tj * Tj;
-  for (int i = tid; i < t.nch * rows * TjP; i += kThreads) Ws[i] = 0.f;
+  for (int i = tid; i < t.nch * rows * TjP; i += nth) Ws[i] = 0.f;
   if (tid < kCntInts) cnt[tid] = 0;
   pdl_trigger();
   pdl_wait();   // the previous step's pastes and reads of the records are done
@@ -67,22 +68,34 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   // counts sit in 16-bit lanes: facies 0-3 in `lo`, 4-7 in `hi`.
   int my_known = 0, my_const = 0, my_mask = 0, bad = 0;
   const int Oj = a.Oj;
-  for (int u = tid; u < ncells; u += kThreads) {
+  // 4-cell rows of a block are one aligned 32-bit word of the grid when the
+  // window origin and the grid pitch are multiples of 4
+  const bool words = MODE == kModeSim && s == 4 && ((it.o[0] | it.Gp[0]) & 3) == 0;
+  for (int u = tid; u < ncells; u += nth) {
     const int ux = u % Tj, uy = (u / Tj) % Tj, uz = (D == 3) ? u / (Tj * Tj) : 0;
     uint64_t lo = 0, hi = 0;
     for (int cz = 0; cz < ((D == 3) ? s : 1); ++cz)
       for (int cy = 0; cy < s; ++cy) {
         const int qy = uy * s + cy, qz = uz * s + cz;
+        uint32_t word = 0;
+        if (words) {
+          const int gy = it.o[1] + qy, gz = it.o[2] + qz;
+          word = *reinterpret_cast<const uint32_t*>(
+              sg + it.o[0] + ux * s + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz));
+        }
 #pragma unroll 4
         for (int cx = 0; cx < s; ++cx) {
           const int qx = ux * s + cx;
           uint8_t v, h = CCW_UNKNOWN;
           if (MODE == kModeSim) {
             const int gx = it.o[0] + qx, gy = it.o[1] + qy, gz = it.o[2] + qz;
-            const int hx = gx - it.off[0], hy = gy - it.off[1], hz = gz - it.off[2];
-            if (hx >= 0 && hy >= 0 && hz >= 0 && hx < it.G[0] && hy < it.G[1] && hz < it.G[2])
-              h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
-            v = sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
+            if (it.overlay) {   // the group has hard data
+              const int hx = gx - it.off[0], hy = gy - it.off[1], hz = gz - it.off[2];
+              if (hx >= 0 && hy >= 0 && hz >= 0 && hx < it.G[0] && hy < it.G[1] && hz < it.G[2])
+                h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
+            }
+            v = words ? (uint8_t)(word >> (8 * cx))
+                      : sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
             if (h != CCW_UNKNOWN) v = h;
           } else {
             const int q = qx + T * (qy + T * qz);
@@ -136,19 +149,25 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
       Ws[row * TjP + ux] = (float)csum;
     }
   }
-  if (my_known) atomicAdd(&cnt[0], my_known);
-  if (my_const) atomicAdd(&cnt[1], my_const);
-  if (my_mask) atomicAdd(&cnt[2], my_mask);
-  if (bad) atomicOr(&cnt[4], bad);
+  my_known = __reduce_add_sync(0xffffffffu, my_known);
+  my_const = __reduce_add_sync(0xffffffffu, my_const);
+  my_mask = __reduce_add_sync(0xffffffffu, my_mask);
+  bad = (int)__reduce_or_sync(0xffffffffu, (unsigned)bad);
+  if ((tid & 31) == 0) {
+    if (my_known) atomicAdd(&cnt[0], my_known);
+    if (my_const) atomicAdd(&cnt[1], my_const);
+    if (my_mask) atomicAdd(&cnt[2], my_mask);
+    if (bad) atomicOr(&cnt[4], bad);
+  }
   __syncthreads();
   if (MODE == kModeSim && it.counts)
-    for (int i = tid; i < t.F * ncells; i += kThreads) it.counts[i] = (uint8_t)counts[i];
+    for (int i = tid; i < t.F * ncells; i += nth) it.counts[i] = (uint8_t)counts[i];
   if (a.learned) {
     uint8_t* rc = rec + a.ev.counts_off;
-    for (int i = tid; i < t.F * ncells; i += kThreads) rc[i] = (uint8_t)min(counts[i], 255);
+    for (int i = tid; i < t.F * ncells; i += nth) rc[i] = (uint8_t)min(counts[i], 255);
   }
   // chunk masks of the template rows and the weights, to the record
-  for (int row = tid; row < rows; row += kThreads) {
+  for (int row = tid; row < rows; row += nth) {
     uint32_t m = 0;
     for (int ch = 0; ch < t.nch; ++ch) {
       const float* wr = Ws + (ch * rows + row) * TjP;
@@ -160,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   {
     const float4* src = reinterpret_cast<const float4*>(Ws);
     float4* dst = reinterpret_cast<float4*>(wout);
-    for (int i = tid; i < t.nch * rows * TjP / 4; i += kThreads) dst[i] = src[i];
+    for (int i = tid; i < t.nch * rows * TjP / 4; i += nth) dst[i] = src[i];
   }
   if (a.bmat) {
     // the weights as the B operand of the tensor-core CCF: item n is row
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     const int ntile = item / nt, ni = item % nt;
     unsigned char* base = reinterpret_cast<unsigned char*>(a.bmat) +
                           (int64_t)ntile * a.ksteps * 32 * nt + (ni / 8) * 256 + (ni % 8) * 16;
-    for (int i = tid; i < a.ksteps * 2; i += kThreads) {
+    for (int i = tid; i < a.ksteps * 2; i += nth) {
       const int k = i >> 1, kc = i & 1;
       const int k16 = k % k16n, rc = k / k16n;
       const float* wr = Ws + rc * TjP;
@@ -234,9 +253,9 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
                                     : (tid < 3 ? 0 : -1));
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
-  paste_pixels<D>(g, pk, t.J, kThreads);
+  paste_pixels<D>(g, pk, t.J, nth);
   __syncthreads();
-  paste_hard_data<D>(g, hdl, min(cnt[3], a.ev.hd_cap), T, kThreads);
+  paste_hard_data<D>(g, hdl, min(cnt[3], a.ev.hd_cap), T, nth);
 }
 
 // Standalone Inverse-DWT paste (ccw_idwt_paste): one CTA per batch element.
@@ -294,7 +313,10 @@ static cudaError_t launch_events_t(const WaveArgs& a, bool pdl, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  return launch_pdl(fn, dim3(a.n_items), dim3(kThreads), smem, st, pdl, a);
+  // one thread per level-J block up to kThreads (fewer threads per CTA let
+  // more CTAs share an SM when the template has few blocks)
+  const int nth = std::min(kThreads, std::max(96, (ncells + 31) / 32 * 32));   // >= 4 + K log words
+  return launch_pdl(fn, dim3(a.n_items), dim3(nth), smem, st, pdl, a);
 }
 
 cudaError_t launch_events(int mode, const WaveArgs& a, bool pdl, cudaStream_t st) {

@@ -10,12 +10,12 @@ namespace ccw {
 
 // Minimum over the CTA, broadcast to every thread.
 __device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_min_u64(v);
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
-    uint64_t w = (lane < kWarps) ? red[lane] : kNoKey;
+    uint64_t w = (lane < nw) ? red[lane] : kNoKey;
     w = warp_min_u64(w);
     if (lane == 0) red[kWarps] = w;
   }
@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
   extern __shared__ __align__(16) int16_t staged[];
   const TiDev& t = a.ti;
   const int tid = threadIdx.x;
+  const int nth = blockDim.x;   // a multiple of 32, at most kThreads
   const int item = blockIdx.x;
   pdl_trigger();
   pdl_wait();   // the per-tile keys of this step are complete
@@ -45,10 +46,10 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
   const int M = a.n_parts * K;
   // keys of this thread (slots >= Kp of a tile are unused)
   uint64_t mine[kKeysPerThread];
-  const bool in_regs = M <= kKeysPerThread * kThreads;
+  const bool in_regs = M <= kKeysPerThread * nth;
 #pragma unroll
   for (int i = 0; i < kKeysPerThread; ++i) {
-    const int j = tid + i * kThreads;
+    const int j = tid + i * nth;
     mine[i] = (in_regs && j < M && (j % K) < Kp) ? all[j] : kNoKey;
   }
   uint64_t prev = 0;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
       for (int i = 0; i < kKeysPerThread; ++i)
         if ((r == 0 || mine[i] > prev) && mine[i] < m) m = mine[i];
     } else {
-      for (int j = tid; j < M; j += kThreads) {
+      for (int j = tid; j < M; j += nth) {
         if ((j % K) >= Kp) continue;
         const uint64_t v = all[j];
         if ((r == 0 || v > prev) && v < m) m = v;
@@ -109,23 +110,23 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
   if (staged_bytes > 0) {
-    stage_blocks<D>(g, pk, t.J, staged, kThreads);
+    stage_blocks<D>(g, pk, t.J, staged, nth);
     __syncthreads();
     // block-wise inverse in registers for the common levels, else per cell
     const bool aligned = (g.o[0] % t.s) == 0 && (g.g[0] % t.s) == 0;
     if (D == 2 && t.J == 2)
-      paste_blocks<D, 4>(g, staged, kThreads, aligned);
+      paste_blocks<D, 4>(g, staged, nth, aligned);
     else if (t.J == 1)
-      paste_blocks<D, 2>(g, staged, kThreads, aligned);
+      paste_blocks<D, 2>(g, staged, nth, aligned);
     else
-      paste_pixels<D>(g, pk, t.J, kThreads, staged);
+      paste_pixels<D>(g, pk, t.J, nth, staged);
   } else {
-    paste_pixels<D>(g, pk, t.J, kThreads);
+    paste_pixels<D>(g, pk, t.J, nth);
   }
   __syncthreads();
   paste_hard_data<D>(g, reinterpret_cast<const int2*>(a.ev.base + (int64_t)item * a.ev.stride +
                                                       a.ev.hd_off),
-                     em[kEvNHd], t.T, kThreads);
+                     em[kEvNHd], t.T, nth);
 }
 
 template <int D, int MODE>
@@ -139,7 +140,10 @@ static cudaError_t launch_t(const WaveArgs& a, bool pdl, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, staged);
     if (e != cudaSuccess) return e;
   }
-  return launch_pdl(fn, dim3(a.n_items), dim3(kThreads), staged, st, pdl, a, staged);
+  // one thread per level-J block of the pattern, up to kThreads
+  const int nblk = (D == 3) ? a.ti.Tj * a.ti.Tj * a.ti.Tj : a.ti.Tj * a.ti.Tj;
+  const int nth = std::min(kThreads, std::max(96, (nblk + 31) / 32 * 32));   // >= 4 + K log words
+  return launch_pdl(fn, dim3(a.n_items), dim3(nth), staged, st, pdl, a, staged);
 }
 
 cudaError_t launch_finish(int mode, const WaveArgs& a, bool pdl, cudaStream_t st) {
