@@ -305,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
             hd_vals=None if hd is None else torch.from_numpy(hd[1]).cuda(),
             hd_host=hd))
     ndim = len(groups[0]["grid"])
-    precision = args.precision if args.precision is not None else (1 if ndim == 2 else 0)
+    precision = args.precision if args.precision is not None else 1
     cells_per_step = sum(gr["n_real"] * cells_of(gr["grid"]) for gr in groups)
     learned_info = None
     if args.learned:
@@ -318,7 +318,7 @@ def run_ours(args, rank, world, local_rank):
     elif not args.no_autotune:
         from paper_2404_00441_gb300 import autotune
         precs = ((precision,) if args.precision is not None
-                 else ((0, 1, 2) if ndim == 2 else (0,)))
+                 else (0, 1, 2))
         tg = [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
                    hd_cells=gr["hd_cells"], hd_vals=gr["hd_vals"]) for gr in groups]
         precision, tile, times = autotune.tune(g, tg, topk=w["K"], seed=w["seed"],

@@ -75,7 +75,7 @@ typedef struct {
                           (Algorithm 1, line 3) */
   int32_t score_mode;  /* 0: one-hot facies indicators; 1: literal codes */
   int32_t precision;   /* CCF arithmetic: 0 FP32 FMA lanes; 1 FP16 and 2 BF16
-                          tensor cores (2D only), FP32 accumulation. Every
+                          tensor cores (3D: K <= 8), FP32 accumulation. Every
                           mode is exact: 1 and 2 are refused (CCW_EINVAL)
                           when an operand could exceed the format's exact
                           integer range (2048 for FP16, 256 for BF16; the
@@ -89,11 +89,14 @@ typedef struct {
                           not depend on it): 0 = the library's choice; with
                           precision 0 the data events per CTA (1, 2, 4 or 8
                           in 2D; 1, 2 or 4 in 3D); with precision 1/2
-                          nt | (mt << 16) | (e << 24): data events per N-tile
-                          nt in {16, 32, 64, 128}, 128-candidate M-tiles per
-                          CTA mt in [1, 4], mt * nt <= 512, epilogue e (0:
-                          per-thread K-lists when K <= 8, 1: lanes on
-                          candidates). An autotuner picks it by timing
+                          nt | (mt << 16) | (e << 24) | (m << 25): data
+                          events per N-tile nt in {16, 32, 64, 128},
+                          128-candidate M-tiles per CTA mt in [1, 4],
+                          mt * nt <= 512, epilogue e (0: per-thread K-lists
+                          when K <= 8, 1: lanes on candidates), m = 1:
+                          operands streamed through a ring of shared-memory
+                          stages (always so in 3D; K <= 8). An autotuner
+                          picks it by timing
                           (paper_2404_00441_gb300.autotune). */
   int32_t reserved[2]; /* must be 0 */
 } ccw_params;

@@ -33,12 +33,15 @@ def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
         if p == 0:
             for nb in ((1, 2, 4, 8) if ti.ndim == 2 else (1, 2, 4)):
                 out.append((0, nb))
-        elif ti.ndim == 2:
-            for epi in (0, 1):
+        else:
+            # tensor cores: bit 24 = lanes-on-candidates epilogue, bit 25 =
+            # streamed operands (the only form in 3D)
+            flags = (0, 1, 2) if ti.ndim == 2 else (2,)
+            for fl in flags:
                 for nt in (16, 32, 64, 128):
                     for mt in (1, 2, 4):
                         if mt * nt <= 512:
-                            out.append((p, nt | (mt << 16) | (epi << 24)))
+                            out.append((p, nt | (mt << 16) | (fl << 24)))
     return out
 
 

@@ -26,6 +26,9 @@ cudaError_t launch_ccf_simt(int mode, const WaveArgs& a, const CUtensorMap& tmap
 // tc.cu
 int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K, int lane_epi);
 cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
+// tcs.cu
+int tcs_smem_bytes(int mt, int nt);
+cudaError_t launch_ccf_tcs(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // prepare.cu
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
                       int64_t nq, int nplanes, void* z8_f16, void* z8_bf16, cudaStream_t st);
@@ -291,11 +294,13 @@ int hd_capacity(const ccw_ti* t) { return (int)std::min<int64_t>(kMaxHd, ipow(t-
 
 // Precision check: the tensor-core path is exact while every operand fits
 // the 16-bit format exactly (FP16: |v| <= 2048, BF16: |v| <= 256).
-int check_precision(const ccw_ti* t, int precision, int score_mode) {
+int check_precision(const ccw_ti* t, int precision, int score_mode, int K = 1, int hint = 0) {
   if (precision == 0) return CCW_OK;
   if (precision != 1 && precision != 2) return fail(CCW_EINVAL, "precision must be 0, 1 or 2");
-  if (t->ndim != 2)
-    return fail(CCW_EUNSUPPORTED, "the tensor-core CCF is built for 2D training images only");
+  // the streamed tensor-core kernel (3D, or 2D on request) keeps the K best
+  // keys of each thread in registers: K <= 8
+  if ((t->ndim == 3 || ((hint >> 25) & 1)) && K > 8)
+    return fail(CCW_EUNSUPPORTED, "the streamed tensor-core CCF supports K <= 8");
   const int64_t vmax = (int64_t)(score_mode == 0 ? 1 : t->F - 1) * t->sd;
   const int64_t lim = precision == 1 ? 2048 : 256;
   if (vmax > lim)
@@ -312,7 +317,10 @@ int tc_a_nq(const ccw_ti* t, int mt) {
 
 // Tensor-core tiling: items per N-tile, M-tiles per CTA, shared memory.
 void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& smem,
-               int hint = 0) {
+               bool& streamed, int hint = 0) {
+  // streamed operands (tcs.cu) in 3D, where a CTA's whole Hankel view does
+  // not fit in shared memory, and in 2D when the hint asks for them
+  streamed = t->ndim == 3 || ((hint >> 25) & 1);
   a.nt = n_items <= 16 ? 16 : n_items <= 32 ? 32 : n_items <= 64 ? 64 : 128;
   // epilogue: per-thread K-lists pay off for K = 1; lanes on candidates
   // keep every lane busy when the item count is small and K > 1
@@ -332,13 +340,14 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
   if (hint) mt = (hint >> 16) & 0xFF;
   while (mt * a.nt > 512) --mt;
   for (;;) {
-    smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
+    smem = streamed ? tcs_smem_bytes(mt, a.nt)
+                    : tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
     if (hint || smem <= 220 * 1024 || (mt == 1 && a.nt == 16)) break;
     if (mt > 1) --mt;
     else a.nt /= 2;
   }
   a.mt = mt;
-  a.a_nq = tc_a_nq(t, mt);
+  a.a_nq = streamed ? 0 : tc_a_nq(t, mt);
   a.n_mgroups = (t->mtiles + mt - 1) / mt;
   a.z8_nq = t->z8_nq;
 }
@@ -361,6 +370,7 @@ struct DevBuf {
 struct CcfPlan {
   int precision = 0;
   int nb = 1, nbuf = 1, smem = 0;   // SIMT
+  bool streamed = false;             // tensor cores with streamed operands (tcs.cu)
   WaveArgs tc;                       // tensor-core tiling fields
   int n_parts = 0;                   // partial key lists per item
   int64_t ev_bytes = 0, part_bytes = 0, bmat_bytes = 0;
@@ -378,9 +388,9 @@ bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
   if (precision == 0)
     return t->ndim == 2 ? (hint == 1 || hint == 2 || hint == 4 || hint == 8)
                         : (hint == 1 || hint == 2 || hint == 4);
-  const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, epi = hint >> 24;
+  const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, flags = hint >> 24;
   return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
-         mt * nt <= 512 && (epi == 0 || epi == 1);
+         mt * nt <= 512 && flags >= 0 && flags <= 3;
 }
 
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
@@ -393,7 +403,7 @@ void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const
     cp.bmat_bytes = 0;
   } else {
     memset(&cp.tc, 0, sizeof(cp.tc));
-    choose_tc(t, nch, K, (int)chunk, cp.tc, cp.smem, hint);
+    choose_tc(t, nch, K, (int)chunk, cp.tc, cp.smem, cp.streamed, hint);
     cp.n_parts = cp.tc.n_mgroups;
     cp.bmat_bytes = ((chunk + cp.tc.nt - 1) / cp.tc.nt) * (int64_t)cp.tc.ksteps * 32 * cp.tc.nt;
   }
@@ -424,6 +434,7 @@ void apply_ccf(const ccw_ti* t, const CcfPlan& cp, void* bmat, WaveArgs& c) {
 
 cudaError_t launch_ccf(const ccw_ti* t, int mode, const CcfPlan& cp, const WaveArgs& c, bool pdl,
                        cudaStream_t st) {
+  if (cp.precision && cp.streamed) return launch_ccf_tcs(mode, c, cp.smem, pdl, st);
   if (cp.precision) return launch_ccf_tc(mode, c, cp.smem, pdl, st);
   return launch_ccf_simt(mode, c, t->tmap, cp.nbuf, cp.smem, pdl, st);
 }
@@ -503,7 +514,7 @@ int search_common(const ccw_ti* t, int mode, int32_t B, const uint8_t* de, const
   int score_mode, precision;
   if (int rc = split_mode(score_arg, score_mode, precision)) return rc;
   if (int rc = check_score_bound(t, score_mode)) return rc;
-  if (int rc = check_precision(t, precision, score_mode)) return rc;
+  if (int rc = check_precision(t, precision, score_mode, mode == kModeSearch ? k : 1)) return rc;
   if (mode == kModeSearch && (k < 1 || k > CCW_MAX_TOPK))
     return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
   if (B == 0) return CCW_OK;
@@ -739,12 +750,18 @@ int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3], i
     release();
     return fail(CCW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
   }
-  if (ndim == 2) {
-    // 8-shift copies of the planes for the tensor-core CCF
+  {
+    // 8-shift copies of the planes for the tensor-core CCF, over the line
+    // L = x + px8 (y + nc1 z) of the level-J grid
     t->px8 = (int)align_up(t->nc[0], 8);
     t->ks = 16 * ((t->Tj + 15) / 16);
-    t->mtiles = (int)((int64_t)t->px8 * t->cd[1] + 127) / 128;
-    t->z8_nq = 16LL * t->mtiles + 128 + (int64_t)(t->rows - 1) * t->px8 / 8 + 2 * (t->ks / 16) + 32;
+    const int64_t lines = (ndim == 2) ? t->cd[1] : (int64_t)t->nc[1] * (t->cd[2] - 1) + t->cd[1];
+    t->mtiles = (int)(((int64_t)t->px8 * lines + 127) / 128);
+    const int64_t roff_max =
+        (int64_t)t->px8 * ((t->Tj - 1) + (ndim == 3 ? (int64_t)t->nc[1] * (t->Tj - 1) : 0));
+    t->z8_nq = std::max<int64_t>(
+        16LL * t->mtiles + 128 + (int64_t)(t->rows - 1) * t->px8 / 8 + 2 * (t->ks / 16) + 32,
+        (128LL * t->mtiles + roff_max + t->ks + 256) / 8 + 8);
     const size_t zb = (size_t)t->F * t->z8_nq * 128;
     if ((e = cudaMalloc(&t->z8_f16, zb)) != cudaSuccess ||
         (e = cudaMalloc(&t->z8_bf16, zb)) != cudaSuccess) {
@@ -753,8 +770,8 @@ int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3], i
       release();
       return fail(CCW_ENOMEM, "tensor-core TI buffers: %s", cudaGetErrorString(e));
     }
-    if ((e = launch_z8(t->d_planes, t->px, t->plane_vol, t->nc[0], t->nc[1], t->px8, t->z8_nq,
-                       t->F, t->z8_f16, t->z8_bf16, st)) != cudaSuccess) {
+    if ((e = launch_z8(t->d_planes, t->px, t->plane_vol, t->nc[0], t->nc[1] * t->nc[2], t->px8,
+                       t->z8_nq, t->F, t->z8_f16, t->z8_bf16, st)) != cudaSuccess) {
       cudaFree(t->z8_f16);
       cudaFree(t->z8_bf16);
       release();
@@ -878,7 +895,7 @@ int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
   int sm, precision;
   if (int rc = split_mode(score_mode, sm, precision)) return rc;
   if (int rc = check_score_bound(t, sm)) return rc;
-  if (int rc = check_precision(t, precision, sm)) return rc;
+  if (int rc = check_precision(t, precision, sm, k)) return rc;
   if (k < 1 || k > CCW_MAX_TOPK) return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
   if (B == 0) return CCW_OK;
   if (!de_dev || !ctr_dev || !topk_idx_dev || !topk_score_dev || !topk_mis_dev || !pick_dev)
@@ -1148,7 +1165,7 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if (p->topk < 1 || p->topk > CCW_MAX_TOPK)
     return fail(CCW_EINVAL, "topk must be in [1, %d]", CCW_MAX_TOPK);
   if (p->score_mode != 0 && p->score_mode != 1) return fail(CCW_EINVAL, "bad score_mode");
-  if (int rc = check_precision(t, p->precision, p->score_mode)) return rc;
+  if (int rc = check_precision(t, p->precision, p->score_mode, p->topk, p->ccf_tile)) return rc;
   if (p->path_random != 0 && p->path_random != 1) return fail(CCW_EINVAL, "bad path_random");
   if (p->learned != 0 && p->learned != 1) return fail(CCW_EINVAL, "bad learned flag");
   if (!valid_tile_hint(t, p->precision, p->ccf_tile))

@@ -1,0 +1,317 @@
+// tcs.cu -- phase B of a search step on the tensor cores with streamed
+// operands: the masked cross-correlation of Eq. CCW (Algorithm 1, line 10)
+// as the contraction S[c, n] = sum_k A[c, k] B[n, k] of tc.cu, for training
+// images whose Hankel view is too large to hold whole in shared memory (3D,
+// where a template row is a (ky, kz) pair) and as a tiling choice in 2D.
+//
+// Candidate positions are read as a line L = x + px8 (y + nc1 z) of the
+// level-J grid (px8 a multiple of 8). For the 128 positions L0..L0+127 of an
+// M-tile, template row (ky, kz) and taps [16 k16, 16 k16 + 16):
+//   A[m, kx] = plane[L0 + m + px8 (ky + nc1 kz) + 16 k16 + kx],
+// whose 8 x 8 core matrices are the 17 consecutive entries q0 .. q0 + 16 of
+// the 8-shift copy z8 (q0 = (L0 + px8 (ky + nc1 kz) + 16 k16) / 8): one
+// contiguous bulk copy of 2176 bytes per M-tile and K step. The items' B
+// tile of the K step (canonical K-major, written by the event kernel) is one
+// more bulk copy. A ring of kTcsStages shared-memory stages is filled by one
+// producer thread and drained by one MMA thread; tcgen05.commit on a
+// stage's "empty" barrier hands it back to the producer. Accumulators: mt
+// M-tiles x nt FP32 columns of tensor memory. Epilogue: per-thread K-lists
+// (K <= 8) as in tc.cu, or the full map.
+#include "tc_util.cuh"
+
+namespace ccw {
+
+constexpr int kTcsThreads = 256;
+constexpr int kTcsStages = 4;
+constexpr int kTcsRegK = 8;
+constexpr int kATile = 17 * 128;   // one M-tile's A operand of one K step
+
+struct TcsSmem {
+  int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, bytes;
+};
+
+__host__ __device__ inline TcsSmem tcs_smem(int mt, int nt) {
+  TcsSmem L;
+  int off = 0;
+  L.bar_off = off;   // full[4], empty[4], done, TMEM slot, flags
+  off += 256;
+  L.meta_off = off;
+  off += ((nt * 16 + 127) / 128) * 128;
+  L.stage_off = off;
+  L.b_in_stage = mt * kATile;   // a multiple of 128
+  L.stage_bytes = ((mt * kATile + 32 * nt + 127) / 128) * 128;
+  off += kTcsStages * L.stage_bytes;
+  L.s_off = off;
+  const int s_bytes = 128 * (nt + 4) * 4, l_bytes = kTcsThreads * kTcsRegK * 8;
+  off += (((s_bytes > l_bytes ? s_bytes : l_bytes) + 127) / 128) * 128;
+  L.c_off = off;
+  off += kTcMaxMt * 128 * 8;
+  L.bytes = off + 128;   // slack for aligning the dynamic shared memory base
+  return L;
+}
+
+int tcs_smem_bytes(int mt, int nt) { return tcs_smem(mt, nt).bytes; }
+
+template <int MODE, bool BF16>
+__global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__ WaveArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const TiDev& t = a.ti;
+  const int nt = a.nt, K = a.K;
+  const TcsSmem L = tcs_smem(a.mt, nt);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint64_t* empty = full + 8;
+  uint64_t* done = full + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 17);
+  volatile int* flag = reinterpret_cast<volatile int*>(full + 18);
+  int4* meta = reinterpret_cast<int4*>(smem + L.meta_off);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quarter = warp & 3, parity = warp >> 2;
+  const int mg = blockIdx.x, ntile = blockIdx.y;
+  const int64_t L_start = (int64_t)mg * a.mt * 128;
+  const int n_mt = min(a.mt, a.mtiles - mg * a.mt);
+  const int Kp = (int)((int64_t)K < t.P ? K : t.P);
+  const uint32_t b_bytes = 32u * (uint32_t)nt;
+  const int k16n = a.ks / 16;
+  const int ksteps = a.ksteps;
+
+  if (tid == 0) {
+    for (int s = 0; s < kTcsStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+    flag[0] = 0;
+  }
+  pdl_trigger();
+  pdl_wait();   // event records and B operands of this step are complete
+  for (int i = tid; i < nt; i += kTcsThreads) {
+    const int item = ntile * nt + i;
+    int4 m = make_int4(0, 0, 0, 0);
+    if (item < a.n_items) {
+      const int* em = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+      m.x = em[kEvKnown];
+      m.y = em[kEvConst];
+      m.z = em[kEvNHd];
+      m.w = (MODE == kModeMap) ? 1 : (m.x > 0 && !em[kEvResolved]);
+    }
+    meta[i] = m;
+  }
+  unsigned long long* work = (MODE == kModeSim) ? a.call->work : a.work;
+  if (work && mg == 0 && MODE != kModeMap) {
+    for (int i = tid; i < nt; i += kTcsThreads) {
+      const int item = ntile * nt + i;
+      if (item >= a.n_items) continue;
+      const int* em = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+      if (em[kEvKnown] <= 0 || em[kEvResolved]) continue;
+      atomicAdd(&work[0], (unsigned long long)t.P);
+      atomicAdd(&work[1], (unsigned long long)t.P * em[kEvMaskCells] * t.nch);
+    }
+  }
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(a.mt * nt)) ncols <<= 1;
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // ---- K loop: producer (thread 0) and MMA issuer (thread 32) -------------
+  if (tid == 0) {
+    const unsigned char* z8 = reinterpret_cast<const unsigned char*>(a.z8);
+    const unsigned char* bsrc =
+        reinterpret_cast<const unsigned char*>(a.bmat) + (int64_t)ntile * ksteps * b_bytes;
+    int issued = 0;
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % kTcsStages;
+      if (k >= kTcsStages &&
+          !mbar_wait_bounded(&empty[s], (uint32_t)(((k / kTcsStages) - 1) & 1))) {
+        flag[0] = 1;
+        break;
+      }
+      if (flag[0]) break;
+      unsigned char* st = smem + L.stage_off + s * L.stage_bytes;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)n_mt * kATile + b_bytes);
+      const int k16 = k % k16n, rc = k / k16n;
+      const int row = rc % t.rows, ch = rc / t.rows;
+      const int ky = row % t.Tj, kz = row / t.Tj;
+      const int64_t roff = (int64_t)a.px8 * (ky + (int64_t)t.nc[1] * kz);
+      const unsigned char* zp = z8 + (int64_t)(t.plane0 + ch) * a.z8_nq * 128;
+      for (int j = 0; j < n_mt; ++j) {
+        const int64_t q0 = (L_start + 128 * j + roff + 16 * k16) / 8;
+        bulk_g2s(st + j * kATile, zp + q0 * 128, kATile, &full[s]);
+      }
+      bulk_g2s(st + L.b_in_stage, bsrc + (int64_t)k * b_bytes, b_bytes, &full[s]);
+      issued = k + 1;
+    }
+    if (flag[0]) {
+      // let the copies that may still be in flight land
+      for (int k = issued - kTcsStages > 0 ? issued - kTcsStages : 0; k < issued; ++k)
+        mbar_wait_bounded(&full[k % kTcsStages], (uint32_t)((k / kTcsStages) & 1));
+    }
+  } else if (tid == 32) {
+    const uint32_t idesc = instr_desc(BF16, 128, nt);
+    const uint32_t base = smem_u32(smem + L.stage_off);
+    for (int k = 0; k < ksteps; ++k) {
+      const int s = k % kTcsStages;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / kTcsStages) & 1))) {
+        flag[0] = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = base + (uint32_t)(s * L.stage_bytes);
+      const uint64_t bd = smem_desc(st + (uint32_t)L.b_in_stage, 128u, 256u);
+      for (int j = 0; j < n_mt; ++j) {
+        const uint64_t ad = smem_desc(st + (uint32_t)(j * kATile), 128u, 128u);
+        mma_f16(tmem + (uint32_t)(j * nt), ad, bd, idesc, k > 0 ? 1u : 0u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+    if (!mbar_wait_bounded(done, 0u)) flag[0] = 1;
+  }
+  __syncthreads();
+  const bool failed = flag[0] != 0;
+
+  // ---- epilogue: scores of one M-tile through shared memory; thread
+  // (item n, segment) keeps its item's K best keys in registers or writes
+  // the map --------------------------------------------------------------
+  if (!failed) {
+    mbar_try_wait(done, 0u);
+    tc_fence_after();
+    float* S = reinterpret_cast<float*>(smem + L.s_off);
+    int2* cand = reinterpret_cast<int2*>(smem + L.c_off);
+    const int sp = nt + 4;
+    for (int i = tid; i < n_mt * 128; i += kTcsThreads) {
+      const int64_t Lpos = L_start + i;
+      const int cx = (int)(Lpos % a.px8);
+      const int64_t rest = Lpos / a.px8;
+      const int cy = (int)(rest % t.nc[1]), cz = (int)(rest / t.nc[1]);
+      const bool valid = cx < t.cd[0] && cy < t.cd[1] && cz < t.cd[2];
+      cand[i] = make_int2(valid ? cx + t.cd[0] * (cy + t.cd[1] * cz) : -1,
+                          t.s * cx + t.n[0] * (t.s * cy + t.n[1] * (t.s * cz)));
+    }
+    const int n = tid % nt, nseg = kTcsThreads / nt, seg = tid / nt;
+    const int seg_len = 128 / nseg;
+    const int4 mt4 = meta[n];
+    const int item = ntile * nt + n;
+    const int2* hdl = reinterpret_cast<const int2*>(
+        a.ev.base + (int64_t)(item < a.n_items ? item : 0) * a.ev.stride + a.ev.hd_off);
+    uint64_t lst[kTcsRegK];
+#pragma unroll
+    for (int i = 0; i < kTcsRegK; ++i) lst[i] = kNoKey;
+    uint64_t worst = kNoKey;
+    const int m = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int half = nt / 2;
+#pragma unroll 1
+    for (int j = 0; j < n_mt; ++j) {
+#pragma unroll 1
+      for (int c0 = parity * half; c0 < (parity + 1) * half; c0 += 8) {
+        uint32_t v[8];
+        tmem_ld8(lane_base + (uint32_t)(j * nt + c0), v);
+        float4* dst = reinterpret_cast<float4*>(S + m * sp + c0);
+        dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]),
+                             __uint_as_float(v[2]), __uint_as_float(v[3]));
+        dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
+                             __uint_as_float(v[6]), __uint_as_float(v[7]));
+      }
+      __syncthreads();
+      if (mt4.w) {
+#pragma unroll 2
+        for (int r = seg * seg_len; r < (seg + 1) * seg_len; ++r) {
+          const int2 ci = cand[j * 128 + r];
+          if (ci.x < 0) continue;
+          const int score = __float2int_rn(S[r * sp + n]) + mt4.y;
+          int mis = 0;
+#pragma unroll 1
+          for (int k = 0; k < mt4.z; ++k) {
+            const int2 e = __ldg(hdl + k);
+            mis += (__ldg(t.ti + ci.y + e.x) != (uint8_t)(e.y & 0xFF));
+          }
+          if (MODE == kModeMap) {
+            a.map_score[(int64_t)item * t.P + ci.x] = mt4.x ? score : 0;
+            if (a.map_mis) a.map_mis[(int64_t)item * t.P + ci.x] = mt4.x ? mis : 0;
+            continue;
+          }
+          const uint64_t key = make_key(mis, score, ci.x);
+          if (key < worst) {
+            if (K == 1) {
+              lst[0] = key;
+              worst = key;
+            } else {
+              uint64_t x = key;
+#pragma unroll
+              for (int i = 0; i < kTcsRegK; ++i) {
+                const uint64_t lo = lst[i] < x ? lst[i] : x;
+                x = lst[i] < x ? x : lst[i];
+                lst[i] = lo;
+              }
+              worst = lst[0];
+#pragma unroll
+              for (int i = 1; i < kTcsRegK; ++i)
+                if (i < K) worst = lst[i];
+            }
+          }
+        }
+      }
+      __syncthreads();   // S is rewritten by the next M-tile
+    }
+    if (MODE != kModeMap) {
+      uint64_t* seglists = reinterpret_cast<uint64_t*>(S);
+#pragma unroll
+      for (int i = 0; i < kTcsRegK; ++i)
+        if (i < K) seglists[(seg * nt + n) * kTcsRegK + i] = lst[i];
+      __syncthreads();
+      for (int nn = warp; nn < nt; nn += kTcsThreads / 32) {
+        if (!meta[nn].w) continue;
+        const int item2 = ntile * nt + nn;
+        unsigned long long* part = a.part + ((int64_t)item2 * a.n_parts + mg) * K;
+        int head = 0;
+        const bool has = lane < nseg;
+        for (int r = 0; r < Kp; ++r) {
+          const uint64_t mine =
+              (has && head < Kp) ? seglists[(lane * nt + nn) * kTcsRegK + head] : kNoKey;
+          const uint64_t best = warp_min_u64(mine);
+          if (has && best != kNoKey && mine == best) ++head;
+          if (lane == 0) part[r] = best;
+        }
+      }
+    }
+  }
+  if (failed && tid == 0) atomicOr(a.status, kStatusTimeout);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+template <int MODE, bool BF16>
+static cudaError_t launch_t(const WaveArgs& a, int smem, bool pdl, cudaStream_t st) {
+  auto fn = k_ccf_tcs<MODE, BF16>;
+  static int configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  dim3 grid(a.n_mgroups, (a.n_items + a.nt - 1) / a.nt);
+  return launch_pdl(fn, grid, dim3(kTcsThreads), smem, st, pdl, a);
+}
+
+cudaError_t launch_ccf_tcs(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st) {
+  const bool bf = a.precision == 2;
+  if (mode == kModeSim)
+    return bf ? launch_t<kModeSim, true>(a, smem, pdl, st)
+              : launch_t<kModeSim, false>(a, smem, pdl, st);
+  if (mode == kModeSearch)
+    return bf ? launch_t<kModeSearch, true>(a, smem, pdl, st)
+              : launch_t<kModeSearch, false>(a, smem, pdl, st);
+  return bf ? launch_t<kModeMap, true>(a, smem, pdl, st)
+            : launch_t<kModeMap, false>(a, smem, pdl, st);
+}
+
+}  // namespace ccw

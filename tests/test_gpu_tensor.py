@@ -120,6 +120,64 @@ def test_tensor_precision_bounds(ccw):
         ccw.ccf_map(g, de, score_mode=1, precision=2)
     ti3 = synth.random_field_ti((20, 20, 20), 2, seed=1)
     g3 = ccw.TI(dev(ti3), 2, 1, 8, 2)
-    with pytest.raises(ccw.CCWError, match="2D"):
-        ccw.ccf_map(g3, torch.full((1, 8, 8, 8), 255, dtype=torch.uint8, device="cuda"),
-                    precision=1)
+    de3 = torch.full((1, 8, 8, 8), 255, dtype=torch.uint8, device="cuda")
+    ccw.ccf_search(g3, de3, k=8, precision=1)
+    with pytest.raises(ccw.CCWError, match="K <= 8"):
+        ccw.ccf_search(g3, de3, k=9, precision=1)
+
+
+CASES_3D = [
+    # name, TI factory, F, J, T, O
+    ("tube_j1", lambda: synth.tube_lobe_ti_3d(60, 50, 40, seed=5), 4, 1, 12, 2),
+    ("rand_j0", lambda: synth.random_field_ti((22, 26, 18), 3, seed=4), 3, 0, 6, 2),
+    ("rand_j2", lambda: synth.random_field_ti((48, 40, 44), 2, seed=6), 2, 2, 16, 4),
+]
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("case", CASES_3D, ids=[c[0] for c in CASES_3D])
+def test_streamed_tensor_ccf_3d_matches_oracle(ccw, case, precision):
+    """3D on the tensor cores (operands streamed through shared-memory
+    stages): maps and K = 1 / 5 searches equal the oracle's."""
+    name, mk, F, J, T, Ov = case
+    ti = mk()
+    rng = np.random.default_rng(len(name) + 7 * precision)
+    B = 19
+    de, hd = configs.structured_events(ti, T, Ov, B, rng, n_hd=2, F=F)
+    de[3] = 255
+    hd[3] = 255
+    g = ccw.TI(dev(ti), F, J, T, Ov)
+    o = O.OracleTI(ti, F, J)
+    sc, mm = ccw.ccf_map(g, dev(de), dev(hd), precision=precision)
+    sc, mm = sc.cpu().numpy(), mm.cpu().numpy()
+    for b in range(B):
+        ref = o.search(T, de[b], hd[b], K=1, maps=True)
+        assert np.array_equal(sc[b], ref["scores"]), f"score map {b}"
+        assert np.array_equal(mm[b], ref["mis"]), f"mismatch map {b}"
+    ctr = torch.from_numpy(np.stack([np.arange(B), np.arange(B) * 3], 1).astype(np.int32)).cuda()
+    for K in (1, 5):
+        res = ccw.ccf_search(g, dev(de), dev(hd), k=K, seed=17, ctr=ctr, precision=precision)
+        for b in range(B):
+            ref = o.search(T, de[b], hd[b], K=K, seed=17, r=b, p=3 * b)
+            n = ref["n"]
+            assert int(res["pick"][b]) == ref["pick"], f"pick {b} K {K}"
+            assert np.array_equal(res["topk_idx"][b][:n].cpu().numpy(), ref["topk_idx"])
+            assert np.array_equal(res["topk_score"][b][:n].cpu().numpy(), ref["topk_score"])
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_streamed_tensor_3d_simulation_bit_exact(ccw, precision):
+    """Whole 3D simulations with hard data on the streamed tensor-core CCF
+    equal the oracle's realizations and patch logs."""
+    ti = synth.tube_lobe_ti_3d(60, 50, 40, seed=5)
+    field = synth.tube_lobe_ti_3d(50, 44, 30, seed=6)
+    cells, vals = synth.sample_hard_data(field, 40, seed=7)
+    g = ccw.TI(dev(ti), 4, 1, 12, 2)
+    out, log = ccw.simulate(g, (50, 44, 30), n_real=2, topk=5, seed=9, hd_cells=dev(cells),
+                            hd_vals=dev(vals), path_random=1, precision=precision, want_log=True)
+    o = O.OracleTI(ti, 4, 1)
+    for i in range(2):
+        ref, rlog = o.simulate((50, 44, 30), 12, 2, K=5, path_random=1, hd_cells=cells,
+                               hd_vals=vals, seed=9, r=i)
+        assert np.array_equal(log.cpu().numpy()[i], rlog)
+        assert np.array_equal(out.cpu().numpy()[i], ref)
