@@ -27,7 +27,7 @@ cudaError_t launch_ccf_simt(int mode, const WaveArgs& a, const CUtensorMap& tmap
 int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K, int lane_epi);
 cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // tcs.cu
-int tcs_smem_bytes(int mt, int nt);
+int tcs_smem_bytes(int mt, int nt, int Tj, int px8, int k16n, int stages);
 cudaError_t launch_ccf_tcs(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // prepare.cu
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
@@ -340,8 +340,17 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
   if (hint) mt = (hint >> 16) & 0xFF;
   while (mt * a.nt > 512) --mt;
   for (;;) {
-    smem = streamed ? tcs_smem_bytes(mt, a.nt)
-                    : tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
+    if (streamed) {
+      // as many stages (2..3) as fit
+      a.tcs_stages = 3;
+      smem = tcs_smem_bytes(mt, a.nt, t->Tj, t->px8, t->ks / 16, 3);
+      if (smem > 220 * 1024) {
+        a.tcs_stages = 2;
+        smem = tcs_smem_bytes(mt, a.nt, t->Tj, t->px8, t->ks / 16, 2);
+      }
+    } else {
+      smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
+    }
     if (hint || smem <= 220 * 1024 || (mt == 1 && a.nt == 16)) break;
     if (mt > 1) --mt;
     else a.nt /= 2;
@@ -428,6 +437,7 @@ void apply_ccf(const ccw_ti* t, const CcfPlan& cp, void* bmat, WaveArgs& c) {
     c.nt = cp.tc.nt;
     c.a_nq = cp.tc.a_nq;
     c.tc_lane_epi = cp.tc.tc_lane_epi;
+    c.tcs_stages = cp.tc.tcs_stages;
     c.bmat = bmat;
   }
 }
@@ -761,7 +771,7 @@ int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3], i
         (int64_t)t->px8 * ((t->Tj - 1) + (ndim == 3 ? (int64_t)t->nc[1] * (t->Tj - 1) : 0));
     t->z8_nq = std::max<int64_t>(
         16LL * t->mtiles + 128 + (int64_t)(t->rows - 1) * t->px8 / 8 + 2 * (t->ks / 16) + 32,
-        (128LL * t->mtiles + roff_max + t->ks + 256) / 8 + 8);
+        (128LL * (t->mtiles + kTcMaxMt) + roff_max + t->ks + 256) / 8 + 8);
     const size_t zb = (size_t)t->F * t->z8_nq * 128;
     if ((e = cudaMalloc(&t->z8_f16, zb)) != cudaSuccess ||
         (e = cudaMalloc(&t->z8_bf16, zb)) != cudaSuccess) {

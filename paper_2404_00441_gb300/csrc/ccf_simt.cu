@@ -263,6 +263,22 @@ __global__ void __launch_bounds__(kThreads)
     const int nhd = meta[nb * 8 + kMNHd];
     const int2* hdl = reinterpret_cast<const int2*>(a.ev.base + (int64_t)item * a.ev.stride +
                                                     a.ev.hd_off);
+    // hard-data mismatches of the thread's candidates, loads overlapped
+    const uint8_t* tb0 =
+        t.ti + (int64_t)s * (cx0 + kRx * ltx) + (int64_t)t.n[0] * ((int64_t)s * cy + (int64_t)t.n[1] * s * cz);
+    const bool row_ok = cy < t.cd[1] && cz < t.cd[2];
+    int misv[kRx];
+#pragma unroll
+    for (int i = 0; i < kRx; ++i) misv[i] = 0;
+    if (row_ok) {
+      for (int k = 0; k < nhd; ++k) {
+        const int2 e = __ldg(hdl + k);
+#pragma unroll
+        for (int i = 0; i < kRx; ++i)
+          if (cx0 + kRx * ltx + i < t.cd[0])
+            misv[i] += (__ldg(tb0 + (int64_t)s * i + e.x) != (uint8_t)e.y);
+      }
+    }
     uint64_t keys[kRx];
 #pragma unroll
     for (int i = 0; i < kRx; ++i) {
@@ -270,13 +286,7 @@ __global__ void __launch_bounds__(kThreads)
       keys[i] = kNoKey;
       if (cx >= t.cd[0] || cy >= t.cd[1] || cz >= t.cd[2]) continue;
       const int score = __float2int_rn(acc[i][nb]) + cons;
-      const uint8_t* tb =
-          t.ti + (int64_t)s * cx + (int64_t)t.n[0] * ((int64_t)s * cy + (int64_t)t.n[1] * s * cz);
-      int mis = 0;
-      for (int k = 0; k < nhd; ++k) {
-        const int2 e = __ldg(hdl + k);
-        mis += (__ldg(tb + e.x) != (uint8_t)e.y);
-      }
+      const int mis = misv[i];
       const int c = cx + t.cd[0] * (cy + t.cd[1] * cz);
       if (MODE == kModeMap) {
         a.map_score[(int64_t)item * t.P + c] = known ? score : 0;

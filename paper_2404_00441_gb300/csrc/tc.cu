@@ -228,39 +228,9 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
                              __uint_as_float(v[6]), __uint_as_float(v[7]));
       }
       __syncthreads();
-      if (mt4.w) {
-#pragma unroll 2
-        for (int r = seg * seg_len; r < (seg + 1) * seg_len; ++r) {
-          const int2 ci = cand[j * 128 + r];
-          if (ci.x < 0) continue;
-          const int score = __float2int_rn(S[r * sp + n]) + mt4.y;
-          int mis = 0;
-#pragma unroll 1
-          for (int k = 0; k < mt4.z; ++k) {
-            const int2 e = __ldg(hdl + k);
-            mis += (__ldg(t.ti + ci.y + e.x) != (uint8_t)(e.y & 0xFF));
-          }
-          const uint64_t key = make_key(mis, score, ci.x);
-          if (key < worst) {
-            if (K == 1) {
-              lst[0] = key;
-              worst = key;
-            } else {
-              uint64_t x = key;
-#pragma unroll
-              for (int i = 0; i < kTcRegK; ++i) {
-                const uint64_t lo = lst[i] < x ? lst[i] : x;
-                x = lst[i] < x ? x : lst[i];
-                lst[i] = lo;
-              }
-              worst = lst[0];
-#pragma unroll
-              for (int i = 1; i < kTcRegK; ++i)
-                if (i < K) worst = lst[i];
-            }
-          }
-        }
-      }
+      if (mt4.w)
+        scan_segment<MODE, kTcRegK>(a, S, sp, n, cand + j * 128, seg * seg_len, seg_len, mt4,
+                                    hdl, item, K, lst, worst);
       __syncthreads();   // S is rewritten by the next M-tile
     }
     // segment lists -> shared memory (over S), then one warp per item merges
@@ -314,18 +284,25 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       const int item = ntile * nt + n;
       const int2* hdl = reinterpret_cast<const int2*>(a.ev.base + (int64_t)item * a.ev.stride +
                                                       a.ev.hd_off);
+      // hard-data mismatches of the M-tiles' candidates, loads overlapped
+      int misj[kTcMaxMt];
+#pragma unroll
+      for (int j = 0; j < kTcMaxMt; ++j) misj[j] = 0;
+#pragma unroll 1
+      for (int k = 0; k < mt4.z; ++k) {
+        const int2 e = __ldg(hdl + k);
+        const uint8_t code = (uint8_t)(e.y & 0xFF);
+#pragma unroll
+        for (int j = 0; j < kTcMaxMt; ++j)
+          if (cidx[j] >= 0) misj[j] += (__ldg(tb[j] + e.x) != code);
+      }
       uint64_t keys[kTcMaxMt];
 #pragma unroll
       for (int j = 0; j < kTcMaxMt; ++j) {
         keys[j] = kNoKey;
         if (cidx[j] < 0) continue;
         const int score = __float2int_rn(__uint_as_float(v[j])) + mt4.y;
-        int mis = 0;
-#pragma unroll 1
-        for (int k = 0; k < mt4.z; ++k) {
-          const int2 e = __ldg(hdl + k);
-          mis += (__ldg(tb[j] + e.x) != (uint8_t)(e.y & 0xFF));
-        }
+        const int mis = misj[j];
         if (MODE == kModeMap) {
           a.map_score[(int64_t)item * t.P + cidx[j]] = mt4.x ? score : 0;
           if (a.map_mis) a.map_mis[(int64_t)item * t.P + cidx[j]] = mt4.x ? mis : 0;

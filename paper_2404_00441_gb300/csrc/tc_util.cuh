@@ -107,4 +107,67 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+
+// Epilogue scan of the tensor-core CCF kernels: candidates r0 .. r0+len-1
+// (len a multiple of 8) of one M-tile for item column n. Scores come from
+// the shared-memory tile S (row pitch sp floats); `cand` holds (candidate
+// index or -1, offset of the candidate's first cell in the fine TI) per row.
+// Hard-data mismatches (Sec. 4.4) are counted for 8 candidates at a time so
+// that their TI loads overlap. Each key enters the thread's sorted list lst
+// (K <= KL best; `worst` is its K-th entry), or the map is written.
+template <int MODE, int KL>
+__device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, int sp, int n,
+                                             const int2* cand, int r0, int len, int4 mt4,
+                                             const int2* hdl, int64_t item, int K,
+                                             uint64_t (&lst)[KL], uint64_t& worst) {
+  const TiDev& t = a.ti;
+#pragma unroll 1
+  for (int rb = r0; rb < r0 + len; rb += 8) {
+    int2 ci[8];
+    int mis[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      ci[u] = cand[rb + u];
+      mis[u] = 0;
+    }
+#pragma unroll 1
+    for (int k = 0; k < mt4.z; ++k) {
+      const int2 e = __ldg(hdl + k);
+      const uint8_t code = (uint8_t)(e.y & 0xFF);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ci[u].x >= 0) mis[u] += (__ldg(t.ti + ci[u].y + e.x) != code);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (ci[u].x < 0) continue;
+      const int score = __float2int_rn(S[(rb + u) * sp + n]) + mt4.y;
+      if (MODE == kModeMap) {
+        a.map_score[item * t.P + ci[u].x] = mt4.x ? score : 0;
+        if (a.map_mis) a.map_mis[item * t.P + ci[u].x] = mt4.x ? mis[u] : 0;
+        continue;
+      }
+      const uint64_t key = make_key(mis[u], score, ci[u].x);
+      if (key < worst) {
+        if (K == 1) {
+          lst[0] = key;
+          worst = key;
+        } else {
+          uint64_t x = key;
+#pragma unroll
+          for (int i = 0; i < KL; ++i) {
+            const uint64_t lo = lst[i] < x ? lst[i] : x;
+            x = lst[i] < x ? x : lst[i];
+            lst[i] = lo;
+          }
+          worst = lst[0];
+#pragma unroll
+          for (int i = 1; i < KL; ++i)
+            if (i < K) worst = lst[i];
+        }
+      }
+    }
+  }
+}
+
 }  // namespace ccw

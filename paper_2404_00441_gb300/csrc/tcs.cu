@@ -9,12 +9,13 @@
 // M-tile, template row (ky, kz) and taps [16 k16, 16 k16 + 16):
 //   A[m, kx] = plane[L0 + m + px8 (ky + nc1 kz) + 16 k16 + kx],
 // whose 8 x 8 core matrices are the 17 consecutive entries q0 .. q0 + 16 of
-// the 8-shift copy z8 (q0 = (L0 + px8 (ky + nc1 kz) + 16 k16) / 8): one
-// contiguous bulk copy of 2176 bytes per M-tile and K step. The items' B
-// tile of the K step (canonical K-major, written by the event kernel) is one
-// more bulk copy. A ring of kTcsStages shared-memory stages is filled by one
-// producer thread and drained by one MMA thread; tcgen05.commit on a
-// stage's "empty" barrier hands it back to the producer. Accumulators: mt
+// the 8-shift copy z8 (q0 = (L0 + px8 (ky + nc1 kz) + 16 k16) / 8). A stage
+// holds one slice (channel, kz): the A operands of all its Tj rows, all
+// taps and the CTA's mt M-tiles are one contiguous run of the 8-shift copy
+// (one bulk copy), and the items' B tiles of its K steps (canonical K-major,
+// written by the event kernel) another. A ring of 2-3 shared-memory stages
+// is filled by one producer thread and drained by one MMA thread;
+// tcgen05.commit on a stage's "empty" barrier hands it back. Accumulators: mt
 // M-tiles x nt FP32 columns of tensor memory. Epilogue: per-thread K-lists
 // (K <= 8) as in tc.cu, or the full map.
 #include "tc_util.cuh"
@@ -22,15 +23,21 @@
 namespace ccw {
 
 constexpr int kTcsThreads = 256;
-constexpr int kTcsStages = 4;
+constexpr int kTcsMaxStages = 4;
 constexpr int kTcsRegK = 8;
-constexpr int kATile = 17 * 128;   // one M-tile's A operand of one K step
+
+// Core matrices of one stage's A run: mt M-tiles, Tj rows of pitch px8/8,
+// k16n groups of 16 taps.
+__host__ __device__ inline int tcs_a_nq(int mt, int Tj, int px8, int k16n) {
+  return 16 * (mt - 1) + (Tj - 1) * px8 / 8 + 2 * (k16n - 1) + 17;
+}
 
 struct TcsSmem {
   int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, bytes;
 };
 
-__host__ __device__ inline TcsSmem tcs_smem(int mt, int nt) {
+__host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int Tj, int px8, int k16n,
+                                            int stages) {
   TcsSmem L;
   int off = 0;
   L.bar_off = off;   // full[4], empty[4], done, TMEM slot, flags
@@ -38,9 +45,9 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt) {
   L.meta_off = off;
   off += ((nt * 16 + 127) / 128) * 128;
   L.stage_off = off;
-  L.b_in_stage = mt * kATile;   // a multiple of 128
-  L.stage_bytes = ((mt * kATile + 32 * nt + 127) / 128) * 128;
-  off += kTcsStages * L.stage_bytes;
+  L.b_in_stage = tcs_a_nq(mt, Tj, px8, k16n) * 128;   // a multiple of 128
+  L.stage_bytes = ((L.b_in_stage + Tj * k16n * 32 * nt + 127) / 128) * 128;
+  off += stages * L.stage_bytes;
   L.s_off = off;
   const int s_bytes = 128 * (nt + 4) * 4, l_bytes = kTcsThreads * kTcsRegK * 8;
   off += (((s_bytes > l_bytes ? s_bytes : l_bytes) + 127) / 128) * 128;
@@ -50,7 +57,9 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt) {
   return L;
 }
 
-int tcs_smem_bytes(int mt, int nt) { return tcs_smem(mt, nt).bytes; }
+int tcs_smem_bytes(int mt, int nt, int Tj, int px8, int k16n, int stages) {
+  return tcs_smem(mt, nt, Tj, px8, k16n, stages).bytes;
+}
 
 template <int MODE, bool BF16>
 __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__ WaveArgs a) {
@@ -59,7 +68,9 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const TiDev& t = a.ti;
   const int nt = a.nt, K = a.K;
-  const TcsSmem L = tcs_smem(a.mt, nt);
+  const int k16n = a.ks / 16;
+  const int stages = a.tcs_stages;
+  const TcsSmem L = tcs_smem(a.mt, nt, t.Tj, a.px8, k16n, stages);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   uint64_t* empty = full + 8;
   uint64_t* done = full + 16;
@@ -74,11 +85,14 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
   const int n_mt = min(a.mt, a.mtiles - mg * a.mt);
   const int Kp = (int)((int64_t)K < t.P ? K : t.P);
   const uint32_t b_bytes = 32u * (uint32_t)nt;
-  const int k16n = a.ks / 16;
   const int ksteps = a.ksteps;
+  const int kz_n = t.rows / t.Tj;              // 1 in 2D
+  const int n_slices = t.nch * kz_n;           // stages of work: (channel, kz)
+  const int kps = t.Tj * k16n;                 // K steps per slice
+  const uint32_t a_bytes = (uint32_t)L.b_in_stage;
 
   if (tid == 0) {
-    for (int s = 0; s < kTcsStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -119,55 +133,56 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // ---- K loop: producer (thread 0) and MMA issuer (thread 32) -------------
+  // ---- slice loop: producer (thread 0) and MMA issuer (thread 32) ---------
   if (tid == 0) {
     const unsigned char* z8 = reinterpret_cast<const unsigned char*>(a.z8);
     const unsigned char* bsrc =
         reinterpret_cast<const unsigned char*>(a.bmat) + (int64_t)ntile * ksteps * b_bytes;
     int issued = 0;
-    for (int k = 0; k < ksteps; ++k) {
-      const int s = k % kTcsStages;
-      if (k >= kTcsStages &&
-          !mbar_wait_bounded(&empty[s], (uint32_t)(((k / kTcsStages) - 1) & 1))) {
+    for (int i = 0; i < n_slices; ++i) {
+      const int s = i % stages;
+      if (i >= stages && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / stages) - 1) & 1))) {
         flag[0] = 1;
         break;
       }
       if (flag[0]) break;
       unsigned char* st = smem + L.stage_off + s * L.stage_bytes;
-      mbar_arrive_expect_tx(&full[s], (uint32_t)n_mt * kATile + b_bytes);
-      const int k16 = k % k16n, rc = k / k16n;
-      const int row = rc % t.rows, ch = rc / t.rows;
-      const int ky = row % t.Tj, kz = row / t.Tj;
-      const int64_t roff = (int64_t)a.px8 * (ky + (int64_t)t.nc[1] * kz);
-      const unsigned char* zp = z8 + (int64_t)(t.plane0 + ch) * a.z8_nq * 128;
-      for (int j = 0; j < n_mt; ++j) {
-        const int64_t q0 = (L_start + 128 * j + roff + 16 * k16) / 8;
-        bulk_g2s(st + j * kATile, zp + q0 * 128, kATile, &full[s]);
-      }
-      bulk_g2s(st + L.b_in_stage, bsrc + (int64_t)k * b_bytes, b_bytes, &full[s]);
-      issued = k + 1;
+      const uint32_t bb = (uint32_t)kps * b_bytes;
+      mbar_arrive_expect_tx(&full[s], a_bytes + bb);
+      const int ch = i / kz_n, kz = i % kz_n;
+      const int64_t q0 = (L_start + (int64_t)a.px8 * t.nc[1] * kz) / 8;
+      bulk_g2s(st, z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + q0) * 128, a_bytes, &full[s]);
+      bulk_g2s(st + L.b_in_stage, bsrc + (int64_t)i * kps * b_bytes, bb, &full[s]);
+      issued = i + 1;
     }
     if (flag[0]) {
       // let the copies that may still be in flight land
-      for (int k = issued - kTcsStages > 0 ? issued - kTcsStages : 0; k < issued; ++k)
-        mbar_wait_bounded(&full[k % kTcsStages], (uint32_t)((k / kTcsStages) & 1));
+      for (int i = issued - stages > 0 ? issued - stages : 0; i < issued; ++i)
+        mbar_wait_bounded(&full[i % stages], (uint32_t)((i / stages) & 1));
     }
   } else if (tid == 32) {
     const uint32_t idesc = instr_desc(BF16, 128, nt);
     const uint32_t base = smem_u32(smem + L.stage_off);
-    for (int k = 0; k < ksteps; ++k) {
-      const int s = k % kTcsStages;
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / kTcsStages) & 1))) {
+    const int row_q = a.px8 / 8;   // core matrices between template rows
+    for (int i = 0; i < n_slices; ++i) {
+      const int s = i % stages;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((i / stages) & 1))) {
         flag[0] = 1;
         break;
       }
       tc_fence_after();
       const uint32_t st = base + (uint32_t)(s * L.stage_bytes);
-      const uint64_t bd = smem_desc(st + (uint32_t)L.b_in_stage, 128u, 256u);
-      for (int j = 0; j < n_mt; ++j) {
-        const uint64_t ad = smem_desc(st + (uint32_t)(j * kATile), 128u, 128u);
-        mma_f16(tmem + (uint32_t)(j * nt), ad, bd, idesc, k > 0 ? 1u : 0u);
-      }
+      for (int ky = 0; ky < t.Tj; ++ky)
+        for (int k16 = 0; k16 < k16n; ++k16) {
+          const uint64_t bd = smem_desc(
+              st + (uint32_t)L.b_in_stage + (uint32_t)(ky * k16n + k16) * b_bytes, 128u, 256u);
+          const uint32_t acc = (i > 0 || ky > 0 || k16 > 0) ? 1u : 0u;
+          for (int j = 0; j < n_mt; ++j) {
+            const uint64_t ad =
+                smem_desc(st + (uint32_t)((16 * j + ky * row_q + 2 * k16) * 128), 128u, 128u);
+            mma_f16(tmem + (uint32_t)(j * nt), ad, bd, idesc, acc);
+          }
+        }
       mma_commit(&empty[s]);
     }
     mma_commit(done);
@@ -220,44 +235,9 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
                              __uint_as_float(v[6]), __uint_as_float(v[7]));
       }
       __syncthreads();
-      if (mt4.w) {
-#pragma unroll 2
-        for (int r = seg * seg_len; r < (seg + 1) * seg_len; ++r) {
-          const int2 ci = cand[j * 128 + r];
-          if (ci.x < 0) continue;
-          const int score = __float2int_rn(S[r * sp + n]) + mt4.y;
-          int mis = 0;
-#pragma unroll 1
-          for (int k = 0; k < mt4.z; ++k) {
-            const int2 e = __ldg(hdl + k);
-            mis += (__ldg(t.ti + ci.y + e.x) != (uint8_t)(e.y & 0xFF));
-          }
-          if (MODE == kModeMap) {
-            a.map_score[(int64_t)item * t.P + ci.x] = mt4.x ? score : 0;
-            if (a.map_mis) a.map_mis[(int64_t)item * t.P + ci.x] = mt4.x ? mis : 0;
-            continue;
-          }
-          const uint64_t key = make_key(mis, score, ci.x);
-          if (key < worst) {
-            if (K == 1) {
-              lst[0] = key;
-              worst = key;
-            } else {
-              uint64_t x = key;
-#pragma unroll
-              for (int i = 0; i < kTcsRegK; ++i) {
-                const uint64_t lo = lst[i] < x ? lst[i] : x;
-                x = lst[i] < x ? x : lst[i];
-                lst[i] = lo;
-              }
-              worst = lst[0];
-#pragma unroll
-              for (int i = 1; i < kTcsRegK; ++i)
-                if (i < K) worst = lst[i];
-            }
-          }
-        }
-      }
+      if (mt4.w)
+        scan_segment<MODE, kTcsRegK>(a, S, sp, n, cand + j * 128, seg * seg_len, seg_len, mt4,
+                                     hdl, item, K, lst, worst);
       __syncthreads();   // S is rewritten by the next M-tile
     }
     if (MODE != kModeMap) {
