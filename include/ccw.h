@@ -95,7 +95,8 @@ typedef struct {
                           mt * nt <= 512, epilogue e (0: per-thread K-lists
                           when K <= 8, 1: lanes on candidates), m = 1:
                           operands streamed through a ring of shared-memory
-                          stages (always so in 3D; K <= 8). An autotuner
+                          stages (always so in 3D; K <= 8), bit 26: three
+                          stages instead of two. An autotuner
                           picks it by timing
                           (paper_2404_00441_gb300.autotune). */
   int32_t reserved[2]; /* must be 0 */

@@ -36,7 +36,8 @@ def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
         else:
             # tensor cores: bit 24 = lanes-on-candidates epilogue, bit 25 =
             # streamed operands (the only form in 3D)
-            flags = (0, 1, 2) if ti.ndim == 2 else (2,)
+            # bit 26 = three stages in the streamed kernel (else two)
+            flags = (0, 1, 2, 6) if ti.ndim == 2 else (2, 6)
             for fl in flags:
                 for nt in (16, 32, 64, 128):
                     for mt in (1, 2, 4):

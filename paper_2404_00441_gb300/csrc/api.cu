@@ -341,13 +341,10 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
   while (mt * a.nt > 512) --mt;
   for (;;) {
     if (streamed) {
-      // as many stages (2..3) as fit
-      a.tcs_stages = 3;
-      smem = tcs_smem_bytes(mt, a.nt, t->Tj, t->px8, t->ks / 16, 3);
-      if (smem > 220 * 1024) {
-        a.tcs_stages = 2;
-        smem = tcs_smem_bytes(mt, a.nt, t->Tj, t->px8, t->ks / 16, 2);
-      }
+      // double-buffered slices (two CTAs can then share an SM); three
+      // stages on request (bit 26 of the hint)
+      a.tcs_stages = ((hint >> 26) & 1) ? 3 : 2;
+      smem = tcs_smem_bytes(mt, a.nt, t->Tj, t->px8, t->ks / 16, a.tcs_stages);
     } else {
       smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
     }
@@ -399,7 +396,7 @@ bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
                         : (hint == 1 || hint == 2 || hint == 4);
   const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, flags = hint >> 24;
   return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
-         mt * nt <= 512 && flags >= 0 && flags <= 3;
+         mt * nt <= 512 && flags >= 0 && flags <= 7;
 }
 
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
