@@ -36,8 +36,10 @@ def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
         else:
             # tensor cores: bit 24 = lanes-on-candidates epilogue, bit 25 =
             # streamed operands (the only form in 3D)
-            # bit 26 = three stages in the streamed kernel (else two)
-            flags = (0, 1, 2, 6) if ti.ndim == 2 else (2, 6)
+            # bit 26 = three stages in the streamed kernel (else two); bits
+            # 27-28 = template rows per stage Tj / 2^v
+            streamed = (2, 6, 2 | 8, 2 | 16, 6 | 8)
+            flags = (0, 1) + streamed if ti.ndim == 2 else streamed
             for fl in flags:
                 for nt in (16, 32, 64, 128):
                     for mt in (1, 2, 4):

@@ -27,7 +27,7 @@ cudaError_t launch_ccf_simt(int mode, const WaveArgs& a, const CUtensorMap& tmap
 int tc_smem_bytes(int nch, int a_nq, int ksteps, int nt, int K, int lane_epi);
 cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // tcs.cu
-int tcs_smem_bytes(int mt, int nt, int Tj, int px8, int k16n, int stages);
+int tcs_smem_bytes(int mt, int nt, int R, int px8, int k16n, int stages);
 cudaError_t launch_ccf_tcs(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
 // prepare.cu
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
@@ -344,7 +344,10 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
       // double-buffered slices (two CTAs can then share an SM); three
       // stages on request (bit 26 of the hint)
       a.tcs_stages = ((hint >> 26) & 1) ? 3 : 2;
-      smem = tcs_smem_bytes(mt, a.nt, t->Tj, t->px8, t->ks / 16, a.tcs_stages);
+      // rows per stage: Tj, or Tj split in 2 or 4 blocks (bits 27-28)
+      const int split = 1 << ((hint >> 27) & 3);
+      a.tcs_rows = (t->Tj + split - 1) / split;
+      smem = tcs_smem_bytes(mt, a.nt, a.tcs_rows, t->px8, t->ks / 16, a.tcs_stages);
     } else {
       smem = tc_smem_bytes(nch, tc_a_nq(t, mt), a.ksteps, a.nt, K, a.tc_lane_epi);
     }
@@ -396,7 +399,7 @@ bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
                         : (hint == 1 || hint == 2 || hint == 4);
   const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, flags = hint >> 24;
   return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
-         mt * nt <= 512 && flags >= 0 && flags <= 7;
+         mt * nt <= 512 && flags >= 0 && flags <= 23 && ((flags >> 3) & 3) != 3;
 }
 
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
@@ -435,6 +438,7 @@ void apply_ccf(const ccw_ti* t, const CcfPlan& cp, void* bmat, WaveArgs& c) {
     c.a_nq = cp.tc.a_nq;
     c.tc_lane_epi = cp.tc.tc_lane_epi;
     c.tcs_stages = cp.tc.tcs_stages;
+    c.tcs_rows = cp.tc.tcs_rows;
     c.bmat = bmat;
   }
 }

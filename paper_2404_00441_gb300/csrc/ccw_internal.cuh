@@ -181,6 +181,7 @@ struct WaveArgs {
   int a_nq;                 // core matrices of one channel's A region per CTA
   int tc_lane_epi;          // 1: epilogue with lanes on candidates (else per-thread lists)
   int tcs_stages;           // shared-memory stages of the streamed tensor-core kernel
+  int tcs_rows;             // template rows ky per stage of the streamed kernel
   void* bmat;               // [N-tiles][ksteps][nt/8][2][8][8] 16-bit weights
   // selection
   int K;

@@ -10,10 +10,10 @@
 //   A[m, kx] = plane[L0 + m + px8 (ky + nc1 kz) + 16 k16 + kx],
 // whose 8 x 8 core matrices are the 17 consecutive entries q0 .. q0 + 16 of
 // the 8-shift copy z8 (q0 = (L0 + px8 (ky + nc1 kz) + 16 k16) / 8). A stage
-// holds one slice (channel, kz): the A operands of all its Tj rows, all
-// taps and the CTA's mt M-tiles are one contiguous run of the 8-shift copy
-// (one bulk copy), and the items' B tiles of its K steps (canonical K-major,
-// written by the event kernel) another. A ring of 2-3 shared-memory stages
+// holds one slice (channel, kz, block of R consecutive rows ky): the A
+// operands of its rows, all taps and the CTA's mt M-tiles are one contiguous
+// run of the 8-shift copy (one bulk copy), and the items' B tiles of its K
+// steps (canonical K-major, written by the event kernel) another. A ring of 2-3 shared-memory stages
 // is filled by one producer thread and drained by one MMA thread;
 // tcgen05.commit on a stage's "empty" barrier hands it back. Accumulators: mt
 // M-tiles x nt FP32 columns of tensor memory. Epilogue: per-thread K-lists
@@ -26,17 +26,17 @@ constexpr int kTcsThreads = 256;
 constexpr int kTcsMaxStages = 4;
 constexpr int kTcsRegK = 8;
 
-// Core matrices of one stage's A run: mt M-tiles, Tj rows of pitch px8/8,
+// Core matrices of one stage's A run: mt M-tiles, R rows of pitch px8/8,
 // k16n groups of 16 taps.
-__host__ __device__ inline int tcs_a_nq(int mt, int Tj, int px8, int k16n) {
-  return 16 * (mt - 1) + (Tj - 1) * px8 / 8 + 2 * (k16n - 1) + 17;
+__host__ __device__ inline int tcs_a_nq(int mt, int R, int px8, int k16n) {
+  return 16 * (mt - 1) + (R - 1) * px8 / 8 + 2 * (k16n - 1) + 17;
 }
 
 struct TcsSmem {
   int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, bytes;
 };
 
-__host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int Tj, int px8, int k16n,
+__host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int k16n,
                                             int stages) {
   TcsSmem L;
   int off = 0;
@@ -45,8 +45,8 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int Tj, int px8, int
   L.meta_off = off;
   off += ((nt * 16 + 127) / 128) * 128;
   L.stage_off = off;
-  L.b_in_stage = tcs_a_nq(mt, Tj, px8, k16n) * 128;   // a multiple of 128
-  L.stage_bytes = ((L.b_in_stage + Tj * k16n * 32 * nt + 127) / 128) * 128;
+  L.b_in_stage = tcs_a_nq(mt, R, px8, k16n) * 128;   // a multiple of 128
+  L.stage_bytes = ((L.b_in_stage + R * k16n * 32 * nt + 127) / 128) * 128;
   off += stages * L.stage_bytes;
   L.s_off = off;
   const int s_bytes = 128 * (nt + 4) * 4, l_bytes = kTcsThreads * kTcsRegK * 8;
@@ -57,8 +57,8 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int Tj, int px8, int
   return L;
 }
 
-int tcs_smem_bytes(int mt, int nt, int Tj, int px8, int k16n, int stages) {
-  return tcs_smem(mt, nt, Tj, px8, k16n, stages).bytes;
+int tcs_smem_bytes(int mt, int nt, int R, int px8, int k16n, int stages) {
+  return tcs_smem(mt, nt, R, px8, k16n, stages).bytes;
 }
 
 template <int MODE, bool BF16>
@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
   const int nt = a.nt, K = a.K;
   const int k16n = a.ks / 16;
   const int stages = a.tcs_stages;
-  const TcsSmem L = tcs_smem(a.mt, nt, t.Tj, a.px8, k16n, stages);
+  const int R = a.tcs_rows;   // template rows ky per slice
+  const TcsSmem L = tcs_smem(a.mt, nt, R, a.px8, k16n, stages);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
   uint64_t* empty = full + 8;
   uint64_t* done = full + 16;
@@ -87,9 +88,8 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
   const uint32_t b_bytes = 32u * (uint32_t)nt;
   const int ksteps = a.ksteps;
   const int kz_n = t.rows / t.Tj;              // 1 in 2D
-  const int n_slices = t.nch * kz_n;           // stages of work: (channel, kz)
-  const int kps = t.Tj * k16n;                 // K steps per slice
-  const uint32_t a_bytes = (uint32_t)L.b_in_stage;
+  const int parts = (t.Tj + R - 1) / R;        // row blocks per (channel, kz)
+  const int n_slices = t.nch * kz_n * parts;   // stages of work: (channel, kz, block)
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -147,12 +147,16 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       }
       if (flag[0]) break;
       unsigned char* st = smem + L.stage_off + s * L.stage_bytes;
-      const uint32_t bb = (uint32_t)kps * b_bytes;
-      mbar_arrive_expect_tx(&full[s], a_bytes + bb);
-      const int ch = i / kz_n, kz = i % kz_n;
-      const int64_t q0 = (L_start + (int64_t)a.px8 * t.nc[1] * kz) / 8;
-      bulk_g2s(st, z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + q0) * 128, a_bytes, &full[s]);
-      bulk_g2s(st + L.b_in_stage, bsrc + (int64_t)i * kps * b_bytes, bb, &full[s]);
+      const int rb = i % parts, ck = i / parts;
+      const int ch = ck / kz_n, kz = ck % kz_n;
+      const int r0 = rb * R, ri = min(R, t.Tj - r0);   // rows ky of this slice
+      const uint32_t ab = (uint32_t)tcs_a_nq(a.mt, ri, a.px8, k16n) * 128u;
+      const uint32_t bb = (uint32_t)(ri * k16n) * b_bytes;
+      mbar_arrive_expect_tx(&full[s], ab + bb);
+      const int64_t q0 = (L_start + (int64_t)a.px8 * ((int64_t)t.nc[1] * kz + r0)) / 8;
+      const int64_t k0 = ((int64_t)ch * t.rows + (int64_t)kz * t.Tj + r0) * k16n;
+      bulk_g2s(st, z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + q0) * 128, ab, &full[s]);
+      bulk_g2s(st + L.b_in_stage, bsrc + k0 * b_bytes, bb, &full[s]);
       issued = i + 1;
     }
     if (flag[0]) {
@@ -172,7 +176,8 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       }
       tc_fence_after();
       const uint32_t st = base + (uint32_t)(s * L.stage_bytes);
-      for (int ky = 0; ky < t.Tj; ++ky)
+      const int ri = min(R, t.Tj - (i % parts) * R);
+      for (int ky = 0; ky < ri; ++ky)
         for (int k16 = 0; k16 < k16n; ++k16) {
           const uint64_t bd = smem_desc(
               st + (uint32_t)L.b_in_stage + (uint32_t)(ky * k16n + k16) * b_bytes, 128u, 256u);
