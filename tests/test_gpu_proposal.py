@@ -149,17 +149,19 @@ def test_tables_hold_every_window(ccw, ti):
     ti.attach_proposal(None)
 
 
-def run(ccw, ti, n_real, learned, seed=5, base=0):
+def run(ccw, ti, n_real, learned, seed=5, base=0, precision=0):
     return ccw.simulate_groups(ti, [dict(grid=GRID, n_real=n_real, real_base=base)], topk=1,
-                               seed=seed, want_log=True, want_counts=True, learned=learned)[0]
+                               seed=seed, want_log=True, want_counts=True, learned=learned,
+                               precision=precision)[0]
 
 
-def test_infinite_gap_threshold_is_the_plain_method(ccw, ti):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_infinite_gap_threshold_is_the_plain_method(ccw, ti, precision):
     net = ccw.Net(F, TJ, seed=1)
     ti.attach_proposal(net, 64, float("inf"))
-    po, pl, pc = run(ccw, ti, 4, 0)
+    po, pl, pc = run(ccw, ti, 4, 0, precision=precision)
     ti.proposal_stats()
-    lo, ll, lc = run(ccw, ti, 4, 1)
+    lo, ll, lc = run(ccw, ti, 4, 1, precision=precision)
     assert torch.equal(po, lo) and torch.equal(pl, ll) and torch.equal(pc, lc)
     n_known, n_prop, n_settled = ti.proposal_stats()
     searched = int(((pl[..., 3] & 1) == 0).sum().item())
@@ -176,10 +178,13 @@ def exact_scores(ccw, ti, counts):
     return np.concatenate(out)
 
 
-def test_settled_patches_take_the_exact_best_proposal(ccw, ti):
+@pytest.mark.parametrize("precision", [0, 2])
+def test_settled_patches_take_the_exact_best_proposal(ccw, ti, precision):
+    """The CCF kernels (FP32 lanes or tensor cores) skip settled patches; the
+    finish kernel takes their picks from the re-ranked proposals."""
     net = ccw.Net(F, TJ, seed=1)
     ti.attach_proposal(net, 64, -0.5)    # every patch with proposals is settled
-    out, log, counts = run(ccw, ti, 4, 1)
+    out, log, counts = run(ccw, ti, 4, 1, precision=precision)
     n_known, n_prop, n_settled = ti.proposal_stats()
     flags = log[..., 3].cpu().numpy()
     settled = (flags & ccw.LOG_FLAG_PROPOSAL) != 0
