@@ -161,7 +161,28 @@ __device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, i
   const int Tj = p.Tj;
   const int nrows = (D == 3) ? Tj * Tj : Tj;
   const int run = Tj * sd;   // coefficients per coarse row
-  if (sd % 4 == 0) {
+  if (sd % 4 == 0 && run / 4 <= nthreads) {
+    // rows in parallel: thread (r0, k) copies 8-byte word k of rows r0,
+    // r0 + rpp, ... (one division per thread)
+    const int run4 = run / 4;
+    const int rpp = nthreads / run4;
+    const int r0 = threadIdx.x / run4, k = threadIdx.x % run4;
+    if (r0 < rpp) {
+      int uy = r0 % Tj, uz = r0 / Tj;
+      for (int row = r0; row < nrows; row += rpp) {
+        const int16_t* src =
+            p.pyr +
+            ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
+        reinterpret_cast<uint2*>(sm + (int64_t)row * run)[k] =
+            __ldg(reinterpret_cast<const uint2*>(src) + k);
+        uy += rpp;
+        while (uy >= Tj) {
+          uy -= Tj;
+          ++uz;
+        }
+      }
+    }
+  } else if (sd % 4 == 0) {
     const int run4 = run / 4;
     for (int i = threadIdx.x; i < nrows * run4; i += nthreads) {
       const int row = i / run4, k = i % run4;

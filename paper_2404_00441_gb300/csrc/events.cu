@@ -74,15 +74,59 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
   for (int u = tid; u < ncells; u += nth) {
     const int ux = u % Tj, uy = (u / Tj) % Tj, uz = (D == 3) ? u / (Tj * Tj) : 0;
     uint64_t lo = 0, hi = 0;
+    int cf[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // facies counts (word path)
+    if (words) {
+      // a block row is one 32-bit word of 4 codes: count each facies with
+      // byte-wise compares (SWAR); hard data replace their bytes first
+      for (int cz = 0; cz < ((D == 3) ? 4 : 1); ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 4; ++cy) {
+          const int qy = uy * 4 + cy, qz = uz * 4 + cz;
+          const int gx0 = it.o[0] + ux * 4, gy = it.o[1] + qy, gz = it.o[2] + qz;
+          uint32_t vw = *reinterpret_cast<const uint32_t*>(
+              sg + gx0 + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz));
+          if (it.overlay) {   // the group has hard data
+            const int hy = gy - it.off[1], hz = gz - it.off[2];
+            uint32_t hw = 0xFFFFFFFFu;
+            if (hy >= 0 && hz >= 0 && hy < it.G[1] && hz < it.G[2]) {
+              const uint8_t* orow = it.overlay + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz);
+#pragma unroll
+              for (int cx = 0; cx < 4; ++cx) {
+                const int hx = gx0 + cx - it.off[0];
+                const uint32_t h = (hx >= 0 && hx < it.G[0]) ? __ldg(orow + hx) : 0xFFu;
+                hw = (hw & ~(0xFFu << (8 * cx))) | (h << (8 * cx));
+              }
+            }
+            if (hw != 0xFFFFFFFFu) {
+#pragma unroll
+              for (int cx = 0; cx < 4; ++cx) {
+                const uint32_t h = (hw >> (8 * cx)) & 0xFFu;
+                if (h == CCW_UNKNOWN) continue;
+                const int qx = ux * 4 + cx;
+                const int k = atomicAdd(&cnt[3], 1);
+                if (k < a.ev.hd_cap)
+                  hdl[k] = make_int2(qx + t.n[0] * (qy + t.n[1] * qz),
+                                     ((qx + T * (qy + T * qz)) << 8) | (int)h);
+                if (h >= (uint32_t)t.F) bad |= kStatusBadCode;
+              }
+              const uint32_t keep = __vcmpeq4(hw, 0xFFFFFFFFu);   // 0xFF: no hard datum
+              vw = (vw & keep) | (hw & ~keep);
+            }
+          }
+          int seen = __popc(__vcmpeq4(vw, 0xFFFFFFFFu)) >> 3;   // unknown cells
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            if (f >= t.F) break;
+            const int n = __popc(__vcmpeq4(vw, 0x01010101u * (uint32_t)f)) >> 3;
+            cf[f] += n;
+            seen += n;
+          }
+          if (seen != 4) bad |= kStatusBadCode;   // a code >= F
+        }
+    } else
     for (int cz = 0; cz < ((D == 3) ? s : 1); ++cz)
       for (int cy = 0; cy < s; ++cy) {
         const int qy = uy * s + cy, qz = uz * s + cz;
-        uint32_t word = 0;
-        if (words) {
-          const int gy = it.o[1] + qy, gz = it.o[2] + qz;
-          word = *reinterpret_cast<const uint32_t*>(
-              sg + it.o[0] + ux * s + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz));
-        }
 #pragma unroll 4
         for (int cx = 0; cx < s; ++cx) {
           const int qx = ux * s + cx;
@@ -94,8 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
               if (hx >= 0 && hy >= 0 && hz >= 0 && hx < it.G[0] && hy < it.G[1] && hz < it.G[2])
                 h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
             }
-            v = words ? (uint8_t)(word >> (8 * cx))
-                      : sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
+            v = sg[gx + (int64_t)it.Gp[0] * (gy + (int64_t)it.Gp[1] * gz)];
             if (h != CCW_UNKNOWN) v = h;
           } else {
             const int q = qx + T * (qy + T * qz);
@@ -124,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
       if (f >= t.F) break;
-      const int b = (int)(((f < 4 ? lo : hi) >> (16 * (f & 3))) & 0xFFFF);
+      const int b = words ? cf[f] : (int)(((f < 4 ? lo : hi) >> (16 * (f & 3))) & 0xFFFF);
       counts[f * ncells + u] = b;
       c += b;
       csum += f * b;

@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
                                                      int staged_bytes) {
   __shared__ uint64_t red[2][kWarps + 1];
   __shared__ uint64_t topk[CCW_MAX_TOPK];
+  __shared__ uint64_t sel_sh;
   extern __shared__ __align__(16) int16_t staged[];
   const TiDev& t = a.ti;
   const int tid = threadIdx.x;
@@ -84,8 +85,10 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     cr = a.ctr[2 * item];
     cp = a.ctr[2 * item + 1];
   }
-  const uint32_t u = draw_word(seed, cr, cp, 0u);
-  const uint64_t sel = topk[(int)mul_shift(u, Kp)];
+  // the Philox draw of Algorithm 1 line 12, once per item
+  if (tid == 0) sel_sh = topk[(int)mul_shift(draw_word(seed, cr, cp, 0u), Kp)];
+  __syncthreads();
+  const uint64_t sel = sel_sh;
   const int pk = key_index(sel);
   if (MODE == kModeSearch) {
     if (tid < K) {
