@@ -109,12 +109,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
 
 
 // Epilogue scan of the tensor-core CCF kernels: candidates r0 .. r0+len-1
-// (len a multiple of 8) of one M-tile for item column n. Scores come from
+// (len a multiple of kScanBatch) of one M-tile for item column n. Scores come from
 // the shared-memory tile S (row pitch sp floats); `cand` holds (candidate
 // index or -1, offset of the candidate's first cell in the fine TI) per row.
-// Hard-data mismatches (Sec. 4.4) are counted for 8 candidates at a time so
-// that their TI loads overlap. Each key enters the thread's sorted list lst
+// Hard-data mismatches (Sec. 4.4) are counted for kScanBatch candidates at a
+// time so that their TI loads overlap. Each key enters the thread's sorted list lst
 // (K <= KL best; `worst` is its K-th entry), or the map is written.
+constexpr int kScanBatch = 4;
+
 template <int MODE, int KL>
 __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, int sp, int n,
                                              const int2* cand, int r0, int len, int4 mt4,
@@ -122,11 +124,11 @@ __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, 
                                              uint64_t (&lst)[KL], uint64_t& worst) {
   const TiDev& t = a.ti;
 #pragma unroll 1
-  for (int rb = r0; rb < r0 + len; rb += 8) {
-    int2 ci[8];
-    int mis[8];
+  for (int rb = r0; rb < r0 + len; rb += kScanBatch) {
+    int2 ci[kScanBatch];
+    int mis[kScanBatch];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kScanBatch; ++u) {
       ci[u] = cand[rb + u];
       mis[u] = 0;
     }
@@ -135,11 +137,11 @@ __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, 
       const int2 e = __ldg(hdl + k);
       const uint8_t code = (uint8_t)(e.y & 0xFF);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < kScanBatch; ++u)
         if (ci[u].x >= 0) mis[u] += (__ldg(t.ti + ci[u].y + e.x) != code);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kScanBatch; ++u) {
       if (ci[u].x < 0) continue;
       const int score = __float2int_rn(S[(rb + u) * sp + n]) + mt4.y;
       if (MODE == kModeMap) {

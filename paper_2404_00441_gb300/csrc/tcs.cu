@@ -49,7 +49,8 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int 
   L.stage_bytes = ((L.b_in_stage + R * k16n * 32 * nt + 127) / 128) * 128;
   off += stages * L.stage_bytes;
   L.s_off = off;
-  const int s_bytes = 128 * (nt + 4) * 4, l_bytes = kTcsThreads * kTcsRegK * 8;
+  const int ntc = nt < 32 ? nt : 32;   // items per epilogue chunk
+  const int s_bytes = 128 * (ntc + 4) * 4, l_bytes = kTcsThreads * kTcsRegK * 8;
   off += (((s_bytes > l_bytes ? s_bytes : l_bytes) + 127) / 128) * 128;
   L.c_off = off;
   off += kTcMaxMt * 128 * 8;
@@ -204,7 +205,6 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
     tc_fence_after();
     float* S = reinterpret_cast<float*>(smem + L.s_off);
     int2* cand = reinterpret_cast<int2*>(smem + L.c_off);
-    const int sp = nt + 4;
     for (int i = tid; i < n_mt * 128; i += kTcsThreads) {
       const int64_t Lpos = L_start + i;
       const int cx = (int)(Lpos % a.px8);
@@ -214,56 +214,65 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       cand[i] = make_int2(valid ? cx + t.cd[0] * (cy + t.cd[1] * cz) : -1,
                           t.s * cx + t.n[0] * (t.s * cy + t.n[1] * (t.s * cz)));
     }
-    const int n = tid % nt, nseg = kTcsThreads / nt, seg = tid / nt;
+    // items in chunks of ntc columns: the score tile stays small for any nt
+    const int ntc = nt < 32 ? nt : 32;
+    const int spc = ntc + 4;
+    const int n = tid % ntc, nseg = kTcsThreads / ntc, seg = tid / ntc;
     const int seg_len = 128 / nseg;
-    const int4 mt4 = meta[n];
-    const int item = ntile * nt + n;
-    const int2* hdl = reinterpret_cast<const int2*>(
-        a.ev.base + (int64_t)(item < a.n_items ? item : 0) * a.ev.stride + a.ev.hd_off);
-    uint64_t lst[kTcsRegK];
-#pragma unroll
-    for (int i = 0; i < kTcsRegK; ++i) lst[i] = kNoKey;
-    uint64_t worst = kNoKey;
     const int m = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    const int half = nt / 2;
+    const int half = ntc / 2;
+    uint64_t* seglists = reinterpret_cast<uint64_t*>(S);
 #pragma unroll 1
-    for (int j = 0; j < n_mt; ++j) {
-#pragma unroll 1
-      for (int c0 = parity * half; c0 < (parity + 1) * half; c0 += 8) {
-        uint32_t v[8];
-        tmem_ld8(lane_base + (uint32_t)(j * nt + c0), v);
-        float4* dst = reinterpret_cast<float4*>(S + m * sp + c0);
-        dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]),
-                             __uint_as_float(v[2]), __uint_as_float(v[3]));
-        dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
-                             __uint_as_float(v[6]), __uint_as_float(v[7]));
-      }
-      __syncthreads();
-      if (mt4.w)
-        scan_segment<MODE, kTcsRegK>(a, S, sp, n, cand + j * 128, seg * seg_len, seg_len, mt4,
-                                     hdl, item, K, lst, worst);
-      __syncthreads();   // S is rewritten by the next M-tile
-    }
-    if (MODE != kModeMap) {
-      uint64_t* seglists = reinterpret_cast<uint64_t*>(S);
+    for (int cc = 0; cc < nt / ntc; ++cc) {
+      const int col = cc * ntc + n;
+      const int4 mt4 = meta[col];
+      const int item = ntile * nt + col;
+      const int2* hdl = reinterpret_cast<const int2*>(
+          a.ev.base + (int64_t)(item < a.n_items ? item : 0) * a.ev.stride + a.ev.hd_off);
+      uint64_t lst[kTcsRegK];
 #pragma unroll
-      for (int i = 0; i < kTcsRegK; ++i)
-        if (i < K) seglists[(seg * nt + n) * kTcsRegK + i] = lst[i];
-      __syncthreads();
-      for (int nn = warp; nn < nt; nn += kTcsThreads / 32) {
-        if (!meta[nn].w) continue;
-        const int item2 = ntile * nt + nn;
-        unsigned long long* part = a.part + ((int64_t)item2 * a.n_parts + mg) * K;
-        int head = 0;
-        const bool has = lane < nseg;
-        for (int r = 0; r < Kp; ++r) {
-          const uint64_t mine =
-              (has && head < Kp) ? seglists[(lane * nt + nn) * kTcsRegK + head] : kNoKey;
-          const uint64_t best = warp_min_u64(mine);
-          if (has && best != kNoKey && mine == best) ++head;
-          if (lane == 0) part[r] = best;
+      for (int i = 0; i < kTcsRegK; ++i) lst[i] = kNoKey;
+      uint64_t worst = kNoKey;
+#pragma unroll 1
+      for (int j = 0; j < n_mt; ++j) {
+#pragma unroll 1
+        for (int c0 = parity * half; c0 < (parity + 1) * half; c0 += 8) {
+          uint32_t v[8];
+          tmem_ld8(lane_base + (uint32_t)(j * nt + cc * ntc + c0), v);
+          float4* dst = reinterpret_cast<float4*>(S + m * spc + c0);
+          dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]),
+                               __uint_as_float(v[2]), __uint_as_float(v[3]));
+          dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
+                               __uint_as_float(v[6]), __uint_as_float(v[7]));
         }
+        __syncthreads();
+        if (mt4.w)
+          scan_segment<MODE, kTcsRegK>(a, S, spc, n, cand + j * 128, seg * seg_len, seg_len,
+                                       mt4, hdl, item, K, lst, worst);
+        __syncthreads();   // S is rewritten next
+      }
+      if (MODE != kModeMap) {
+        // segment lists of the chunk's items (over S), one warp per item merges
+#pragma unroll
+        for (int i = 0; i < kTcsRegK; ++i)
+          if (i < K) seglists[(seg * ntc + n) * kTcsRegK + i] = lst[i];
+        __syncthreads();
+        for (int nn = warp; nn < ntc; nn += kTcsThreads / 32) {
+          if (!meta[cc * ntc + nn].w) continue;
+          const int item2 = ntile * nt + cc * ntc + nn;
+          unsigned long long* part = a.part + ((int64_t)item2 * a.n_parts + mg) * K;
+          int head = 0;
+          const bool has = lane < nseg;
+          for (int r = 0; r < Kp; ++r) {
+            const uint64_t mine =
+                (has && head < Kp) ? seglists[(lane * ntc + nn) * kTcsRegK + head] : kNoKey;
+            const uint64_t best = warp_min_u64(mine);
+            if (has && best != kNoKey && mine == best) ++head;
+            if (lane == 0) part[r] = best;
+          }
+        }
+        __syncthreads();   // the lists' space is the next chunk's score tile
       }
     }
   }
