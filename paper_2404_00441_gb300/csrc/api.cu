@@ -1050,9 +1050,9 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   pl->cp = cp;
   plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
   if (cp->smem > 220 * 1024) {
+    const int need = cp->smem;   // the plan owns cp
     delete pl;
-    return fail(CCW_EINVAL, "ccf_tile 0x%x needs %d bytes of shared memory", p->ccf_tile,
-                cp->smem);
+    return fail(CCW_EINVAL, "ccf_tile 0x%x needs %d bytes of shared memory", p->ccf_tile, need);
   }
   cudaError_t e = cudaSuccess;
   for (auto& g : pl->groups) {

@@ -115,13 +115,46 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // Hard-data mismatches (Sec. 4.4) are counted for kScanBatch candidates at a
 // time so that their TI loads overlap. Each key enters the thread's sorted list lst
 // (K <= KL best; `worst` is its K-th entry), or the map is written.
+
+// Hard-data mismatches (Sec. 4.4) of one M-tile's 128 candidates for the
+// items in columns c0 .. c0+ntc-1, into the uint16 tile Mt[row][column]
+// (pitch spm): each warp takes items in turn, its lanes take candidates, so
+// the TI loads of a warp are consecutive cells (coalesced).
+__device__ __forceinline__ void mismatch_tile(const WaveArgs& a, const int4* meta, int ntile,
+                                              int nt, int c0, int ntc, const int2* cand,
+                                              uint16_t* Mt, int spm) {
+  const TiDev& t = a.ti;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int2 cr[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cr[i] = cand[lane + 32 * i];
+  for (int nl = warp; nl < ntc; nl += nw) {
+    const int4 q = meta[c0 + nl];
+    if (!q.w || q.z == 0) continue;
+    const int2* hd = reinterpret_cast<const int2*>(
+        a.ev.base + (int64_t)(ntile * nt + c0 + nl) * a.ev.stride + a.ev.hd_off);
+    int mv[4] = {0, 0, 0, 0};
+#pragma unroll 1
+    for (int k = 0; k < q.z; ++k) {
+      const int2 e = __ldg(hd + k);
+      const uint8_t code = (uint8_t)(e.y & 0xFF);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (cr[i].x >= 0) mv[i] += (__ldg(t.ti + cr[i].y + e.x) != code);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Mt[(lane + 32 * i) * spm + nl] = (uint16_t)min(mv[i], 0xFFFF);
+  }
+}
+
 constexpr int kScanBatch = 4;
 
 template <int MODE, int KL>
 __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, int sp, int n,
                                              const int2* cand, int r0, int len, int4 mt4,
                                              const int2* hdl, int64_t item, int K,
-                                             uint64_t (&lst)[KL], uint64_t& worst) {
+                                             uint64_t (&lst)[KL], uint64_t& worst,
+                                             const uint16_t* Mt = nullptr, int spm = 0) {
   const TiDev& t = a.ti;
 #pragma unroll 1
   for (int rb = r0; rb < r0 + len; rb += kScanBatch) {
@@ -130,10 +163,10 @@ __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, 
 #pragma unroll
     for (int u = 0; u < kScanBatch; ++u) {
       ci[u] = cand[rb + u];
-      mis[u] = 0;
+      mis[u] = (Mt && mt4.z) ? Mt[(rb + u) * spm + n] : 0;   // counted beforehand
     }
 #pragma unroll 1
-    for (int k = 0; k < mt4.z; ++k) {
+    for (int k = 0; k < (Mt ? 0 : mt4.z); ++k) {
       const int2 e = __ldg(hdl + k);
       const uint8_t code = (uint8_t)(e.y & 0xFF);
 #pragma unroll

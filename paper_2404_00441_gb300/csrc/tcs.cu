@@ -33,7 +33,7 @@ __host__ __device__ inline int tcs_a_nq(int mt, int R, int px8, int k16n) {
 }
 
 struct TcsSmem {
-  int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, bytes;
+  int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, m_off, bytes;
 };
 
 __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int k16n,
@@ -54,6 +54,15 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int 
   off += (((s_bytes > l_bytes ? s_bytes : l_bytes) + 127) / 128) * 128;
   L.c_off = off;
   off += kTcMaxMt * 128 * 8;
+  // uint16 mismatch tile [128][ntc + 2] of the epilogue: over the stages
+  // (idle once every MMA has completed) when they are large enough
+  const int m_bytes = 128 * (ntc + 2) * 2;
+  if (stages * L.stage_bytes >= m_bytes) {
+    L.m_off = L.stage_off;
+  } else {
+    L.m_off = off;
+    off += ((m_bytes + 127) / 128) * 128;
+  }
   L.bytes = off + 128;   // slack for aligning the dynamic shared memory base
   return L;
 }
@@ -214,6 +223,7 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       cand[i] = make_int2(valid ? cx + t.cd[0] * (cy + t.cd[1] * cz) : -1,
                           t.s * cx + t.n[0] * (t.s * cy + t.n[1] * (t.s * cz)));
     }
+    __syncthreads();   // cand is read by every warp from here on
     // items in chunks of ntc columns: the score tile stays small for any nt
     const int ntc = nt < 32 ? nt : 32;
     const int spc = ntc + 4;
@@ -223,6 +233,7 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const int half = ntc / 2;
     uint64_t* seglists = reinterpret_cast<uint64_t*>(S);
+    uint16_t* Mt = reinterpret_cast<uint16_t*>(smem + L.m_off);
 #pragma unroll 1
     for (int cc = 0; cc < nt / ntc; ++cc) {
       const int col = cc * ntc + n;
@@ -234,6 +245,10 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
 #pragma unroll
       for (int i = 0; i < kTcsRegK; ++i) lst[i] = kNoKey;
       uint64_t worst = kNoKey;
+      // the same decision in every thread: hard data per item of the chunk
+      int hd_sum = 0;
+      for (int i = 0; i < ntc; ++i) hd_sum += meta[cc * ntc + i].z;
+      const bool hd_tile = hd_sum >= 2 * ntc;
 #pragma unroll 1
       for (int j = 0; j < n_mt; ++j) {
 #pragma unroll 1
@@ -246,10 +261,13 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
           dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
                                __uint_as_float(v[6]), __uint_as_float(v[7]));
         }
+        // many hard data: count mismatches with coalesced loads first
+        if (hd_tile) mismatch_tile(a, meta, ntile, nt, cc * ntc, ntc, cand + j * 128, Mt, ntc + 2);
         __syncthreads();
         if (mt4.w)
           scan_segment<MODE, kTcsRegK>(a, S, spc, n, cand + j * 128, seg * seg_len, seg_len,
-                                       mt4, hdl, item, K, lst, worst);
+                                       mt4, hdl, item, K, lst, worst, hd_tile ? Mt : nullptr,
+                                       ntc + 2);
         __syncthreads();   // S is rewritten next
       }
       if (MODE != kModeMap) {
