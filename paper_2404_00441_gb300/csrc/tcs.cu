@@ -101,6 +101,20 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
   const int parts = (t.Tj + R - 1) / R;        // row blocks per (channel, kz)
   const int n_slices = t.nch * kz_n * parts;   // stages of work: (channel, kz, block)
 
+  // geometry of slice i: channel, rows r0 .. r0 + ri - 1 at kz; bytes of its
+  // A run and B tiles; first core matrix of the A run; first K step
+  const unsigned char* z8 = reinterpret_cast<const unsigned char*>(a.z8);
+  auto slice = [&](int i, uint32_t& ab, uint32_t& bb, const unsigned char*& asrc,
+                   int64_t& k0) {
+    const int rb = i % parts, ck = i / parts;
+    const int ch = ck / kz_n, kz = ck % kz_n;
+    const int r0 = rb * R, ri = min(R, t.Tj - r0);
+    ab = (uint32_t)tcs_a_nq(a.mt, ri, a.px8, k16n) * 128u;
+    bb = (uint32_t)(ri * k16n) * b_bytes;
+    const int64_t q0 = (L_start + (int64_t)a.px8 * ((int64_t)t.nc[1] * kz + r0)) / 8;
+    asrc = z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + q0) * 128;
+    k0 = ((int64_t)ch * t.rows + (int64_t)kz * t.Tj + r0) * k16n;
+  };
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
@@ -109,6 +123,16 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
     mbar_init(done, 1);
     fence_mbar_init();
     flag[0] = 0;
+    // the A runs of the first slices (the TI, not this step's data) load
+    // while the previous kernel finishes
+    for (int i = 0; i < stages && i < n_slices; ++i) {
+      uint32_t ab, bb;
+      const unsigned char* asrc;
+      int64_t k0;
+      slice(i, ab, bb, asrc, k0);
+      mbar_arrive_expect_tx(&full[i], ab + bb);
+      bulk_g2s(smem + L.stage_off + i * L.stage_bytes, asrc, ab, &full[i]);
+    }
   }
   pdl_trigger();
   pdl_wait();   // event records and B operands of this step are complete
@@ -145,7 +169,6 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
 
   // ---- slice loop: producer (thread 0) and MMA issuer (thread 32) ---------
   if (tid == 0) {
-    const unsigned char* z8 = reinterpret_cast<const unsigned char*>(a.z8);
     const unsigned char* bsrc =
         reinterpret_cast<const unsigned char*>(a.bmat) + (int64_t)ntile * ksteps * b_bytes;
     int issued = 0;
@@ -157,15 +180,14 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       }
       if (flag[0]) break;
       unsigned char* st = smem + L.stage_off + s * L.stage_bytes;
-      const int rb = i % parts, ck = i / parts;
-      const int ch = ck / kz_n, kz = ck % kz_n;
-      const int r0 = rb * R, ri = min(R, t.Tj - r0);   // rows ky of this slice
-      const uint32_t ab = (uint32_t)tcs_a_nq(a.mt, ri, a.px8, k16n) * 128u;
-      const uint32_t bb = (uint32_t)(ri * k16n) * b_bytes;
-      mbar_arrive_expect_tx(&full[s], ab + bb);
-      const int64_t q0 = (L_start + (int64_t)a.px8 * ((int64_t)t.nc[1] * kz + r0)) / 8;
-      const int64_t k0 = ((int64_t)ch * t.rows + (int64_t)kz * t.Tj + r0) * k16n;
-      bulk_g2s(st, z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + q0) * 128, ab, &full[s]);
+      uint32_t ab, bb;
+      const unsigned char* asrc;
+      int64_t k0;
+      slice(i, ab, bb, asrc, k0);
+      if (i >= stages) {   // the first slices' A runs are already on their way
+        mbar_arrive_expect_tx(&full[s], ab + bb);
+        bulk_g2s(st, asrc, ab, &full[s]);
+      }
       bulk_g2s(st + L.b_in_stage, bsrc + k0 * b_bytes, bb, &full[s]);
       issued = i + 1;
     }
