@@ -628,3 +628,21 @@ cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, floa
   return cudaGetLastError();
 }
 }  // namespace ccw
+
+namespace ccw {
+// Round the weights (not the biases) of an encoder to BF16 values in place:
+// the inference passes then read BF16 weights without converting.
+__global__ void k_round_weights(float* p, NetShape s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool bias = (i >= s.o_b1 && i < s.o_b1 + 32) || (i >= s.o_b2 && i < s.o_b2 + 32) ||
+                      (i >= s.o_b3 && i < s.o_b3 + 32) || i >= s.o_bf;
+    if (!bias) p[i] = __bfloat162float(__float2bfloat16_rn(p[i]));
+  }
+}
+
+cudaError_t launch_round_weights(float* p, int C, int tj, cudaStream_t st) {
+  k_round_weights<<<64, 256, 0, st>>>(p, net_shape(C, tj));
+  return cudaGetLastError();
+}
+}  // namespace ccw

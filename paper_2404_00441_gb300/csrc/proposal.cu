@@ -14,30 +14,6 @@ namespace ccw {
 cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
                       float* emb, cudaStream_t st);
 
-struct EncShape {
-  int C, tj, h2, h3, flat;
-  int o_w1, o_b1, o_w2, o_b2, o_w3, o_b3, o_wf, o_bf;
-};
-
-__host__ __device__ inline EncShape enc_shape(int C, int tj) {
-  EncShape s;
-  s.C = C;
-  s.tj = tj;
-  s.h2 = (tj - 1) / 2 + 1;
-  s.h3 = (s.h2 - 1) / 2 + 1;
-  s.flat = 32 * s.h3 * s.h3;
-  int o = 0;
-  s.o_w1 = o; o += 32 * C * 9;
-  s.o_b1 = o; o += 32;
-  s.o_w2 = o; o += 32 * 32 * 9;
-  s.o_b2 = o; o += 32;
-  s.o_w3 = o; o += 32 * 32 * 9;
-  s.o_b3 = o; o += 32;
-  s.o_wf = o; o += 64 * s.flat;
-  s.o_bf = o;
-  return s;
-}
-
 // Is level-J cell (ux, uy) inside the overlap strips of mask type `type`?
 __device__ __forceinline__ bool in_mask(int type, int ux, int uy, int Tj, int Oj) {
   return ((type & 1) && ux < Oj) || ((type & 2) && ux >= Tj - Oj) || ((type & 4) && uy < Oj) ||
@@ -124,21 +100,6 @@ __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restri
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = __float2bfloat16_rn(src[i]);
-}
-
-// Round the weights (not the biases) of an encoder to BF16 values in place.
-__global__ void k_round_weights(float* p, EncShape s) {
-  const int total = s.o_bf + 64;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const bool bias = (i >= s.o_b1 && i < s.o_b1 + 32) || (i >= s.o_b2 && i < s.o_b2 + 32) ||
-                      (i >= s.o_b3 && i < s.o_b3 + 32) || i >= s.o_bf;
-    if (!bias) p[i] = bf(p[i]);
-  }
-}
-
-cudaError_t launch_round_weights(float* p, int C, int tj, cudaStream_t st) {
-  k_round_weights<<<64, 256, 0, st>>>(p, enc_shape(C, tj));
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -40,7 +40,7 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int 
                                             int stages) {
   TcsSmem L;
   int off = 0;
-  L.bar_off = off;   // full[4], empty[4], done, TMEM slot, flags
+  L.bar_off = off;   // full[kTcsMaxStages], empty[...], done, TMEM slot, flags
   off += 256;
   L.meta_off = off;
   off += ((nt * 16 + 127) / 128) * 128;
@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
   const int R = a.tcs_rows;   // template rows ky per slice
   const TcsSmem L = tcs_smem(a.mt, nt, R, a.px8, k16n, stages);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
-  uint64_t* empty = full + 8;
-  uint64_t* done = full + 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 17);
-  volatile int* flag = reinterpret_cast<volatile int*>(full + 18);
+  uint64_t* empty = full + kTcsMaxStages;
+  uint64_t* done = full + 2 * kTcsMaxStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 2 * kTcsMaxStages + 1);
+  volatile int* flag = reinterpret_cast<volatile int*>(full + 2 * kTcsMaxStages + 2);
   int4* meta = reinterpret_cast<int4*>(smem + L.meta_off);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
