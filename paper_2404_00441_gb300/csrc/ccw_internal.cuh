@@ -17,7 +17,7 @@ enum : int {
   kStatusTimeout = 4,
 };
 
-constexpr int kThreads = 256;     // threads per CTA of the CCF and event kernels
+constexpr int kThreads = 256;     // threads per CTA (at most, for event and finish kernels)
 constexpr int kWarps = kThreads / 32;
 constexpr int kRx = 4;            // consecutive x-candidates per thread
 constexpr int kMaxHd = 1024;      // hard data kept per template window

@@ -22,11 +22,13 @@
 //
 // Each CTA owns mt (<= 4) consecutive M-tiles and one N-tile of nt items.
 // The accumulators of its M-tiles (128 lanes x nt columns of FP32 each) live
-// side by side in tensor memory. In the epilogue each of 8 warps reads one
-// lane quarter (a candidate per lane and M-tile) and every other item: it
-// turns the scores into ranking keys with the hard-data mismatches, keeps the
-// K best of its 32 x mt candidates per item, and the CTA merges the warps
-// into one K-list per item.
+// side by side in tensor memory. Two epilogues turn the scores into ranking
+// keys with the hard-data mismatches and keep the K best per item: (a) for
+// K <= 8, each M-tile's scores move through a shared-memory tile and thread
+// (item, segment) keeps its item's K best in registers (scan_segment); (b)
+// otherwise, or on request, each of 8 warps reads one lane quarter (a
+// candidate per lane and M-tile) and every other item and selects with warp
+// shuffles. The CTA merges the partial lists into one K-list per item.
 #include "tc_util.cuh"
 
 namespace ccw {

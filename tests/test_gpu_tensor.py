@@ -111,7 +111,7 @@ def test_tensor_simulation_matches_oracle(ccw, precision):
 def test_tensor_precision_bounds(ccw):
     """BF16 is exact up to 256: the one-hot score at J = 4 (2D) fits, the
     literal score of 3 facies (operands up to 512) does not and is refused;
-    the 3D tensor-core path is not built."""
+    the 3D tensor-core path keeps per-thread K-lists, so K > 8 is refused."""
     ti = synth.random_field_ti((128, 128), 3, seed=1)
     g = ccw.TI(dev(ti), 3, 4, 32, 16)
     de = torch.full((1, 32, 32), 255, dtype=torch.uint8, device="cuda")
