@@ -95,7 +95,7 @@ def profiled_traffic(kernel: str, workload: str, tile: int):
     (profiles/traffic.txt), if it was taken on this workload and tiling with
     the current kernel source; None otherwise."""
     import hashlib
-    src = {"k_ccf_tc": "tc.cu", "k_ccf_simt": "ccf_simt.cu"}[kernel]
+    src = {"k_ccf_tc": "tc.cu", "k_ccf_tcs": "tcs.cu", "k_ccf_simt": "ccf_simt.cu"}[kernel]
     path = os.path.join(ROOT, "paper_2404_00441_gb300", "csrc", src)
     try:
         with open(path, "rb") as f:
@@ -220,7 +220,7 @@ def run_reference(args, rank, world):
     w = configs.workload(args.workload)
     if w.get("groups"):
         w = dict(w, grid=w["groups"][0]["grid"], hd=w["groups"][0]["hd"])
-    per_step = max(1.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    per_step = max(0.5, min(args.cpu_seconds, 90.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(w, per_step / 4)
     vals, evs, ts = [], [], []
@@ -278,6 +278,64 @@ def train_proposal(args, ti, w, grid):
             "target_miss": args.target_miss, "held_out_miss_of_settled": miss,
             "held_out_settled_frac": float(settled.float().mean().item()),
             "prep_s": time.time() - t0}
+
+
+def ours_line(args, world, m):
+    """The benchmark's JSON line from the measurements `m` (see run_ours)."""
+    cells = m["cells_per_step"] * world * args.steps
+    total_ms, kern_ms = m["total_ms"], m["kern_ms"]
+    value = cells / (total_ms / 1e3)
+    achieved = 2.0 * m["macs"] / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
+    precision, tile = m["precision"], m["tile"]
+    if precision == 0:
+        bound, peak, peak_src = "alu", FP32_PEAK_TFLOPS, \
+            "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        kernel, kname = "k_ccf_simt", "k_ccf_simt (masked CCF on the FP32 lanes, per-tile top-K)"
+    else:
+        bound = "tensor"
+        peak, peak_src = tensor_peak_tflops()
+        if m["ndim"] == 3 or (tile >> 25) & 1:
+            kernel = "k_ccf_tcs"
+            kname = ("k_ccf_tcs (masked CCF on tcgen05 tensor cores, operands streamed through "
+                     "shared-memory stages, per-CTA top-K)")
+        else:
+            kernel = "k_ccf_tc"
+            kname = "k_ccf_tc (masked CCF on tcgen05 tensor cores, per-CTA top-K)"
+    line = {
+        "metric": "simulated cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "f16", 2: "bf16"}[precision], "data": "synthetic",
+        "cand_evals_per_s": m["cand_evals"] * world / (total_ms / 1e3),
+        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                   "realizations_per_gpu": m["total_real"], "precision": precision,
+                   "ccf_tile": tile,
+                   "l2": "flushed by a 256 MiB write between timed steps",
+                   "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
+        "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(kernel, args.workload, tile),
+                     "traffic_note": "cold-cache DRAM bytes per launch from profiles/traffic.txt "
+                                     "(null unless taken on this workload, tiling and kernel "
+                                     "source)",
+                     "launches": m["n_launch"],
+                     "kernel_ms_per_step": kern_ms / args.steps,
+                     "instrumented_ms_per_step": m["instr_ms"] / args.steps,
+                     "timing": "CUDA events around every CCF launch on its stream, over a "
+                               "second pass of the same K steps",
+                     "peak_source": peak_src,
+                     "work": "2 x (data-holding level-J cells x channels) flop per candidate"},
+        "gpu_launches": int(m["launches"]),
+        "clocks": m["clocks"],
+    }
+    if m.get("learned") is not None:
+        line["config"]["learned"] = m["learned"]
+    if m.get("autotune") is not None:
+        line["config"]["autotune"] = m["autotune"]
+    if m.get("e2e_ms"):
+        line["e2e"] = {"value": cells / (m["e2e_ms"] / 1e3), "unit": "cells/s",
+                       "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]}
+    return line
 
 
 def run_ours(args, rank, world, local_rank):
@@ -435,54 +493,12 @@ def run_ours(args, rank, world, local_rank):
                                                        "cuda")
     if rank != 0:
         return
-    cells = cells_per_step * world * args.steps
-    value = cells / (total_ms / 1e3)
-    flops = 2.0 * macs
-    achieved = flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else 0.0
-    if precision == 0:
-        bound, peak, peak_src = "alu", FP32_PEAK_TFLOPS, \
-            "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
-        kname = "k_ccf_simt (masked CCF on the FP32 lanes, per-tile top-K)"
-    else:
-        bound = "tensor"
-        peak, peak_src = tensor_peak_tflops()
-        kname = "k_ccf_tc (masked CCF on tcgen05 tensor cores, per-CTA top-K)"
-    dtype = {0: "f32", 1: "f16", 2: "bf16"}[precision]
-    line = {
-        "metric": "simulated cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-        "data": "synthetic",
-        "cand_evals_per_s": cand_evals * world / (total_ms / 1e3),
-        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
-                   "realizations_per_gpu": total_real, "precision": precision,
-                   "l2": "flushed by a 256 MiB write between timed steps",
-                   "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
-        "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic("k_ccf_simt" if precision == 0 else "k_ccf_tc",
-                                                 args.workload, tile),
-                     "traffic_note": "cold-cache DRAM bytes per launch from profiles/traffic.txt "
-                                     "(null unless taken on this workload, tiling and kernel "
-                                     "source)",
-                     "launches": n_launch,
-                     "kernel_ms_per_step": kern_ms / args.steps,
-                     "instrumented_ms_per_step": instr_ms / args.steps,
-                     "timing": "CUDA events around every CCF launch on its stream, over a "
-                               "second pass of the same K steps",
-                     "peak_source": peak_src,
-                     "work": "2 x (data-holding level-J cells x channels) flop per candidate"},
-        "gpu_launches": int(launches),
-        "clocks": clk,
-    }
-    if learned_info is not None:
-        line["config"]["learned"] = learned_info
-    line["config"]["ccf_tile"] = tile
-    if tune_info is not None:
-        line["config"]["autotune"] = tune_info
-    if e2e_ms:
-        line["e2e"] = {"value": cells / (e2e_ms_max / 1e3), "unit": "cells/s",
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    line = ours_line(args, world, dict(
+        total_ms=total_ms, kern_ms=kern_ms, instr_ms=instr_ms, macs=macs, cand_evals=cand_evals,
+        n_launch=n_launch, launches=launches, clocks=clk, precision=precision, tile=tile,
+        ndim=ndim, total_real=total_real, cells_per_step=cells_per_step,
+        e2e_ms=e2e_ms_max if e2e_ms else None, h2d=h2d, d2h=d2h, learned=learned_info,
+        autotune=tune_info))
     if not args.no_cpu_baseline:
         w0 = dict(w, grid=groups[0]["grid"], hd=groups[0]["hd_host"])
         n, dt, ce = oracle_sample(w0, args.cpu_seconds)
