@@ -60,6 +60,11 @@ WORKLOAD_TEXT = {
           "100x100x100; T24 OR6 J1; 1000 hard data per grid size; K=5",
     "c5": "2D binary ribbon TI 250x250; 256 realizations 512x512; T48 OR12 J2; K=1",
 }
+for _j in (1, 2, 3):
+    for _h in (1000, 2000):
+        WORKLOAD_TEXT[f"t2_j{_j}_h{_h}"] = (
+            f"Table 2 level sweep: 2D binary ribbon TI 250x250; 20 realizations 512x512; T32 "
+            f"OR8 J{_j}; {_h} hard data; K=5")
 
 
 def parse_args():

@@ -15,6 +15,9 @@ stand-in with ``workloads.synth``:
   hard data per grid size from a second field (seed 6), K = 5.
 * ``c5`` -- c1's TI; 256 realizations of 512x512, template 48, overlap 12,
   level 2 (the learned-proposal geometry), K = 1.
+* ``t2_j<J>_h<n>`` -- the DWT-level sweep of Table 2: c1's TI; 20
+  realizations of 512x512, template 32, overlap 8, level J = 1..3, n = 1000
+  or 2000 hard data from a second ribbon field (512x512, seed 9), K = 5.
 """
 from __future__ import annotations
 
@@ -38,6 +41,11 @@ def channel_lens_ti_1000():
 @lru_cache(maxsize=None)
 def hd_field_2000():
     return synth.channel_lens_ti(2000, 2000, seed=3)
+
+
+@lru_cache(maxsize=None)
+def hd_field_512():
+    return synth.ribbon_ti(512, 512, n_ribbons=24, seed=9)
 
 
 @lru_cache(maxsize=None)
@@ -78,6 +86,16 @@ def workload(name: str) -> dict:
         a["real_base"] = 0
         return dict(name="c4", ti=a["ti"], F=4, J=1, T=24, O=6, K=5, groups=[a, b], seed=4,
                     grid=None, n_real=a["n_real"] + b["n_real"], hd=None)
+    if name.startswith("t2_"):
+        # the DWT-level sweep of Table 2: 512 x 512 grid, template 32,
+        # overlap 8, 20 conditional realizations, level 1-3, 1000 or 2000
+        # hard data (drawn from a second ribbon field), on the 250 x 250
+        # binary channel TI
+        _, j, h = name.split("_")
+        J, n_hd = int(j[1:]), int(h[1:])
+        cells, vals = synth.sample_hard_data(hd_field_512(), n_hd, seed=10 + n_hd)
+        return dict(name=name, ti=ribbon_ti_250(), F=2, J=J, T=32, O=8, K=5,
+                    grid=(512, 512), n_real=20, hd=(cells, vals), seed=6)
     if name == "c5":
         return dict(name="c5", ti=ribbon_ti_250(), F=2, J=2, T=48, O=12, K=1,
                     grid=(512, 512), n_real=256, hd=None, seed=5)
