@@ -393,6 +393,36 @@ int ccw_proposal_inputs(const ccw_ti* ti, int32_t what, const uint8_t* counts_de
  */
 int ccw_proposal_stats(const ccw_ti* ti, int64_t out[3], void* stream);
 
+/*
+ * Pattern-reproduction statistics of realizations (the validation of
+ * Sec. 5.2-5.3; no counterpart as a library call in the paper). real_dev:
+ * uint8 [n_real][dims[2]][dims[1]][dims[0]] facies codes, n_real <= 65535.
+ * Every result is an exact integer count written to caller-owned device
+ * memory; calls are asynchronous on `stream`. Errors: CCW_EINVAL, CCW_ECUDA
+ * (text from ccw_eval_last_error).
+ *
+ * ccw_eval_proportions -- counts_dev uint64 [n_real][n_facies]: cells of
+ *   each facies.
+ * ccw_eval_variogram -- mismatch_dev uint64 [n_real][n_lags]: number of
+ *   cell pairs (x, x + h e_axis) inside the grid whose indicators of `facies`
+ *   differ, h = lags_dev[l] (int32, device); the indicator variogram is
+ *   0.5 * mismatches / pairs, pairs = (n_axis - h) * (cells / n_axis).
+ * ccw_eval_patterns -- hist_dev uint32 [n_facies^(w*w)] (<= 2^26 bins):
+ *   histogram over all realizations of the w x w patterns (2D), each coded
+ *   base n_facies row by row, after a mode downsampling by `down` (the most
+ *   frequent facies of every down x down block, ties to the lower code;
+ *   scratch_dev uint8 [n_real][dims[1]/down][dims[0]/down] when down > 1).
+ */
+int ccw_eval_proportions(const uint8_t* real_dev, int32_t n_real, const int32_t dims[3],
+                         int32_t n_facies, uint64_t* counts_dev, void* stream);
+int ccw_eval_variogram(const uint8_t* real_dev, int32_t n_real, const int32_t dims[3],
+                       int32_t facies, int32_t axis, const int32_t* lags_dev, int32_t n_lags,
+                       uint64_t* mismatch_dev, void* stream);
+int ccw_eval_patterns(const uint8_t* real_dev, int32_t n_real, const int32_t dims[3],
+                      int32_t n_facies, int32_t down, int32_t w, uint8_t* scratch_dev,
+                      uint32_t* hist_dev, void* stream);
+const char* ccw_eval_last_error(void);
+
 /* ccw_last_error -- text of the last failure on the calling host thread. */
 const char* ccw_last_error(void);
 
