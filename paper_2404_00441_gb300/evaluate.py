@@ -38,19 +38,22 @@ def _dims(reals: torch.Tensor):
 
 
 def proportions(reals: torch.Tensor, n_facies: int, stream=None) -> torch.Tensor:
-    """Facies fractions float64 [n_real, n_facies] of uint8 realizations."""
+    """Facies fractions float64 [n_real, n_facies] (host tensor) of uint8
+    realizations."""
     lib = _lib()
     n = reals.shape[0]
     out = torch.empty((n, n_facies), dtype=torch.int64, device=reals.device)
     _check(lib.ccw_eval_proportions(ccw._ptr(reals), n, _dims(reals), n_facies, ccw._ptr(out),
                                     ccw._stream(stream)))
     vol = reals[0].numel()
-    return out.double() / vol
+    # divided on the host: torch may divide by a scalar through its
+    # reciprocal, which is not the correctly rounded quotient
+    return torch.from_numpy(out.cpu().numpy() / vol)
 
 
 def variogram(reals: torch.Tensor, facies: int, axis: int, lags, stream=None) -> torch.Tensor:
-    """Indicator variogram float64 [n_real, len(lags)] of `facies` along axis
-    (0 = x, 1 = y, 2 = z): 0.5 * (differing pairs) / pairs."""
+    """Indicator variogram float64 [n_real, len(lags)] (host tensor) of
+    `facies` along axis (0 = x, 1 = y, 2 = z): 0.5 * (differing pairs) / pairs."""
     lib = _lib()
     n = reals.shape[0]
     lg = torch.tensor(list(lags), dtype=torch.int32, device=reals.device)
@@ -62,7 +65,7 @@ def variogram(reals: torch.Tensor, facies: int, axis: int, lags, stream=None) ->
     per_line = reals[0].numel() // n_axis
     pairs = torch.tensor([(n_axis - h) * per_line if 0 <= h < n_axis else float("nan")
                           for h in lags], dtype=torch.float64, device=reals.device)
-    return 0.5 * out.double() / pairs   # NaN where a lag has no pair
+    return torch.from_numpy(0.5 * out.cpu().numpy() / pairs.cpu().numpy())   # NaN: no pair
 
 
 def pattern_histogram(reals: torch.Tensor, n_facies: int, w: int = 4, down: int = 1,
