@@ -37,6 +37,16 @@ sys.path.insert(0, ROOT)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU pool (MEASURED_PEAKS.json hbm_gbs)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
 def tensor_peak_tflops():
     """Measured dense BF16 GEMM throughput of this GPU pool (FP16 runs at the
     same dense rate): the roofline of the tensor-core CCF kernel."""
@@ -340,6 +350,26 @@ def ours_line(args, world, m):
     if m.get("e2e_ms"):
         line["e2e"] = {"value": cells / (m["e2e_ms"] / 1e3), "unit": "cells/s",
                        "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]}
+    if m.get("phase_ms"):
+        # the other two kernels of a wavefront step against the HBM roofline:
+        # algorithmic bytes per data event / pasted patch
+        hbm, hbm_src = hbm_peak_gbs()
+        ndim = m["ndim"]
+        td, tjd = m["T"] ** ndim, m["Tj"] ** ndim
+        items = m["items_per_step"] * world
+        per = {"k_events": td * (2 if m["has_hd"] else 1) + 4 * (m["F"] - 1) * tjd,
+               "k_finish": 3 * td}
+        kern = {}
+        for name, ms in (("k_events", m["phase_ms"][0]), ("k_finish", m["phase_ms"][2])):
+            ms_step = ms / args.steps
+            by = items * per[name]
+            gbs = by / (ms_step / 1e3) / 1e9 if ms_step > 0 else 0.0
+            kern[name] = {"bound": "hbm", "ms_per_step": ms_step, "bytes_per_step": by,
+                          "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+        kern["note"] = ("bytes per item: events = template window (+ hard-data overlay) read + "
+                        "level-J weights written; finish = pattern written + its 16-bit "
+                        "coefficients read; times from the instrumented pass; peak " + hbm_src)
+        line["kernels"] = kern
     return line
 
 
@@ -454,6 +484,7 @@ def run_ours(args, rank, world, local_rank):
     instr_ms = timed_steps()
     ccw.profile_enable(False)
     n_launch, kern_ms, cand_evals, macs = ccw.profile_read()
+    phase_ms = ccw.profile_read_phases()
     clk = clocks.stop()
 
     # end to end through the public API with host buffers: the hard data come
@@ -503,7 +534,11 @@ def run_ours(args, rank, world, local_rank):
         n_launch=n_launch, launches=launches, clocks=clk, precision=precision, tile=tile,
         ndim=ndim, total_real=total_real, cells_per_step=cells_per_step,
         e2e_ms=e2e_ms_max if e2e_ms else None, h2d=h2d, d2h=d2h, learned=learned_info,
-        autotune=tune_info))
+        autotune=tune_info, phase_ms=phase_ms,
+        items_per_step=sum(gr["n_real"] * n_patches_of(gr["grid"], w["T"], w["O"])
+                           for gr in groups),
+        T=w["T"], Tj=w["T"] // (2 ** w["J"]), F=w["F"],
+        has_hd=any(gr["hd_host"] is not None for gr in groups)))
     if not args.no_cpu_baseline:
         w0 = dict(w, grid=groups[0]["grid"], hd=groups[0]["hd_host"])
         n, dt, ce = oracle_sample(w0, args.cpu_seconds)

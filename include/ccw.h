@@ -437,6 +437,12 @@ const char* ccw_last_error(void);
  */
 int ccw_profile_enable(int32_t enable);
 int ccw_profile_read(int64_t* launches, double* total_ms, double* cand_evals, double* macs);
+/* ccw_profile_read_phases -- summed durations (ms, stream-ordered CUDA events
+ * recorded inside the captured simulation graph) of the three phases of
+ * every wavefront of the profiled simulations: ms[0] data events (and the
+ * learned proposal's kernels), ms[1] CCF, ms[2] finish (top-K merge, pick,
+ * inverse-DWT paste); read and reset. */
+int ccw_profile_read_phases(double ms[3]);
 int64_t ccw_launch_count(void);
 
 #ifdef __cplusplus

@@ -78,6 +78,7 @@ def load():
     lib.ccw_profile_read.argtypes = [C.POINTER(i64), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.ccw_launch_count.restype = i64
+    lib.ccw_profile_read_phases.argtypes = [C.POINTER(C.c_double)]
     f32 = C.c_float
     lib.ccw_net_create.argtypes = [i32, i32, u64, C.POINTER(P)]
     lib.ccw_net_free.argtypes = [P]
@@ -369,6 +370,14 @@ def profile_read():
     ms, ce, mac = C.c_double(), C.c_double(), C.c_double()
     _check(load().ccw_profile_read(C.byref(n), C.byref(ms), C.byref(ce), C.byref(mac)))
     return n.value, ms.value, ce.value, mac.value
+
+
+def profile_read_phases():
+    """(events ms, CCF ms, finish ms) of the profiled simulations since the
+    last read."""
+    v = (C.c_double * 3)()
+    _check(load().ccw_profile_read_phases(v))
+    return tuple(float(x) for x in v)
 
 
 def launch_count() -> int:

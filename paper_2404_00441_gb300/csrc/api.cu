@@ -98,6 +98,7 @@ struct Profiler {
   bool enabled = false;
   int64_t launches = 0;
   double total_ms = 0.0;
+  double phase_ms[3] = {0.0, 0.0, 0.0};   // simulations: events, CCF, finish
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // direct launches
   unsigned long long* d_work = nullptr;
 } g_prof;
@@ -164,14 +165,16 @@ struct SimPlan {
   void* cp = nullptr;   // CcfPlan (defined with the kernels' host helpers)
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [profiling]
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;   // around each CCF launch
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_bounds;   // before events, after finish
   ~SimPlan() {
     for (auto& e : exec)
       if (e) cudaGraphExecDestroy(e);
-    for (auto& pr : prof_events) {
-      cudaEventDestroy(pr.first);
-      cudaEventDestroy(pr.second);
-    }
+    for (auto* v : {&prof_events, &prof_bounds})
+      for (auto& pr : *v) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+      }
     if (cap) cudaStreamDestroy(cap);
     for (auto& g : groups) {
       cudaFree(g.sg);
@@ -614,6 +617,16 @@ int64_t ccw_launch_count(void) { return g_launches.load(); }
 int ccw_profile_enable(int32_t enable) {
   std::lock_guard<std::mutex> g(g_prof.mu);
   g_prof.enabled = enable != 0;
+  return CCW_OK;
+}
+
+int ccw_profile_read_phases(double ms[3]) {
+  if (!ms) return fail(CCW_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  for (int i = 0; i < 3; ++i) {
+    ms[i] = g_prof.phase_ms[i];
+    g_prof.phase_ms[i] = 0.0;
+  }
   return CCW_OK;
 }
 
@@ -1122,6 +1135,15 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
       c.items = (const int4*)pl->items + i0;
       c.n_items = (int)std::min<int64_t>(65535, pl->wave_off[w + 1] - i0);
       apply_ccf(t, cp, pl->bmat, c);
+      if (prof) {
+        if (pe >= pl->prof_bounds.size()) {
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          pl->prof_bounds.emplace_back(e0, e1);
+        }
+        cudaEventRecordWithFlags(pl->prof_bounds[pe].first, st, cudaEventRecordExternal);
+      }
       cudaError_t e = launch_events(kModeSim, c, true, st);
       if (e != cudaSuccess) return cuda_fail(e, "event kernel launch");
       if (pl->learned) {
@@ -1144,9 +1166,10 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
       e = launch_ccf(t, kModeSim, cp, c, !prof, st);
       if (e != cudaSuccess) return cuda_fail(e, "CCF kernel launch");
       if (prof)
-        cudaEventRecordWithFlags(pl->prof_events[pe++].second, st, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(pl->prof_events[pe].second, st, cudaEventRecordExternal);
       e = launch_finish(kModeSim, c, !prof, st);
       if (e != cudaSuccess) return cuda_fail(e, "finish kernel launch");
+      if (prof) cudaEventRecordWithFlags(pl->prof_bounds[pe++].second, st, cudaEventRecordExternal);
     }
   }
   return CCW_OK;
@@ -1293,12 +1316,18 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
     return cuda_fail(e, "simulation");
   if (prof) {
     std::lock_guard<std::mutex> g(g_prof.mu);
-    for (auto& pr : pl->prof_events) {
-      float ms = 0.f;
+    for (size_t i = 0; i < pl->prof_events.size(); ++i) {
+      const auto& pr = pl->prof_events[i];
+      const auto& bd = pl->prof_bounds[i];
+      float ms = 0.f, ev = 0.f, fin = 0.f;
       if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
         g_prof.total_ms += ms;
         ++g_prof.launches;
+        g_prof.phase_ms[1] += ms;
       }
+      if (cudaEventElapsedTime(&ev, bd.first, pr.first) == cudaSuccess) g_prof.phase_ms[0] += ev;
+      if (cudaEventElapsedTime(&fin, pr.second, bd.second) == cudaSuccess)
+        g_prof.phase_ms[2] += fin;
     }
   }
   if (status & kStatusBadCode)
