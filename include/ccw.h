@@ -96,8 +96,9 @@ typedef struct {
                           when K <= 8, 1: lanes on candidates), m = 1:
                           operands streamed through a ring of shared-memory
                           stages (always so in 3D; K <= 8), bit 26: three
-                          stages instead of two, bits 27-28 = v: stages of
-                          Tj / 2^v template rows (v <= 2). An autotuner
+                          stages instead of two, bit 29: four (not with bit
+                          26), bits 27-28 = v: stages of Tj / 2^v template
+                          rows (v <= 2). An autotuner
                           picks it by timing
                           (paper_2404_00441_gb300.autotune). */
   int32_t reserved[2]; /* must be 0 */

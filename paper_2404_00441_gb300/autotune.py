@@ -36,9 +36,9 @@ def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
         else:
             # tensor cores: bit 24 = lanes-on-candidates epilogue, bit 25 =
             # streamed operands (the only form in 3D)
-            # bit 26 = three stages in the streamed kernel (else two); bits
-            # 27-28 = template rows per stage Tj / 2^v
-            streamed = (2, 6, 2 | 8, 2 | 16, 6 | 8)
+            # bit 26 = three stages in the streamed kernel, bit 29 = four
+            # (else two); bits 27-28 = template rows per stage Tj / 2^v
+            streamed = (2, 6, 2 | 8, 2 | 16, 6 | 8, 6 | 16, 2 | 16 | 32, 2 | 8 | 32)
             flags = (0, 1) + streamed if ti.ndim == 2 else streamed
             for fl in flags:
                 for nt in (16, 32, 64, 128):

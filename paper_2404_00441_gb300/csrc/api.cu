@@ -345,8 +345,8 @@ void choose_tc(const ccw_ti* t, int nch, int K, int n_items, WaveArgs& a, int& s
   for (;;) {
     if (streamed) {
       // double-buffered slices (two CTAs can then share an SM); three
-      // stages on request (bit 26 of the hint)
-      a.tcs_stages = ((hint >> 26) & 1) ? 3 : 2;
+      // stages on request (bit 26 of the hint), four with bit 29
+      a.tcs_stages = ((hint >> 29) & 1) ? 4 : ((hint >> 26) & 1) ? 3 : 2;
       // rows per stage: Tj, or Tj split in 2 or 4 blocks (bits 27-28)
       const int split = 1 << ((hint >> 27) & 3);
       a.tcs_rows = (t->Tj + split - 1) / split;
@@ -402,7 +402,8 @@ bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
                         : (hint == 1 || hint == 2 || hint == 4);
   const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, flags = hint >> 24;
   return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
-         mt * nt <= 512 && flags >= 0 && flags <= 23 && ((flags >> 3) & 3) != 3;
+         mt * nt <= 512 && flags >= 0 && flags <= 63 && ((flags >> 3) & 3) != 3 &&
+         !((flags >> 5) & 1 && (flags >> 2) & 1);
 }
 
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,

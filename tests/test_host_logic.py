@@ -48,7 +48,7 @@ def test_autotune_candidates_respect_the_documented_tilings():
                 continue
             nt, mt, fl = t & 0xFFFF, (t >> 16) & 0xFF, t >> 24
             assert nt in (16, 32, 64, 128) and 1 <= mt <= 4 and mt * nt <= 512
-            assert fl <= 23 and ((fl >> 3) & 3) != 3
+            assert fl <= 63 and ((fl >> 3) & 3) != 3 and not (fl & 32 and fl & 4)
             if ndim == 3:
                 assert fl & 2   # streamed operands only in 3D
     assert len(set(c2)) == len(c2) and len(set(c3)) == len(c3)
