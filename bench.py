@@ -144,6 +144,15 @@ def max_over_ranks(values, world: int, device: str):
     return [float(v) for v in t.tolist()]
 
 
+def wavefronts_of(grid, T, O):
+    """Wavefront steps of the raster-equivalent schedule: a patch (ix, iy, iz)
+    runs at step ix + 2 iy + 4 iz."""
+    S = T - O
+    n = [1 + (max(g - T, 0) + S - 1) // S for g in grid]
+    n += [1] * (3 - len(n))
+    return (n[0] - 1) + 2 * (n[1] - 1) + 4 * (n[2] - 1) + 1
+
+
 def n_patches_of(grid, T, O):
     S = T - O
     n = 1
@@ -324,6 +333,9 @@ def ours_line(args, world, m):
         "cand_evals_per_s": m["cand_evals"] * world / (total_ms / 1e3),
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
                    "realizations_per_gpu": m["total_real"], "precision": precision,
+                   "wavefronts": m.get("wavefronts"),
+                   "ms_per_wavefront": (total_ms / args.steps / m["wavefronts"]
+                                        if m.get("wavefronts") else None),
                    "ccf_tile": tile,
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
@@ -538,6 +550,7 @@ def run_ours(args, rank, world, local_rank):
         items_per_step=sum(gr["n_real"] * n_patches_of(gr["grid"], w["T"], w["O"])
                            for gr in groups),
         T=w["T"], Tj=w["T"] // (2 ** w["J"]), F=w["F"],
+        wavefronts=max(wavefronts_of(gr["grid"], w["T"], w["O"]) for gr in groups),
         has_hd=any(gr["hd_host"] is not None for gr in groups)))
     if not args.no_cpu_baseline:
         w0 = dict(w, grid=groups[0]["grid"], hd=groups[0]["hd_host"])
