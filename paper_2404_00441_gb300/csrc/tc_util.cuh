@@ -114,7 +114,8 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // index or -1, offset of the candidate's first cell in the fine TI) per row.
 // Hard-data mismatches (Sec. 4.4) are counted for kScanBatch candidates at a
 // time so that their TI loads overlap. Each key enters the thread's sorted list lst
-// (K <= KL best; `worst` is its K-th entry), or the map is written.
+// (K <= KL best; `worst` is its K-th entry), or the map is written. Keys
+// at or above `bound` are dropped (see the caller).
 
 // Hard-data mismatches (Sec. 4.4) of one M-tile's 128 candidates for the
 // items in columns c0 .. c0+ntc-1, into the uint16 tile Mt[row][column]
@@ -154,7 +155,8 @@ __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, 
                                              const int2* cand, int r0, int len, int4 mt4,
                                              const int2* hdl, int64_t item, int K,
                                              uint64_t (&lst)[KL], uint64_t& worst,
-                                             const uint16_t* Mt = nullptr, int spm = 0) {
+                                             const uint16_t* Mt = nullptr, int spm = 0,
+                                             uint64_t bound = ~0ull) {
   const TiDev& t = a.ti;
 #pragma unroll 1
   for (int rb = r0; rb < r0 + len; rb += kScanBatch) {
@@ -183,7 +185,9 @@ __device__ __forceinline__ void scan_segment(const WaveArgs& a, const float* S, 
         continue;
       }
       const uint64_t key = make_key(mis[u], score, ci[u].x);
-      if (key < worst) {
+      // `bound`: a key above the K-th best of another thread's list for
+      // this item can never be among the item's K best
+      if (key < worst && key < bound) {
         if (K == 1) {
           lst[0] = key;
           worst = key;

@@ -33,7 +33,7 @@ __host__ __device__ inline int tcs_a_nq(int mt, int R, int px8, int k16n) {
 }
 
 struct TcsSmem {
-  int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, m_off, bytes;
+  int bar_off, meta_off, stage_off, stage_bytes, b_in_stage, s_off, c_off, w_off, m_off, bytes;
 };
 
 __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int k16n,
@@ -54,6 +54,8 @@ __host__ __device__ inline TcsSmem tcs_smem(int mt, int nt, int R, int px8, int 
   off += (((s_bytes > l_bytes ? s_bytes : l_bytes) + 127) / 128) * 128;
   L.c_off = off;
   off += kTcMaxMt * 128 * 8;
+  L.w_off = off;   // the K-th best key of every thread's list [nseg][ntc]
+  off += kTcsThreads * 8;
   // uint16 mismatch tile [128][ntc + 2] of the epilogue: over the stages
   // (idle once every MMA has completed) when they are large enough
   const int m_bytes = 128 * (ntc + 2) * 2;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
     const int half = ntc / 2;
     uint64_t* seglists = reinterpret_cast<uint64_t*>(S);
     uint16_t* Mt = reinterpret_cast<uint16_t*>(smem + L.m_off);
+    uint64_t* worsts = reinterpret_cast<uint64_t*>(smem + L.w_off);
 #pragma unroll 1
     for (int cc = 0; cc < nt / ntc; ++cc) {
       const int col = cc * ntc + n;
@@ -286,10 +289,20 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
         // many hard data: count mismatches with coalesced loads first
         if (hd_tile) mismatch_tile(a, meta, ntile, nt, cc * ntc, ntc, cand + j * 128, Mt, ntc + 2);
         __syncthreads();
+        // for K > 1: the smallest K-th best over the item's segment lists of
+        // the previous M-tiles bounds the keys worth inserting (every list's
+        // K-th best is at or above the item's K-th best)
+        uint64_t bound = kNoKey;
+        if (MODE != kModeMap && K > 1 && j > 0)
+          for (int g = 0; g < nseg; ++g) {
+            const uint64_t w2 = worsts[g * ntc + n];
+            bound = w2 < bound ? w2 : bound;
+          }
         if (mt4.w)
           scan_segment<MODE, kTcsRegK>(a, S, spc, n, cand + j * 128, seg * seg_len, seg_len,
                                        mt4, hdl, item, K, lst, worst, hd_tile ? Mt : nullptr,
-                                       ntc + 2);
+                                       ntc + 2, bound);
+        if (MODE != kModeMap && K > 1) worsts[seg * ntc + n] = worst;
         __syncthreads();   // S is rewritten next
       }
       if (MODE != kModeMap) {
