@@ -28,6 +28,18 @@
  *   - Paste overwrites the whole template, then hard data are re-imposed.
  *   - Path randomisation mirrors the patch lattice (the raster starts from
  *     another corner); training-image patterns are never mirrored.
+ *   - Non-causal conditioning (Sec. 4.4, the conditional scheme that the
+ *     paper only sketches): the template grown by E cells along the forward
+ *     directions of the path is the "virtual template"; the hard data in it
+ *     but outside the template add to the mismatch count, a datum whose TI
+ *     position falls outside the TI counting as a mismatch. The score and
+ *     the empty-event rule use the template alone.
+ *   - Minimum-error boundary cut (the image-quilting paste of Sec. 2, 2D):
+ *     in the path frame, a vertical cut through the left overlap strip and
+ *     a horizontal one through the top strip, each the cheapest 8-connected
+ *     path over the 0/1 disagreements between the grid and the new pattern
+ *     (ties to the lower column); the pattern replaces a simulated cell only
+ *     on the far side of both cuts.
  *
  * Array convention: x fastest; dims n[3] = {nx, ny, nz} with nz = 1 in 2D.
  */
@@ -462,10 +474,11 @@ int64_t orc_num_candidates(const orc_ti* t, int T) {
  * Returns the number of ranked candidates written (0 for an empty data
  * event, whose pick is uniform), or a negative error.
  */
-int orc_search(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd, int K,
-               int score_mode, uint64_t seed, uint32_t r, uint32_t p, int64_t* scores,
-               int32_t* mis, int32_t* topk_idx, int64_t* topk_score, int32_t* topk_mis,
-               int32_t* pick_out) {
+static int search_core(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd,
+                       const int32_t* vhd, int n_vhd, int K, int score_mode, uint64_t seed,
+                       uint32_t r, uint32_t p, int64_t* scores, int32_t* mis,
+                       int32_t* topk_idx, int64_t* topk_score, int32_t* topk_mis,
+                       int32_t* pick_out) {
   int32_t cd[3];
   if (cand_dims(t, T, cd) != ORC_OK || K < 1 || (score_mode != 0 && score_mode != 1))
     return ORC_EINVAL;
@@ -547,6 +560,16 @@ int orc_search(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd, int
                 if (t->ti[fx + (int64_t)t->n[0] * (fy + (int64_t)t->n[1] * fz)] != h) ++mm;
               }
         }
+        /* hard data of the virtual template: a datum whose TI position lies
+         * outside the TI cannot be honoured and counts as a mismatch */
+        for (int v = 0; v < n_vhd; ++v) {
+          const int32_t* e = vhd + 4 * v;
+          int64_t fx = (int64_t)s * cx + e[0], fy = (int64_t)(d > 1 ? s : 1) * cy + e[1],
+                  fz = (int64_t)(d > 2 ? s : 1) * cz + e[2];
+          if (fx < 0 || fy < 0 || fz < 0 || fx >= t->n[0] || fy >= t->n[1] || fz >= t->n[2] ||
+              t->ti[fx + (int64_t)t->n[0] * (fy + (int64_t)t->n[1] * fz)] != (uint8_t)e[3])
+            ++mm;
+        }
         if (scores) scores[c] = sc;
         if (mis) mis[c] = mm;
         /* keep the kk best in rank order (equivalent to a full sort followed
@@ -570,6 +593,63 @@ int orc_search(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd, int
   *pick_out = best[scale_u32(u, nbest)].idx;
   free(img); free(pyr); free(cor); free(best);
   return nbest;
+}
+
+int orc_search(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd, int K,
+               int score_mode, uint64_t seed, uint32_t r, uint32_t p, int64_t* scores,
+               int32_t* mis, int32_t* topk_idx, int64_t* topk_score, int32_t* topk_mis,
+               int32_t* pick_out) {
+  return search_core(t, T, de, hd, NULL, 0, K, score_mode, seed, r, p, scores, mis, topk_idx,
+                     topk_score, topk_mis, pick_out);
+}
+
+/* orc_search with the hard data of a virtual template (Sec. 4.4 reading in
+ * the header): vhd is int32 [n_vhd][4] = (qx, qy, qz, code), the datum's
+ * fine offset from the window origin (any sign) and its facies. */
+int orc_search_virtual(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd,
+                       const int32_t* vhd, int n_vhd, int K, int score_mode, uint64_t seed,
+                       uint32_t r, uint32_t p, int64_t* scores, int32_t* mis,
+                       int32_t* topk_idx, int64_t* topk_score, int32_t* topk_mis,
+                       int32_t* pick_out) {
+  if (n_vhd < 0 || (n_vhd > 0 && !vhd)) return ORC_EINVAL;
+  for (int v = 0; v < n_vhd; ++v)
+    if (vhd[4 * v + 3] < 0 || vhd[4 * v + 3] >= t->F) return ORC_EINVAL;
+  return search_core(t, T, de, hd, vhd, n_vhd, K, score_mode, seed, r, p, scores, mis,
+                     topk_idx, topk_score, topk_mis, pick_out);
+}
+
+/* Minimum-error boundary cut of image quilting (Efros and Freeman, the IQ
+ * method of Sec. 2) through an overlap strip of `rows` x `cols` cells with
+ * 0/1 costs err[y * cols + x]: the cumulative cost
+ *   E(0, x) = err(0, x),  E(y, x) = err(y, x) + min_{|x' - x| <= 1} E(y - 1, x'),
+ * then the path traced back from the cheapest cell of the last row, each
+ * step to the cheapest of the (up to) three cells above; ties go to the
+ * lower column. cut[y] = the path's column in row y. */
+int orc_min_cut(const uint8_t* err, int rows, int cols, int32_t* cut) {
+  if (rows < 1 || cols < 1 || !err || !cut) return ORC_EINVAL;
+  int64_t* E = (int64_t*)malloc(sizeof(int64_t) * rows * cols);
+  if (!E) return ORC_ENOMEM;
+  for (int x = 0; x < cols; ++x) E[x] = err[x];
+  for (int y = 1; y < rows; ++y)
+    for (int x = 0; x < cols; ++x) {
+      int64_t m = E[(y - 1) * cols + x];
+      if (x > 0 && E[(y - 1) * cols + x - 1] < m) m = E[(y - 1) * cols + x - 1];
+      if (x + 1 < cols && E[(y - 1) * cols + x + 1] < m) m = E[(y - 1) * cols + x + 1];
+      E[y * cols + x] = err[y * cols + x] + m;
+    }
+  int c = 0;
+  for (int x = 1; x < cols; ++x)
+    if (E[(rows - 1) * cols + x] < E[(rows - 1) * cols + c]) c = x;
+  cut[rows - 1] = c;
+  for (int y = rows - 2; y >= 0; --y) {
+    int lo = c > 0 ? c - 1 : 0, hi = c + 1 < cols ? c + 1 : cols - 1, b = lo;
+    for (int x = lo + 1; x <= hi; ++x)
+      if (E[y * cols + x] < E[y * cols + b]) b = x;
+    c = b;
+    cut[y] = c;
+  }
+  free(E);
+  return ORC_OK;
 }
 
 /* Algorithm 1, line 13: Inverse-DWT of the selected pattern. The pattern's
@@ -662,13 +742,17 @@ uint32_t orc_path_flips(int ndim, uint64_t seed, uint32_t r, int path_random) {
  *   {pick, score of pick, mismatches of pick, flags, topk[0..K-1]}
  * with flags bit0 = uniform pick (empty data event), bit1 = patch done, and
  * unused topk slots = -1. Stops after max_patches patches when >= 0.
+ * vt_ext (0..T) grows the virtual template of the non-causal conditioning;
+ * cut = 1 pastes through the minimum-error boundary cuts (2D only). Both
+ * follow the readings in the header; orc_simulate is vt_ext = cut = 0.
  */
-int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
-                 int score_mode, int path_random, int n_hd, const int32_t* hd_cells,
-                 const uint8_t* hd_vals, uint64_t seed, uint32_t r, int64_t max_patches,
-                 uint8_t* out, int32_t* log) {
+int orc_simulate_ext(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
+                     int score_mode, int path_random, int vt_ext, int cut, int n_hd,
+                     const int32_t* hd_cells, const uint8_t* hd_vals, uint64_t seed, uint32_t r,
+                     int64_t max_patches, uint8_t* out, int32_t* log) {
   const int d = t->ndim;
   if (T % t->s != 0 || O % t->s != 0 || O < 0 || T < 2 * O || K < 1) return ORC_EINVAL;
+  if (vt_ext < 0 || vt_ext > T || (cut != 0 && cut != 1) || (cut && d != 2)) return ORC_EINVAL;
   int32_t np[3], gp[3], cd[3];
   if (orc_lattice(d, grid, T, O, np, gp) != ORC_OK) return ORC_EINVAL;
   if (cand_dims(t, T, cd) != ORC_OK) return ORC_EINVAL;
@@ -690,8 +774,18 @@ int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
   int32_t* ti_mm = (int32_t*)malloc(sizeof(int32_t) * K);
   int64_t* scores = NULL;
   int32_t* mism = NULL;
+  /* the virtual template: the window grown by vt_ext cells along the
+   * forward direction of every axis of the path */
+  const int32_t gw[3] = {T + vt_ext, d > 1 ? T + vt_ext : 1, d > 2 ? T + vt_ext : 1};
+  const int64_t n_vmax = vt_ext ? vol32(gw) - tv : 0;
+  int32_t* vhd = (int32_t*)malloc(sizeof(int32_t) * 4 * (n_vmax > 0 ? n_vmax : 1));
+  uint8_t* errv = (uint8_t*)malloc((size_t)T * (O > 0 ? O : 1));
+  uint8_t* errh = (uint8_t*)malloc((size_t)T * (O > 0 ? O : 1));
+  int32_t* cutv = (int32_t*)malloc(sizeof(int32_t) * T);
+  int32_t* cuth = (int32_t*)malloc(sizeof(int32_t) * T);
   int rc = ORC_OK;
-  if (!sg || !hdo || !de || !hw || !pat || !ti_idx || !ti_sc || !ti_mm) {
+  if (!sg || !hdo || !de || !hw || !pat || !ti_idx || !ti_sc || !ti_mm || !vhd || !errv ||
+      !errh || !cutv || !cuth) {
     rc = ORC_ENOMEM;
     goto done;
   }
@@ -735,9 +829,34 @@ int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
           hw[q] = hdo[cell];
           de[q] = (hdo[cell] != UNKNOWN) ? hdo[cell] : sg[cell];
         }
+    /* the hard data of the virtual template outside the template; path
+     * frame (x', y', z') = window offsets mirrored along flipped axes */
+    int n_vhd = 0;
+    for (int32_t vz = 0; vz < gw[2]; ++vz)
+      for (int32_t vy = 0; vy < gw[1]; ++vy)
+        for (int32_t vx = 0; vx < gw[0]; ++vx) {
+          if (vx < tw[0] && vy < tw[1] && vz < tw[2]) continue;   /* template cell */
+          const int32_t v3[3] = {vx, vy, vz};
+          int32_t q3[3];
+          int inside = 1;
+          for (int a = 0; a < 3; ++a) {
+            q3[a] = (flips >> a & 1u) ? tw[a] - 1 - v3[a] : v3[a];
+            const int64_t gc = (int64_t)o[a] + q3[a];
+            if (gc < 0 || gc >= gp[a]) inside = 0;
+          }
+          if (!inside) continue;
+          const uint8_t h =
+              hdo[(o[0] + q3[0]) + (int64_t)gp[0] * ((o[1] + q3[1]) + (int64_t)gp[1] * (o[2] + q3[2]))];
+          if (h == UNKNOWN) continue;
+          vhd[4 * n_vhd] = q3[0];
+          vhd[4 * n_vhd + 1] = q3[1];
+          vhd[4 * n_vhd + 2] = q3[2];
+          vhd[4 * n_vhd + 3] = h;
+          ++n_vhd;
+        }
     int32_t pick = -1;
-    int nk = orc_search(t, T, de, hw, K, score_mode, seed, r, (uint32_t)p, scores, mism,
-                        ti_idx, ti_sc, ti_mm, &pick);
+    int nk = search_core(t, T, de, hw, vhd, n_vhd, K, score_mode, seed, r, (uint32_t)p, scores,
+                         mism, ti_idx, ti_sc, ti_mm, &pick);
     if (nk < 0) {
       rc = nk;
       goto done;
@@ -745,12 +864,41 @@ int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
     /* Algorithm 1, lines 13-14: reconstruct and paste; hard data stay */
     rc = orc_reconstruct(t, T, pick, pat);
     if (rc != ORC_OK) goto done;
+    if (cut && O > 0) {
+      /* boundary cuts in the path frame: column cut through the left strip
+       * (rows y', columns x' < O), row cut through the top strip (rows x',
+       * columns y' < O); the cost of a cell is 1 where the grid already
+       * holds a value that differs from the pattern */
+      for (int32_t yp = 0; yp < T; ++yp)
+        for (int32_t xp = 0; xp < T; ++xp) {
+          if (xp >= O && yp >= O) continue;
+          const int32_t qx = (flips & 1u) ? T - 1 - xp : xp;
+          const int32_t qy = (flips & 2u) ? T - 1 - yp : yp;
+          const uint8_t old = sg[(o[0] + qx) + (int64_t)gp[0] * (o[1] + qy)];
+          const uint8_t e = (old != UNKNOWN && old != pat[qx + (int64_t)T * qy]) ? 1 : 0;
+          if (xp < O) errv[yp * O + xp] = e;
+          if (yp < O) errh[xp * O + yp] = e;
+        }
+      if ((rc = orc_min_cut(errv, T, O, cutv)) != ORC_OK ||
+          (rc = orc_min_cut(errh, T, O, cuth)) != ORC_OK)
+        goto done;
+    }
     for (int32_t qz = 0; qz < tw[2]; ++qz)
       for (int32_t qy = 0; qy < tw[1]; ++qy)
         for (int32_t qx = 0; qx < tw[0]; ++qx) {
           int64_t q = qx + (int64_t)tw[0] * (qy + (int64_t)tw[1] * qz);
           int64_t cell = (o[0] + qx) + (int64_t)gp[0] * ((o[1] + qy) + (int64_t)gp[1] * (o[2] + qz));
-          sg[cell] = (hw[q] != UNKNOWN) ? hw[q] : pat[q];
+          if (hw[q] != UNKNOWN) {
+            sg[cell] = hw[q];
+            continue;
+          }
+          int take = 1;
+          if (cut && O > 0 && sg[cell] != UNKNOWN) {
+            const int32_t xp = (flips & 1u) ? T - 1 - qx : qx;
+            const int32_t yp = (flips & 2u) ? T - 1 - qy : qy;
+            take = xp >= cutv[yp] && yp >= cuth[xp];
+          }
+          if (take) sg[cell] = pat[q];
         }
     if (log) {
       int32_t* e = log + p * stride;
@@ -778,5 +926,14 @@ int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
 done:
   free(sg); free(hdo); free(de); free(hw); free(pat);
   free(ti_idx); free(ti_sc); free(ti_mm); free(scores); free(mism);
+  free(vhd); free(errv); free(errh); free(cutv); free(cuth);
   return rc;
+}
+
+int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
+                 int score_mode, int path_random, int n_hd, const int32_t* hd_cells,
+                 const uint8_t* hd_vals, uint64_t seed, uint32_t r, int64_t max_patches,
+                 uint8_t* out, int32_t* log) {
+  return orc_simulate_ext(t, grid, T, O, K, score_mode, path_random, 0, 0, n_hd, hd_cells,
+                          hd_vals, seed, r, max_patches, out, log);
 }

@@ -62,6 +62,11 @@ def _load():
     lib.orc_path_flips.restype = u32
     lib.orc_simulate.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.c_int, P, P, u64, u32, i64, P, P]
+    lib.orc_simulate_ext.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_int, C.c_int, C.c_int, P, P, u64, u32, i64, P, P]
+    lib.orc_search_virtual.argtypes = [P, C.c_int, P, P, P, C.c_int, C.c_int, C.c_int, u64,
+                                       u32, u32, P, P, P, P, P, P]
+    lib.orc_min_cut.argtypes = [P, C.c_int, C.c_int, P]
     _lib = lib
     return lib
 
@@ -180,8 +185,11 @@ class OracleTI:
         tj = T // self.s
         return tuple(n - tj + 1 for n in self.cshape)
 
-    def search(self, T, de, hd=None, K=1, score_mode=0, seed=0, r=0, p=0, maps=False):
+    def search(self, T, de, hd=None, K=1, score_mode=0, seed=0, r=0, p=0, maps=False,
+               vhd=None):
         """Best-match search for one data event (numpy [T]*d u8, 255 = unknown).
+        vhd: hard data of a virtual template, int [n][4] rows (qx, qy, qz, code)
+        of fine offsets from the window origin (any sign).
         Returns dict(topk_idx, topk_score, topk_mis, pick[, scores, mis])."""
         de = np.ascontiguousarray(de, dtype=np.uint8)
         hdp = None
@@ -195,9 +203,17 @@ class OracleTI:
         ti_sc = np.zeros(K, dtype=np.int64)
         ti_mm = np.zeros(K, dtype=np.int32)
         pick = np.zeros(1, dtype=np.int32)
-        nk = self._lib.orc_search(self.h, T, _p(de), hdp, K, score_mode, seed, r, p,
-                                  _p(sc) if maps else None, _p(mm) if maps else None,
-                                  _p(ti_idx), _p(ti_sc), _p(ti_mm), _p(pick))
+        if vhd is None:
+            nk = self._lib.orc_search(self.h, T, _p(de), hdp, K, score_mode, seed, r, p,
+                                      _p(sc) if maps else None, _p(mm) if maps else None,
+                                      _p(ti_idx), _p(ti_sc), _p(ti_mm), _p(pick))
+        else:
+            v = np.ascontiguousarray(np.asarray(vhd, dtype=np.int32).reshape(-1, 4))
+            nk = self._lib.orc_search_virtual(self.h, T, _p(de), hdp, _p(v), len(v), K,
+                                              score_mode, seed, r, p,
+                                              _p(sc) if maps else None,
+                                              _p(mm) if maps else None, _p(ti_idx), _p(ti_sc),
+                                              _p(ti_mm), _p(pick))
         if nk < 0:
             raise ValueError(f"orc_search failed ({nk})")
         out = dict(n=nk, topk_idx=ti_idx[:nk], topk_score=ti_sc[:nk], topk_mis=ti_mm[:nk],
@@ -215,8 +231,10 @@ class OracleTI:
         return pat.reshape((T,) * self.ndim)
 
     def simulate(self, grid, T, O, K=1, score_mode=0, path_random=0, hd_cells=None,
-                 hd_vals=None, seed=0, r=0, max_patches=-1, want_log=True):
+                 hd_vals=None, seed=0, r=0, max_patches=-1, want_log=True, vt_ext=0, cut=0):
         """One realization along the raster path (Algorithm 1). grid = (nx, ny[, nz]).
+        vt_ext grows the virtual template of the non-causal conditioning; cut = 1
+        pastes through the minimum-error boundary cuts (2D).
         Returns (realization numpy array, patch log [n_patches, 4+K] or None)."""
         g = _dims3(grid)
         npch, gp = lattice(self.ndim, grid, T, O)
@@ -229,10 +247,10 @@ class OracleTI:
             hc = np.ascontiguousarray(hd_cells, dtype=np.int32)
             hv = np.ascontiguousarray(hd_vals, dtype=np.uint8)
             n_hd = len(hv)
-        rc = self._lib.orc_simulate(self.h, _p(g), T, O, K, score_mode, path_random, n_hd,
-                                    _p(hc) if n_hd else None, _p(hv) if n_hd else None,
-                                    seed, r, max_patches, _p(out),
-                                    _p(log) if want_log else None)
+        rc = self._lib.orc_simulate_ext(self.h, _p(g), T, O, K, score_mode, path_random,
+                                        vt_ext, cut, n_hd, _p(hc) if n_hd else None,
+                                        _p(hv) if n_hd else None, seed, r, max_patches,
+                                        _p(out), _p(log) if want_log else None)
         if rc != 0:
             raise ValueError(f"orc_simulate failed ({rc})")
         return out, log
@@ -250,3 +268,15 @@ def lattice(ndim, grid, T, O):
 
 def path_flips(ndim, seed, r, path_random=1) -> int:
     return int(_load().orc_path_flips(ndim, seed, r, path_random))
+
+
+def min_cut(err) -> np.ndarray:
+    """Minimum-error boundary cut of image quilting through a [rows, cols]
+    0/1 cost array: the column of the cut in every row."""
+    e = np.ascontiguousarray(err, dtype=np.uint8)
+    rows, cols = e.shape
+    cut = np.zeros(rows, dtype=np.int32)
+    rc = _load().orc_min_cut(_p(e), rows, cols, _p(cut))
+    if rc != 0:
+        raise ValueError(f"orc_min_cut failed ({rc})")
+    return cut
