@@ -95,6 +95,11 @@ def parse_args():
                     help="skip the CCF tiling autotuner (library heuristic, --precision or 1/0)")
     ap.add_argument("--ccf-tile", type=lambda v: int(v, 0), default=None,
                     help="force this ccw_params.ccf_tile (implies --no-autotune)")
+    ap.add_argument("--vt-ext", type=int, default=0,
+                    help="non-causal conditioning: hard data up to this many cells beyond the "
+                         "template's forward edges join the mismatch count (0 = off)")
+    ap.add_argument("--boundary-cut", action="store_true",
+                    help="paste through the minimum-error boundary cuts (2D)")
     ap.add_argument("--learned", action="store_true",
                     help="learned proposal (2D): train the encoder on pairs from plain runs "
                          "before timing, calibrate the gap threshold on held-out pairs")
@@ -357,6 +362,10 @@ def ours_line(args, world, m):
     }
     if m.get("learned") is not None:
         line["config"]["learned"] = m["learned"]
+    if getattr(args, "vt_ext", 0):
+        line["config"]["vt_ext"] = args.vt_ext
+    if getattr(args, "boundary_cut", False):
+        line["config"]["boundary_cut"] = 1
     if m.get("autotune") is not None:
         line["config"]["autotune"] = m["autotune"]
     if m.get("e2e_ms"):
@@ -427,7 +436,9 @@ def run_ours(args, rank, world, local_rank):
         tg = [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
                    hd_cells=gr["hd_cells"], hd_vals=gr["hd_vals"]) for gr in groups]
         precision, tile, times = autotune.tune(g, tg, topk=w["K"], seed=w["seed"],
-                                               precisions=precs, use_cache=False)
+                                               precisions=precs, use_cache=False,
+                                               vt_ext=args.vt_ext,
+                                               boundary_cut=int(args.boundary_cut))
         tune_info = {"chosen": f"p{precision}/{tile:#x}", "timed_candidates": len(times),
                      "ms": {k: round(v, 3) for k, v in sorted(times.items(),
                                                                 key=lambda kv: kv[1])[:6]}}
@@ -443,13 +454,15 @@ def run_ours(args, rank, world, local_rank):
             ccw.simulate(g, gr["grid"], n_real=gr["n_real"], topk=w["K"], seed=w["seed"],
                          hd_cells=hd_dev[0][0], hd_vals=hd_dev[0][1],
                          real_base=gr["real_base"], out=outs[0], precision=precision,
-                         learned=1 if args.learned else 0, ccf_tile=tile)
+                         learned=1 if args.learned else 0, ccf_tile=tile,
+                         vt_ext=args.vt_ext, boundary_cut=int(args.boundary_cut))
             return outs
         res = ccw.simulate_groups(
             g, [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
                      hd_cells=h[0], hd_vals=h[1]) for gr, h in zip(groups, hd_dev)],
             topk=w["K"], seed=w["seed"], precision=precision,
-            learned=1 if args.learned else 0, ccf_tile=tile)
+            learned=1 if args.learned else 0, ccf_tile=tile, vt_ext=args.vt_ext,
+            boundary_cut=int(args.boundary_cut))
         return [r[0] for r in res]
 
     for _ in range(max(args.warmup, 0)):

@@ -101,7 +101,24 @@ typedef struct {
                           rows (v <= 2). An autotuner
                           picks it by timing
                           (paper_2404_00441_gb300.autotune). */
-  int32_t reserved[2]; /* must be 0 */
+  int32_t vt_ext;      /* non-causal conditioning (Sec. 4.4), 0..templ: the
+                          template grown by vt_ext cells along the forward
+                          direction of every axis of the path is a virtual
+                          template; hard data in it but outside the template
+                          add to each candidate's mismatch count, a datum
+                          whose TI position falls outside the TI counting
+                          as a mismatch. Scores and the empty-event rule use
+                          the template alone. 0 = off. */
+  int32_t boundary_cut; /* 0: the pattern overwrites its whole window; 1
+                          (2D, templ <= 128): minimum-error boundary cut of
+                          image quilting (Sec. 2): in the path frame, the
+                          cheapest 8-connected column path through the left
+                          overlap strip and row path through the top strip,
+                          over the cells where the grid already holds a
+                          value that differs from the pattern (ties to the
+                          lower column, traced from the last row up); a
+                          simulated cell takes the pattern only on the far
+                          side of both cuts. Hard data are re-imposed. */
 } ccw_params;
 
 /* Shape information of a prepared TI. */

@@ -48,12 +48,12 @@ def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
     return out
 
 
-def _key(ti, groups, topk, score_mode, learned, precisions):
+def _key(ti, groups, topk, score_mode, learned, precisions, vt_ext=0, boundary_cut=0):
     dev = torch.cuda.get_device_name()
     shape = [(tuple(g["grid"]), int(g["n_real"]), 0 if g.get("hd_vals") is None
               else int(g["hd_vals"].numel())) for g in groups]
     return json.dumps([dev, ti.dims, ti.n_facies, ti.level, ti.templ, ti.overlap, shape, topk,
-                       score_mode, learned, list(precisions)])
+                       score_mode, learned, list(precisions), vt_ext, boundary_cut])
 
 
 def _time_call(fn, reps):
@@ -70,11 +70,11 @@ def _time_call(fn, reps):
 
 
 def tune(ti: "ccw.TI", groups, topk=1, seed=0, score_mode=0, learned=0, precisions=(0, 1, 2),
-         reps=2, use_cache=True):
+         reps=2, use_cache=True, vt_ext=0, boundary_cut=0):
     """Times every candidate tiling on simulate_groups(ti, groups, ...) and
     returns (precision, ccf_tile, {"p<precision>/<tile>": ms}). Candidates the
     library refuses (shared memory, exactness bounds) are skipped."""
-    key = _key(ti, groups, topk, score_mode, learned, precisions)
+    key = _key(ti, groups, topk, score_mode, learned, precisions, vt_ext, boundary_cut)
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -91,7 +91,8 @@ def tune(ti: "ccw.TI", groups, topk=1, seed=0, score_mode=0, learned=0, precisio
     for prec, tile in candidates(ti, precisions):
         def call():
             ccw.simulate_groups(ti, groups, topk=topk, seed=seed, score_mode=score_mode,
-                                precision=prec, learned=learned, ccf_tile=tile)
+                                precision=prec, learned=learned, ccf_tile=tile,
+                                vt_ext=vt_ext, boundary_cut=boundary_cut)
         try:
             call()   # builds the plan and captures its graph
         except ccw.CCWError:

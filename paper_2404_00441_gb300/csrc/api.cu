@@ -37,6 +37,8 @@ cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst,
 cudaError_t launch_ti_pyramid(int d, const uint8_t* ti, const int n[3], const int nc[3], int s,
                               int J, int F, float* planes, int px, int16_t* pyr,
                               cudaStream_t st);
+cudaError_t launch_pad_ti(const uint8_t* ti, const int n[3], uint8_t* dst, const int tp[3],
+                          const int border[3], cudaStream_t st);
 cudaError_t launch_hd_overlay(const int32_t* cells, const uint8_t* vals, int n, int d,
                               const int g[3], int F, uint8_t* overlay, int* status,
                               cudaStream_t st);
@@ -148,6 +150,7 @@ struct SimPlan {
   std::vector<GroupPlan> groups;
   int K, score_mode, precision;
   int learned = 0, n_prop = 0, ccf_tile = 0;
+  int vt_ext = 0, cut = 0;        // virtual-template extension, boundary cut
   int n_waves, max_items;
   std::vector<int64_t> wave_off;
   void* items = nullptr;
@@ -205,6 +208,9 @@ struct ccw_ti {
   int device;
   int tile[3], tiles[3], n_tiles;
   uint8_t* d_ti = nullptr;      // cropped fine TI
+  uint8_t* d_tip = nullptr;     // the same inside a border of T cells of 255 (hard-data checks)
+  int tp[3];                    // dims of d_tip
+  int64_t tip_origin = 0;       // offset of cell (0, 0, 0) in d_tip
   float* d_planes = nullptr;    // F planes [nc2][nc1][px]: facies 0..F-2 counts, code sums
   int16_t* d_pyr = nullptr;     // [ncv][sd]
   int* d_status = nullptr;      // device status word
@@ -235,7 +241,7 @@ void fill_ti(const ccw_ti* t, int score_mode, WaveArgs& a) {
   d.plane_vol = t->plane_vol;
   d.plane0 = score_mode == 0 ? 0 : t->F - 1;
   d.nch = score_mode == 0 ? t->F - 1 : 1;
-  d.ti = t->d_ti;
+  d.ti = t->d_tip + t->tip_origin;
   d.pyr = t->d_pyr;
   d.F = t->F;
   d.J = t->J;
@@ -250,6 +256,7 @@ void fill_ti(const ccw_ti* t, int score_mode, WaveArgs& a) {
   d.score_mode = score_mode;
   for (int i = 0; i < 3; ++i) {
     d.n[i] = t->n[i];
+    d.tp[i] = t->tp[i];
     d.nc[i] = t->nc[i];
     d.cd[i] = t->cd[i];
     d.tile[i] = t->tile[i];
@@ -293,7 +300,11 @@ void choose_simt(const ccw_ti* t, int nch, int K, int n_items, int& nb, int& nbu
   }
 }
 
-int hd_capacity(const ccw_ti* t) { return (int)std::min<int64_t>(kMaxHd, ipow(t->T, t->ndim)); }
+// Hard data kept per event record: the window, grown by the virtual
+// template's extension when there is one.
+int hd_capacity(const ccw_ti* t, int vt_ext = 0) {
+  return (int)std::min<int64_t>(kMaxHd, ipow(t->T + vt_ext, t->ndim));
+}
 
 // Precision check: the tensor-core path is exact while every operand fits
 // the 16-bit format exactly (FP16: |v| <= 2048, BF16: |v| <= 256).
@@ -718,14 +729,19 @@ int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3], i
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t nv = (int64_t)t->n[0] * t->n[1] * t->n[2];
   cudaError_t e;
+  for (int a = 0; a < 3; ++a) t->tp[a] = a < ndim ? t->n[a] + 2 * t->T : 1;
+  t->tip_origin = t->T + (int64_t)t->tp[0] * (t->T + (ndim == 3 ? (int64_t)t->tp[1] * t->T : 0));
+  const int64_t tipv = (int64_t)t->tp[0] * t->tp[1] * t->tp[2];
   auto release = [&]() {
     cudaFree(t->d_ti);
+    cudaFree(t->d_tip);
     cudaFree(t->d_planes);
     cudaFree(t->d_pyr);
     cudaFree(t->d_status);
     delete t;
   };
   if ((e = cudaMalloc(&t->d_ti, nv)) != cudaSuccess ||
+      (e = cudaMalloc(&t->d_tip, tipv)) != cudaSuccess ||
       (e = cudaMalloc(&t->d_planes, sizeof(float) * t->plane_vol * t->F)) != cudaSuccess ||
       (e = cudaMalloc(&t->d_pyr, sizeof(int16_t) * t->ncv * t->sd)) != cudaSuccess ||
       (e = cudaMalloc(&t->d_status, sizeof(int))) != cudaSuccess) {
@@ -750,6 +766,14 @@ int ccw_ti_prepare(const uint8_t* ti_dev, int32_t ndim, const int32_t dims[3], i
     return cuda_fail(e, "pyramid kernel");
   }
   ++g_launches;
+  {
+    const int border[3] = {t->T, t->T, ndim == 3 ? t->T : 0};
+    if ((e = launch_pad_ti(t->d_ti, t->n, t->d_tip, t->tp, border, st)) != cudaSuccess) {
+      release();
+      return cuda_fail(e, "padded TI kernel");
+    }
+    ++g_launches;
+  }
   // TMA view of the planes: (x: px, y: nc1, z: nc2, plane: F), one tile box
   auto encode = tensor_map_encoder();
   if (!encode) {
@@ -847,6 +871,7 @@ void ccw_ti_free(ccw_ti* t) {
   cudaFree(t->z8_f16);
   cudaFree(t->z8_bf16);
   cudaFree(t->d_ti);
+  cudaFree(t->d_tip);
   cudaFree(t->d_planes);
   cudaFree(t->d_pyr);
   cudaFree(t->d_status);
@@ -991,7 +1016,7 @@ namespace {
 bool plan_matches(const SimPlan* pl, const ccw_params* p, const ccw_group* groups, int n_groups) {
   if (!pl || pl->n_groups != n_groups || pl->K != p->topk || pl->score_mode != p->score_mode ||
       pl->precision != p->precision || pl->learned != p->learned ||
-      pl->ccf_tile != p->ccf_tile)
+      pl->ccf_tile != p->ccf_tile || pl->vt_ext != p->vt_ext || pl->cut != p->boundary_cut)
     return false;
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
@@ -1014,6 +1039,8 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   pl->precision = p->precision;
   pl->learned = p->learned;
   pl->ccf_tile = p->ccf_tile;
+  pl->vt_ext = p->vt_ext;
+  pl->cut = p->boundary_cut;
   pl->n_prop = p->learned ? t->n_prop : 0;
   pl->n_waves = 0;
   for (int i = 0; i < n_groups; ++i) {
@@ -1059,7 +1086,7 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   }
   pl->wave_off[pl->n_waves] = (int64_t)items.size();
   const int nch = p->score_mode == 0 ? t->F - 1 : 1;
-  event_layout(nch, t->rows, t->TjP, hd_capacity(t), t->F, t->rows * t->Tj, pl->evl);
+  event_layout(nch, t->rows, t->TjP, hd_capacity(t, p->vt_ext), t->F, t->rows * t->Tj, pl->evl);
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
   plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
@@ -1117,6 +1144,8 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
   a.call = pl->call;
   a.K = pl->K;
   a.part = (unsigned long long*)pl->part;
+  a.vt_ext = pl->vt_ext;
+  a.cut = pl->cut;
   if (pl->learned) {
     a.learned = 1;
     a.net = t->d_net;
@@ -1211,8 +1240,11 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
     if (p->score_mode != 0) return fail(CCW_EINVAL, "learned = 1 needs the one-hot score");
     if (p->topk > t->n_prop) return fail(CCW_EINVAL, "topk > the proposal's n_prop");
   }
-  for (int i = 0; i < 2; ++i)
-    if (p->reserved[i]) return fail(CCW_EINVAL, "reserved fields must be 0");
+  if (p->vt_ext < 0 || p->vt_ext > t->T)
+    return fail(CCW_EINVAL, "vt_ext must be in [0, templ = %d]", t->T);
+  if (p->boundary_cut != 0 && p->boundary_cut != 1) return fail(CCW_EINVAL, "bad boundary_cut");
+  if (p->boundary_cut && (d != 2 || t->T > kMaxCutTempl))
+    return fail(CCW_EINVAL, "the boundary cut needs 2D and templ <= %d", kMaxCutTempl);
   if (int rc = check_score_bound(t, p->score_mode)) return rc;
   if (n_groups < 1 || !groups) return fail(CCW_EINVAL, "at least one grid group is needed");
   for (int i = 0; i < n_groups; ++i) {

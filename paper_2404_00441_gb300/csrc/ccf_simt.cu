@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads)
                                                     a.ev.hd_off);
     // hard-data mismatches of the thread's candidates, loads overlapped
     const uint8_t* tb0 =
-        t.ti + (int64_t)s * (cx0 + kRx * ltx) + (int64_t)t.n[0] * ((int64_t)s * cy + (int64_t)t.n[1] * s * cz);
+        t.ti + (int64_t)s * (cx0 + kRx * ltx) + (int64_t)t.tp[0] * ((int64_t)s * cy + (int64_t)t.tp[1] * s * cz);
     const bool row_ok = cy < t.cd[1] && cz < t.cd[2];
     int misv[kRx];
 #pragma unroll

@@ -21,6 +21,7 @@ constexpr int kThreads = 256;     // threads per CTA (at most, for event and fin
 constexpr int kWarps = kThreads / 32;
 constexpr int kRx = 4;            // consecutive x-candidates per thread
 constexpr int kMaxHd = 1024;      // hard data kept per template window
+constexpr int kMaxCutTempl = 128; // largest template of the boundary-cut paste
 constexpr int kMaxLevel2D = 4;
 constexpr int kMaxLevel3D = 2;
 constexpr int kTcMaxMt = 4;       // M-tiles per CTA of the tensor-core CCF
@@ -103,10 +104,12 @@ struct TiDev {
   int px;               // plane row pitch (floats, multiple of 4, zero padded)
   int64_t plane_vol;    // floats per plane
   int plane0, nch;      // planes scored by the active score mode
-  const uint8_t* ti;    // cropped fine TI [n]
+  const uint8_t* ti;    // cropped fine TI, cell (0, 0, 0) of a copy padded by T cells
+                        // of 255 on both sides of every axis (pitches tp)
   const int16_t* pyr;   // per-block Haar coefficients [ncv][sd]
   int F, J, s, sd, T, Tj, TjP, chunks, rows, d, score_mode;
   int n[3], nc[3], cd[3];
+  int tp[3];            // row and plane pitches of the padded fine TI
   int64_t ncv, P;
   int tile[3];          // candidates per CTA tile along x, y, z
   int tiles[3], n_tiles;
@@ -116,8 +119,9 @@ struct TiDev {
 // the CCF kernel (phase B). Record of item i starts at base + i * stride:
 //   int32 meta[16] (kEv*), uint32 rowmask[rows] (bit g: 4-wide tap chunk g
 //   holds a non-zero weight in some channel), int2 hd[hd_cap] (.x: offset of
-//   the hard datum in the cropped fine TI relative to a candidate's first
-//   cell; .y: (offset in the template window << 8) | code),
+//   the hard datum in the padded fine TI relative to a candidate's first
+//   cell; .y: (offset in the template window << 8) | code, or kHdVirtual |
+//   code for a datum of the virtual template outside the window),
 //   float w[nch][rows][TjP], uint8 counts[F][Tj^d] (facies counts of the
 //   level-J blocks, saturated at 255).
 // meta[kEvMaskType]: overlap strips fully known in 2D (bit 0 low x, 1 high x,
@@ -125,6 +129,9 @@ struct TiDev {
 // the item (the full CCF then skips it).
 enum { kEvKnown = 0, kEvConst = 1, kEvMaskCells = 2, kEvNHd = 3, kEvMaskType = 4,
        kEvResolved = 5 };
+// Hard-data record flag: the datum lies in the virtual template (non-causal
+// conditioning), outside the window, so it is counted but never pasted.
+constexpr int kHdVirtual = (int)0x80000000u;
 struct EvDev {
   unsigned char* base;
   int64_t stride;
@@ -207,6 +214,9 @@ struct WaveArgs {
   float* prop_gap;          // [n_items] relative embedding gap of the proposals
   int n_prop;
   int Oj;                   // overlap in level-J blocks
+  // paste and conditioning variants (simulation mode)
+  int vt_ext;               // cells the virtual template extends the window forward
+  int cut;                  // 1: minimum-error boundary cut at paste (2D)
 };
 
 }  // namespace ccw

@@ -324,12 +324,14 @@ __device__ void paste_blocks(const PasteGeom& p, const int16_t* staged, int nthr
 }
 
 // Re-impose the hard data of a pasted window (event-record list, int2 .y =
-// (window offset << 8) | code). Call after a barrier that follows the paste.
+// (window offset << 8) | code; virtual-template entries are skipped). Call
+// after a barrier that follows the paste.
 template <int D>
 __device__ void paste_hard_data(const PasteGeom& p, const int2* hdl, int n_hd, int T,
                                 int nthreads) {
   for (int k = threadIdx.x; k < n_hd; k += nthreads) {
     const int e = hdl[k].y;
+    if (e < 0) continue;   // kHdVirtual: outside the window
     const int q = e >> 8;
     const int qx = q % T, qy = (q / T) % T, qz = (D == 3) ? q / (T * T) : 0;
     const int gx = p.o[0] + qx, gy = p.o[1] + qy, gz = p.o[2] + qz;
@@ -343,6 +345,7 @@ __device__ void paste_hard_data(const PasteGeom& p, const int2* hdl, int n_hd, i
 struct ItemPos {
   int group, slot, patch;
   uint32_t r, p;
+  uint32_t flips;           // bit a: the path runs backwards along axis a
   int o[3], off[3];
   uint8_t* sg;              // this realization's padded grid
   const uint8_t* overlay;   // the group's hard data
@@ -364,6 +367,7 @@ __device__ __forceinline__ ItemPos decode_sim_item(const WaveArgs& a, int item) 
   it.p = (uint32_t)it.patch;
   const uint32_t flips =
       c->path_random ? (draw_word(c->seed, it.r, 0u, 1u) & ((1u << D) - 1u)) : 0u;
+  it.flips = flips;
   const int np0 = s.np[0], np1 = s.np[1];
   const int ip[3] = {it.patch % np0, (it.patch / np0) % np1, it.patch / (np0 * np1)};
 #pragma unroll

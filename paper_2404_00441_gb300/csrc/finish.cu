@@ -26,6 +26,78 @@ __device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
 
 constexpr int kKeysPerThread = 8;
 
+// Shared-memory bytes of the boundary-cut paste behind the staged
+// coefficients: the pattern (T^2 bytes), the cumulative costs of the two
+// strips (2 x T x O uint16) and the two cuts (2 x T int16).
+__host__ __device__ inline int cut_smem_bytes(int T, int O) {
+  return ((T * T + 15) & ~15) + 4 * T * O + 4 * T;
+}
+
+// Paste of a 2D pattern through the minimum-error boundary cuts of image
+// quilting (Efros and Freeman; the IQ method reviewed in Sec. 2). `pat` holds
+// the pattern (T x T, x fastest) in shared memory. In the path frame (x', y')
+// = window offsets mirrored along the axes the path runs backwards, the cost
+// of a cell is 1 where the grid already holds a value that differs from the
+// pattern. Warp 0 runs the dynamic program of the column cut through the
+// left strip (rows y', columns x' < O), warp 1 that of the row cut through
+// the top strip (rows x', columns y' < O), lanes over the strip's columns;
+// lane 0 traces each cut back from the cheapest cell of the last row (ties
+// to the lower column). A simulated cell then takes the pattern only on the
+// far side of both cuts; cells never simulated always take it.
+__device__ void quilt_paste(const PasteGeom& g, const uint8_t* pat, int T, int O, uint32_t flips,
+                            unsigned char* work, int nth) {
+  uint16_t* Ev = reinterpret_cast<uint16_t*>(work);
+  uint16_t* Eh = Ev + T * O;
+  int16_t* cv = reinterpret_cast<int16_t*>(Eh + T * O);
+  int16_t* ch = cv + T;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool fx = flips & 1u, fy = flips & 2u;
+  if (warp < 2) {
+    uint16_t* E = warp == 0 ? Ev : Eh;
+    for (int i = 0; i < T; ++i) {
+      for (int j = lane; j < O; j += 32) {
+        const int xp = warp == 0 ? j : i, yp = warp == 0 ? i : j;
+        const int qx = fx ? T - 1 - xp : xp, qy = fy ? T - 1 - yp : yp;
+        const uint8_t old = g.grid[(g.o[0] + qx) + (int64_t)g.g[0] * (g.o[1] + qy)];
+        int e = (old != CCW_UNKNOWN && old != pat[qx + T * qy]) ? 1 : 0;
+        if (i > 0) {
+          const uint16_t* prev = E + (i - 1) * O;
+          int m = prev[j];
+          if (j > 0) m = min(m, (int)prev[j - 1]);
+          if (j + 1 < O) m = min(m, (int)prev[j + 1]);
+          e += m;
+        }
+        E[i * O + j] = (uint16_t)e;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      int16_t* cut = warp == 0 ? cv : ch;
+      const uint16_t* last = E + (T - 1) * O;
+      int c = 0;
+      for (int j = 1; j < O; ++j)
+        if (last[j] < last[c]) c = j;
+      cut[T - 1] = (int16_t)c;
+      for (int i = T - 2; i >= 0; --i) {
+        const uint16_t* row = E + i * O;
+        const int lo = c > 0 ? c - 1 : 0, hi = c + 1 < O ? c + 1 : O - 1;
+        int b = lo;
+        for (int j = lo + 1; j <= hi; ++j)
+          if (row[j] < row[b]) b = j;
+        c = b;
+        cut[i] = (int16_t)c;
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < T * T; q += nth) {
+    const int qx = q % T, qy = q / T;
+    uint8_t* cell = g.grid + (g.o[0] + qx) + (int64_t)g.g[0] * (g.o[1] + qy);
+    const int xp = fx ? T - 1 - qx : qx, yp = fy ? T - 1 - qy : qy;
+    if (*cell == CCW_UNKNOWN || (xp >= cv[yp] && yp >= ch[xp])) *cell = pat[q];
+  }
+}
+
 template <int D, int MODE>
 __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ WaveArgs a,
                                                      int staged_bytes) {
@@ -112,7 +184,27 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     e[tid] = val;
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
-  if (staged_bytes > 0) {
+  if (D == 2 && a.cut && a.Oj > 0) {
+    // the pattern into shared memory, then the boundary-cut paste (the
+    // launch guarantees staged_bytes > 0 and the cut buffers behind it)
+    unsigned char* pat = reinterpret_cast<unsigned char*>(staged) + ((staged_bytes + 15) & ~15);
+    stage_blocks<D>(g, pk, t.J, staged, nth);
+    __syncthreads();
+    PasteGeom gl = g;
+    gl.grid = pat;
+    gl.g[0] = t.T;
+    gl.g[1] = t.T;
+    gl.g[2] = 1;
+    gl.o[0] = gl.o[1] = gl.o[2] = 0;
+    if (t.J == 2)
+      paste_blocks<D, 4>(gl, staged, nth, true);
+    else if (t.J == 1)
+      paste_blocks<D, 2>(gl, staged, nth, true);
+    else
+      paste_pixels<D>(gl, pk, t.J, nth, staged);
+    __syncthreads();
+    quilt_paste(g, pat, t.T, a.Oj * t.s, it.flips, pat + ((t.T * t.T + 15) & ~15), nth);
+  } else if (staged_bytes > 0) {
     stage_blocks<D>(g, pk, t.J, staged, nth);
     __syncthreads();
     // block-wise inverse in registers for the common levels, else per cell
@@ -138,15 +230,20 @@ static cudaError_t launch_t(const WaveArgs& a, bool pdl, cudaStream_t st) {
   // simulating, if they fit
   const int64_t tv = (D == 3) ? (int64_t)a.ti.T * a.ti.T * a.ti.T : (int64_t)a.ti.T * a.ti.T;
   const int staged = (MODE == kModeSim && tv * 2 <= 160 * 1024) ? (int)(tv * 2) : 0;
+  // the boundary-cut paste (2D, T <= kMaxCutTempl, so staged > 0) keeps the
+  // pattern and the cut buffers behind the coefficients
+  const bool cut = D == 2 && MODE == kModeSim && a.cut && a.Oj > 0;
+  const int smem =
+      cut ? ((staged + 15) & ~15) + cut_smem_bytes(a.ti.T, a.Oj * a.ti.s) : staged;
   auto fn = k_finish<D, MODE>;
-  if (staged > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, staged);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
   // one thread per level-J block of the pattern, up to kThreads
   const int nblk = (D == 3) ? a.ti.Tj * a.ti.Tj * a.ti.Tj : a.ti.Tj * a.ti.Tj;
   const int nth = std::min(kThreads, std::max(96, (nblk + 31) / 32 * 32));   // >= 4 + K log words
-  return launch_pdl(fn, dim3(a.n_items), dim3(nth), staged, st, pdl, a, staged);
+  return launch_pdl(fn, dim3(a.n_items), dim3(nth), smem, st, pdl, a, staged);
 }
 
 cudaError_t launch_finish(int mode, const WaveArgs& a, bool pdl, cudaStream_t st) {

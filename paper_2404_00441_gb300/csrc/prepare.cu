@@ -28,6 +28,23 @@ __global__ void k_crop_ti(const uint8_t* __restrict__ src, int sx, int sy, uint8
   }
 }
 
+// The cropped TI inside a border of (bx, by, bz) cells of 255: the fine TI
+// that the hard-data checks read, so that a datum of the virtual template
+// whose position falls outside the TI never matches.
+__global__ void k_pad_ti(const uint8_t* __restrict__ ti, int nx, int ny, int nz,
+                         uint8_t* __restrict__ dst, int px, int py, int pz, int bx, int by,
+                         int bz) {
+  const int64_t total = (int64_t)px * py * pz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % px) - bx;
+    const int y = (int)((i / px) % py) - by;
+    const int z = (int)(i / ((int64_t)px * py)) - bz;
+    const bool in = x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz;
+    dst[i] = in ? ti[x + (int64_t)nx * (y + (int64_t)ny * z)] : (uint8_t)CCW_UNKNOWN;
+  }
+}
+
 // Forward scaled Haar of one s^d block in place (the layout inverted by
 // haar_block_inverse in search.cu): level j = 1..J, axes x, y, z; samples
 // 2^(j-1) apart are replaced by their sum (lower position) and difference
@@ -197,6 +214,15 @@ cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst,
   const int64_t total = (int64_t)n[0] * n[1] * n[2];
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
   k_crop_ti<<<blocks, 256, 0, st>>>(src, sdims[0], sdims[1], dst, n[0], n[1], n[2], F, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_ti(const uint8_t* ti, const int n[3], uint8_t* dst, const int tp[3],
+                          const int border[3], cudaStream_t st) {
+  const int64_t total = (int64_t)tp[0] * tp[1] * tp[2];
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_pad_ti<<<blocks, 256, 0, st>>>(ti, n[0], n[1], n[2], dst, tp[0], tp[1], tp[2], border[0],
+                                   border[1], border[2]);
   return cudaGetLastError();
 }
 

@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256) k_rerank(const __grid_constant__ WaveArgs
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   if (pi < np && part == 0) {
     const uint8_t* tb = t.ti + (int64_t)t.s * (c % t.cd[0]) +
-                        (int64_t)t.n[0] * ((int64_t)t.s * (c / t.cd[0]));
+                        (int64_t)t.tp[0] * ((int64_t)t.s * (c / t.cd[0]));
     int mis = 0;
     for (int k = 0; k < nhd; ++k) {
       const int2 e = hdl[k];

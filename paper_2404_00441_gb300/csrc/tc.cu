@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       const int cx = (int)(Lpos % a.px8), cy = (int)(Lpos / a.px8);
       const bool valid = cx < t.cd[0] && cy < t.cd[1];
       cand[i] = make_int2(valid ? cx + t.cd[0] * cy : -1,
-                          t.s * cx + t.n[0] * (t.s * cy));
+                          t.s * cx + t.tp[0] * (t.s * cy));
     }
     const int n = tid % nt, nseg = kTcThreads / nt, seg = tid / nt;
     const int seg_len = 128 / nseg;
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       const int cx = (int)(Lpos % a.px8), cy = (int)(Lpos / a.px8);
       const bool valid = j < n_mt && cx < t.cd[0] && cy < t.cd[1];
       cidx[j] = valid ? cx + t.cd[0] * cy : -1;
-      tb[j] = t.ti + (int64_t)t.s * cx + (int64_t)t.n[0] * ((int64_t)t.s * cy);
+      tb[j] = t.ti + (int64_t)t.s * cx + (int64_t)t.tp[0] * ((int64_t)t.s * cy);
     }
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1

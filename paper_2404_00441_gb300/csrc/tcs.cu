@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kTcsThreads) k_ccf_tcs(const __grid_constant__
       const int cy = (int)(rest % t.nc[1]), cz = (int)(rest / t.nc[1]);
       const bool valid = cx < t.cd[0] && cy < t.cd[1] && cz < t.cd[2];
       cand[i] = make_int2(valid ? cx + t.cd[0] * (cy + t.cd[1] * cz) : -1,
-                          t.s * cx + t.n[0] * (t.s * cy + t.n[1] * (t.s * cz)));
+                          t.s * cx + t.tp[0] * (t.s * cy + t.tp[1] * (t.s * cz)));
     }
     __syncthreads();   // cand is read by every warp from here on
     // items in chunks of ntc columns: the score tile stays small for any nt
