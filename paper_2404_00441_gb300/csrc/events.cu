@@ -199,22 +199,35 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     // along the axes the path runs backwards; the data only join the
     // mismatch count (record flag kHdVirtual: never pasted).
     const int W = T + a.vt_ext;
-    const int64_t nv = (D == 3) ? (int64_t)W * W * W : (int64_t)W * W;
-    for (int64_t v = tid; v < nv; v += nth) {
-      const int vx = (int)(v % W), vy = (int)((v / W) % W);
-      const int vz = (D == 3) ? (int)(v / ((int64_t)W * W)) : 0;
-      if (vx < T && vy < T && vz < T) continue;   // a window cell
-      const int qx = (it.flips & 1u) ? T - 1 - vx : vx;
-      const int qy = (it.flips & 2u) ? T - 1 - vy : vy;
-      const int qz = (D == 3 && (it.flips & 4u)) ? T - 1 - vz : vz;
-      const int hx = it.o[0] + qx - it.off[0], hy = it.o[1] + qy - it.off[1],
-                hz = it.o[2] + qz - it.off[2];
-      if (hx < 0 || hy < 0 || hz < 0 || hx >= it.G[0] || hy >= it.G[1] || hz >= it.G[2]) continue;
-      const int h = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
-      if (h == CCW_UNKNOWN) continue;
-      const int k = atomicAdd(&cnt[3], 1);
-      if (k < a.ev.hd_cap) hdl[k] = make_int2(qx + t.tp[0] * (qy + t.tp[1] * qz), kHdVirtual | h);
-      if (h >= t.F) bad |= kStatusBadCode;
+    const int nv = (D == 3) ? W * W * W : W * W;
+    constexpr int kB = 4;   // cells per thread whose overlay loads are in flight together
+    for (int v0 = tid; v0 < nv; v0 += kB * nth) {
+      int h[kB], off[kB];
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        h[b] = CCW_UNKNOWN;
+        off[b] = 0;
+        const int v = v0 + b * nth;
+        if (v >= nv) continue;
+        const int vx = v % W, vy = (v / W) % W, vz = (D == 3) ? v / (W * W) : 0;
+        if (vx < T && vy < T && vz < T) continue;   // a window cell
+        const int qx = (it.flips & 1u) ? T - 1 - vx : vx;
+        const int qy = (it.flips & 2u) ? T - 1 - vy : vy;
+        const int qz = (D == 3 && (it.flips & 4u)) ? T - 1 - vz : vz;
+        const int hx = it.o[0] + qx - it.off[0], hy = it.o[1] + qy - it.off[1],
+                  hz = it.o[2] + qz - it.off[2];
+        if (hx < 0 || hy < 0 || hz < 0 || hx >= it.G[0] || hy >= it.G[1] || hz >= it.G[2])
+          continue;
+        h[b] = __ldg(it.overlay + hx + (int64_t)it.G[0] * (hy + (int64_t)it.G[1] * hz));
+        off[b] = qx + t.tp[0] * (qy + t.tp[1] * qz);
+      }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        if (h[b] == CCW_UNKNOWN) continue;
+        const int k = atomicAdd(&cnt[3], 1);
+        if (k < a.ev.hd_cap) hdl[k] = make_int2(off[b], kHdVirtual | h[b]);
+        if (h[b] >= t.F) bad |= kStatusBadCode;
+      }
     }
   }
   my_known = __reduce_add_sync(0xffffffffu, my_known);

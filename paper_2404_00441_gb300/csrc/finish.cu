@@ -27,10 +27,71 @@ __device__ __forceinline__ uint64_t block_min_u64(uint64_t v, uint64_t* red) {
 constexpr int kKeysPerThread = 8;
 
 // Shared-memory bytes of the boundary-cut paste behind the staged
-// coefficients: the pattern (T^2 bytes), the cumulative costs of the two
-// strips (2 x T x O uint16) and the two cuts (2 x T int16).
+// coefficients: the pattern (T^2 bytes), the 0/1 costs and the predecessor
+// columns of the two strips (2 x T x O bytes each) and the two cuts (2 x T
+// int16).
 __host__ __device__ inline int cut_smem_bytes(int T, int O) {
   return ((T * T + 15) & ~15) + 4 * T * O + 4 * T;
+}
+
+// Minimum-error cut of one strip (rows i = 0..T-1, columns j < O <= 64) by
+// one warp: lane l holds the cumulative costs of columns l and l + 32 in
+// registers,
+//   E(0, j) = err(0, j),  E(i, j) = err(i, j) + min_{|j' - j| <= 1} E(i - 1, j'),
+// and records for every cell the predecessor column that attains the min
+// (the lowest on ties). Lane 0 then starts at the cheapest column of the
+// last row (the lowest on ties) and follows the predecessors up; the result
+// is the same path as tracing back through E itself.
+__device__ void strip_cut(const uint8_t* err, uint8_t* pred, int T, int O, int16_t* cut) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  constexpr int kBig = 1 << 20;
+  const int j0 = lane, j1 = lane + 32;
+  int e0 = kBig, e1 = kBig;   // E of the previous row (kBig beyond the strip)
+  for (int i = 0; i < T; ++i) {
+    const int up0 = __shfl_up_sync(full, e0, 1), up1 = __shfl_up_sync(full, e1, 1);
+    const int dn0 = __shfl_down_sync(full, e0, 1), dn1 = __shfl_down_sync(full, e1, 1);
+    const int last0 = __shfl_sync(full, e0, 31), first1 = __shfl_sync(full, e1, 0);
+    if (i == 0) {
+      if (j0 < O) e0 = err[j0];
+      if (j1 < O) e1 = err[j1];
+      continue;
+    }
+    // neighbours in column order: left (j - 1), self, right (j + 1)
+    const int l0 = lane > 0 ? up0 : kBig, r0 = lane < 31 ? dn0 : first1;
+    const int l1 = lane > 0 ? up1 : last0, r1 = lane < 31 ? dn1 : kBig;
+    int m0 = l0, p0 = j0 - 1;
+    if (e0 < m0) { m0 = e0; p0 = j0; }
+    if (r0 < m0) { m0 = r0; p0 = j0 + 1; }
+    int m1 = l1, p1 = j1 - 1;
+    if (e1 < m1) { m1 = e1; p1 = j1; }
+    if (r1 < m1) { m1 = r1; p1 = j1 + 1; }
+    if (j0 < O) {
+      e0 = err[i * O + j0] + m0;
+      pred[i * O + j0] = (uint8_t)p0;
+    }
+    if (j1 < O) {
+      e1 = err[i * O + j1] + m1;
+      pred[i * O + j1] = (uint8_t)p1;
+    }
+  }
+  // cheapest column of the last row, lowest on ties: (E, column) minimum
+  int bv = j0 < O ? e0 : kBig, bj = j0;
+  if (j1 < O && e1 < bv) { bv = e1; bj = j1; }
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const int ov = __shfl_xor_sync(full, bv, d), oj = __shfl_xor_sync(full, bj, d);
+    if (ov < bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    int c = bj;
+    cut[T - 1] = (int16_t)c;
+    for (int i = T - 1; i > 0; --i) {
+      c = pred[i * O + c];
+      cut[i - 1] = (int16_t)c;
+    }
+  }
 }
 
 // Paste of a 2D pattern through the minimum-error boundary cuts of image
@@ -38,57 +99,32 @@ __host__ __device__ inline int cut_smem_bytes(int T, int O) {
 // the pattern (T x T, x fastest) in shared memory. In the path frame (x', y')
 // = window offsets mirrored along the axes the path runs backwards, the cost
 // of a cell is 1 where the grid already holds a value that differs from the
-// pattern. Warp 0 runs the dynamic program of the column cut through the
-// left strip (rows y', columns x' < O), warp 1 that of the row cut through
-// the top strip (rows x', columns y' < O), lanes over the strip's columns;
-// lane 0 traces each cut back from the cheapest cell of the last row (ties
-// to the lower column). A simulated cell then takes the pattern only on the
-// far side of both cuts; cells never simulated always take it.
+// pattern. The column cut runs through the left strip (rows y', columns
+// x' < O; warp 0), the row cut through the top strip (rows x', columns
+// y' < O; warp 1). A simulated cell then takes the pattern only on the far
+// side of both cuts; cells never simulated always take it.
 __device__ void quilt_paste(const PasteGeom& g, const uint8_t* pat, int T, int O, uint32_t flips,
                             unsigned char* work, int nth) {
-  uint16_t* Ev = reinterpret_cast<uint16_t*>(work);
-  uint16_t* Eh = Ev + T * O;
-  int16_t* cv = reinterpret_cast<int16_t*>(Eh + T * O);
+  uint8_t* errv = work;
+  uint8_t* errh = errv + T * O;
+  uint8_t* predv = errh + T * O;
+  uint8_t* predh = predv + T * O;
+  int16_t* cv = reinterpret_cast<int16_t*>(predh + T * O);   // 4 T O bytes: even
   int16_t* ch = cv + T;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const bool fx = flips & 1u, fy = flips & 2u;
-  if (warp < 2) {
-    uint16_t* E = warp == 0 ? Ev : Eh;
-    for (int i = 0; i < T; ++i) {
-      for (int j = lane; j < O; j += 32) {
-        const int xp = warp == 0 ? j : i, yp = warp == 0 ? i : j;
-        const int qx = fx ? T - 1 - xp : xp, qy = fy ? T - 1 - yp : yp;
-        const uint8_t old = g.grid[(g.o[0] + qx) + (int64_t)g.g[0] * (g.o[1] + qy)];
-        int e = (old != CCW_UNKNOWN && old != pat[qx + T * qy]) ? 1 : 0;
-        if (i > 0) {
-          const uint16_t* prev = E + (i - 1) * O;
-          int m = prev[j];
-          if (j > 0) m = min(m, (int)prev[j - 1]);
-          if (j + 1 < O) m = min(m, (int)prev[j + 1]);
-          e += m;
-        }
-        E[i * O + j] = (uint16_t)e;
-      }
-      __syncwarp();
-    }
-    if (lane == 0) {
-      int16_t* cut = warp == 0 ? cv : ch;
-      const uint16_t* last = E + (T - 1) * O;
-      int c = 0;
-      for (int j = 1; j < O; ++j)
-        if (last[j] < last[c]) c = j;
-      cut[T - 1] = (int16_t)c;
-      for (int i = T - 2; i >= 0; --i) {
-        const uint16_t* row = E + i * O;
-        const int lo = c > 0 ? c - 1 : 0, hi = c + 1 < O ? c + 1 : O - 1;
-        int b = lo;
-        for (int j = lo + 1; j <= hi; ++j)
-          if (row[j] < row[b]) b = j;
-        c = b;
-        cut[i] = (int16_t)c;
-      }
-    }
+  // costs of both strips, every thread (row i runs along the strip)
+  for (int k = tid; k < 2 * T * O; k += nth) {
+    const int strip = k / (T * O), r = k - strip * T * O;
+    const int i = r / O, j = r - i * O;
+    const int xp = strip == 0 ? j : i, yp = strip == 0 ? i : j;
+    const int qx = fx ? T - 1 - xp : xp, qy = fy ? T - 1 - yp : yp;
+    const uint8_t old = g.grid[(g.o[0] + qx) + (int64_t)g.g[0] * (g.o[1] + qy)];
+    (strip == 0 ? errv : errh)[r] = (old != CCW_UNKNOWN && old != pat[qx + T * qy]) ? 1 : 0;
   }
+  __syncthreads();
+  if (warp == 0) strip_cut(errv, predv, T, O, cv);
+  else if (warp == 1) strip_cut(errh, predh, T, O, ch);
   __syncthreads();
   for (int q = tid; q < T * T; q += nth) {
     const int qx = q % T, qy = q / T;
