@@ -198,8 +198,14 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
     // of the path, outside the window. Path-frame offsets v are mirrored
     // along the axes the path runs backwards; the data only join the
     // mismatch count (record flag kHdVirtual: never pasted).
-    const int W = T + a.vt_ext;
-    const int nv = (D == 3) ? W * W * W : W * W;
+    const int E = a.vt_ext, W = T + E;
+    // the cells of the grown window outside the window, in path frame:
+    // 2D: rows vy >= T (every vx), then vx >= T of rows vy < T;
+    // 3D: planes vz >= T, then rows vy >= T of planes vz < T, then vx >= T
+    const int nA = (D == 3) ? W * W * E : W * E;
+    const int nB = (D == 3) ? T * E * W : T * E;
+    const int nC = (D == 3) ? T * T * E : 0;
+    const int nv = nA + nB + nC;
     constexpr int kB = 4;   // cells per thread whose overlay loads are in flight together
     for (int v0 = tid; v0 < nv; v0 += kB * nth) {
       int h[kB], off[kB];
@@ -209,8 +215,30 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
         off[b] = 0;
         const int v = v0 + b * nth;
         if (v >= nv) continue;
-        const int vx = v % W, vy = (v / W) % W, vz = (D == 3) ? v / (W * W) : 0;
-        if (vx < T && vy < T && vz < T) continue;   // a window cell
+        int vx, vy, vz = 0;
+        if (D == 2) {
+          if (v < nA) {
+            vy = T + v / W;
+            vx = v % W;
+          } else {
+            vy = (v - nA) / E;
+            vx = T + (v - nA) % E;
+          }
+        } else if (v < nA) {
+          vz = T + v / (W * W);
+          vy = (v / W) % W;
+          vx = v % W;
+        } else if (v < nA + nB) {
+          const int r = v - nA;
+          vz = r / (E * W);
+          vy = T + (r / W) % E;
+          vx = r % W;
+        } else {
+          const int r = v - nA - nB;
+          vz = r / (T * E);
+          vy = (r / E) % T;
+          vx = T + r % E;
+        }
         const int qx = (it.flips & 1u) ? T - 1 - vx : vx;
         const int qy = (it.flips & 2u) ? T - 1 - vy : vy;
         const int qz = (D == 3 && (it.flips & 4u)) ? T - 1 - vz : vz;

@@ -34,9 +34,9 @@ __host__ __device__ inline int cut_smem_bytes(int T, int O) {
   return ((T * T + 15) & ~15) + 4 * T * O + 4 * T;
 }
 
-// Minimum-error cut of one strip (rows i = 0..T-1, columns j < O <= 64) by
-// one warp: lane l holds the cumulative costs of columns l and l + 32 in
-// registers,
+// Minimum-error cut of one strip (rows i = 0..T-1, columns j < O <= 64; the
+// 0/1 cost of a cell in bit 0 of err) by one warp: lane l holds the
+// cumulative costs of columns l and l + 32 in registers,
 //   E(0, j) = err(0, j),  E(i, j) = err(i, j) + min_{|j' - j| <= 1} E(i - 1, j'),
 // and records for every cell the predecessor column that attains the min
 // (the lowest on ties). Lane 0 then starts at the cheapest column of the
@@ -53,8 +53,8 @@ __device__ void strip_cut(const uint8_t* err, uint8_t* pred, int T, int O, int16
     const int dn0 = __shfl_down_sync(full, e0, 1), dn1 = __shfl_down_sync(full, e1, 1);
     const int last0 = __shfl_sync(full, e0, 31), first1 = __shfl_sync(full, e1, 0);
     if (i == 0) {
-      if (j0 < O) e0 = err[j0];
-      if (j1 < O) e1 = err[j1];
+      if (j0 < O) e0 = err[j0] & 1;
+      if (j1 < O) e1 = err[j1] & 1;
       continue;
     }
     // neighbours in column order: left (j - 1), self, right (j + 1)
@@ -67,11 +67,11 @@ __device__ void strip_cut(const uint8_t* err, uint8_t* pred, int T, int O, int16
     if (e1 < m1) { m1 = e1; p1 = j1; }
     if (r1 < m1) { m1 = r1; p1 = j1 + 1; }
     if (j0 < O) {
-      e0 = err[i * O + j0] + m0;
+      e0 = (err[i * O + j0] & 1) + m0;
       pred[i * O + j0] = (uint8_t)p0;
     }
     if (j1 < O) {
-      e1 = err[i * O + j1] + m1;
+      e1 = (err[i * O + j1] & 1) + m1;
       pred[i * O + j1] = (uint8_t)p1;
     }
   }
@@ -113,24 +113,52 @@ __device__ void quilt_paste(const PasteGeom& g, const uint8_t* pat, int T, int O
   int16_t* ch = cv + T;
   const int tid = threadIdx.x, warp = tid >> 5;
   const bool fx = flips & 1u, fy = flips & 2u;
-  // costs of both strips, every thread (row i runs along the strip)
+  // costs of both strips, every thread (row i runs along the strip): bit 0
+  // = the grid holds a value that differs from the pattern, bit 1 = the
+  // grid holds a value
+#pragma unroll 4
   for (int k = tid; k < 2 * T * O; k += nth) {
     const int strip = k / (T * O), r = k - strip * T * O;
     const int i = r / O, j = r - i * O;
     const int xp = strip == 0 ? j : i, yp = strip == 0 ? i : j;
     const int qx = fx ? T - 1 - xp : xp, qy = fy ? T - 1 - yp : yp;
     const uint8_t old = g.grid[(g.o[0] + qx) + (int64_t)g.g[0] * (g.o[1] + qy)];
-    (strip == 0 ? errv : errh)[r] = (old != CCW_UNKNOWN && old != pat[qx + T * qy]) ? 1 : 0;
+    (strip == 0 ? errv : errh)[r] =
+        old == CCW_UNKNOWN ? 0 : (old != pat[qx + T * qy] ? 3 : 2);
   }
   __syncthreads();
   if (warp == 0) strip_cut(errv, predv, T, O, cv);
   else if (warp == 1) strip_cut(errh, predh, T, O, ch);
   __syncthreads();
-  for (int q = tid; q < T * T; q += nth) {
-    const int qx = q % T, qy = q / T;
-    uint8_t* cell = g.grid + (g.o[0] + qx) + (int64_t)g.g[0] * (g.o[1] + qy);
-    const int xp = fx ? T - 1 - qx : qx, yp = fy ? T - 1 - qy : qy;
-    if (*cell == CCW_UNKNOWN || (xp >= cv[yp] && yp >= ch[xp])) *cell = pat[q];
+  // the paste, 4 cells per thread: a cell keeps the grid's value when it
+  // lies in a strip, holds a value and is on the near side of a cut (the
+  // strips' flags say which cells hold a value, so the grid is not read)
+  const bool aligned = (T & 3) == 0 && (g.o[0] & 3) == 0 && (g.g[0] & 3) == 0;
+  const int T4 = (T + 3) >> 2;
+  for (int w = tid; w < T * T4; w += nth) {
+    const int qy = w / T4, qx0 = (w - qy * T4) * 4;
+    const int yp = fy ? T - 1 - qy : qy;
+    unsigned keep = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int qx = qx0 + c;
+      if (qx >= T) {
+        keep |= 1u << c;   // beyond the window (T not a multiple of 4)
+        continue;
+      }
+      const int xp = fx ? T - 1 - qx : qx;
+      if (xp >= O && yp >= O) continue;
+      const uint8_t f = xp < O ? errv[yp * O + xp] : errh[xp * O + yp];
+      if ((f & 2) && !(xp >= cv[yp] && yp >= ch[xp])) keep |= 1u << c;
+    }
+    uint8_t* row = g.grid + (g.o[0] + qx0) + (int64_t)g.g[0] * (g.o[1] + qy);
+    if (aligned && keep == 0) {
+      *reinterpret_cast<uint32_t*>(row) = *reinterpret_cast<const uint32_t*>(pat + qx0 + T * qy);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (!((keep >> c) & 1u)) row[c] = pat[qx0 + c + T * qy];
+    }
   }
 }
 
