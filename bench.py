@@ -87,6 +87,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-parallel", action="store_true",
+                    help="skip the realization-parallel oracle run on all host cores")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP32 FMA lanes, 1 FP16 tensor cores, 2 BF16 tensor cores "
@@ -194,6 +196,56 @@ def oracle_sample(w, target_s, r=0):
     o.simulate(w["grid"], w["T"], w["O"], max_patches=n, **kw)
     dt = time.perf_counter() - t0
     return n, dt, n * o.num_candidates(w["T"])
+
+
+_barrier = None
+
+
+def _oracle_worker_init(barrier):
+    global _barrier
+    _barrier = barrier
+
+
+def _oracle_worker(job):
+    """One realization's first n patches on the oracle, in a worker process:
+    the TI is prepared first, then every worker starts the clock together
+    (a barrier) and returns its (start, end) on the host's monotonic clock."""
+    try:
+        from oracle import oracle as O
+        w, r, n = job
+        o = O.OracleTI(w["ti"], w["F"], w["J"])
+        hd = w["hd"]
+        kw = dict(K=w["K"], hd_cells=None if hd is None else hd[0],
+                  hd_vals=None if hd is None else hd[1], seed=w["seed"], r=r, want_log=False)
+    except BaseException:
+        _barrier.abort()   # release the other workers at once
+        raise
+    _barrier.wait(timeout=120)
+    t0 = time.monotonic()
+    o.simulate(w["grid"], w["T"], w["O"], max_patches=n, **kw)
+    return t0, time.monotonic()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(w, n, procs):
+    """The oracle realization-parallel over `procs` host cores: one process
+    per realization (0 .. procs-1), each running the first n patches of its
+    raster path. Returns the wall seconds from the first start to the last
+    end (TI preparation and process start-up excluded)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")   # no fork after CUDA is initialised
+    keys = ("ti", "F", "J", "grid", "T", "O", "K", "hd", "seed")
+    wj = {k: w[k] for k in keys}
+    barrier = ctx.Barrier(procs)
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(barrier,)) as pool:
+        spans = pool.map(_oracle_worker, [(wj, r, n) for r in range(procs)], chunksize=1)
+    return max(e for _, e in spans) - min(s0 for s0, _ in spans)
 
 
 # ------------------------------------------------------------- clocks -----
@@ -565,7 +617,7 @@ def run_ours(args, rank, world, local_rank):
         T=w["T"], Tj=w["T"] // (2 ** w["J"]), F=w["F"],
         wavefronts=max(wavefronts_of(gr["grid"], w["T"], w["O"]) for gr in groups),
         has_hd=any(gr["hd_host"] is not None for gr in groups)))
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         w0 = dict(w, grid=groups[0]["grid"], hd=groups[0]["hd_host"])
         n, dt, ce = oracle_sample(w0, args.cpu_seconds)
         grid = groups[0]["grid"]
@@ -575,6 +627,17 @@ def run_ours(args, rank, world, local_rank):
                                 "sample": f"first {n} of {n_tot} patches of one realization, "
                                           f"{dt:.1f} s, single thread",
                                 "cand_evals_per_s": ce / dt}
+        if not args.no_cpu_parallel:
+            procs = host_cores()
+            try:
+                wall = oracle_parallel(w0, n, procs)
+                line["cpu_baseline"]["parallel"] = {
+                    "value": procs * n * cells_of(grid) / n_tot / wall, "unit": "cells/s",
+                    "cores": procs, "kind": "oracle",
+                    "sample": f"first {n} of {n_tot} patches of realizations 0..{procs - 1}, "
+                              f"one process per host core, {wall:.1f} s wall"}
+            except Exception as e:   # the single-thread figure above stands
+                line["cpu_baseline"]["parallel"] = {"unavailable": f"{type(e).__name__}: {e}"}
     print(json.dumps(line), flush=True)
 
 

@@ -54,3 +54,14 @@ def test_reference_arm_prints_a_complete_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_realization_parallel_oracle_baseline():
+    """The all-cores oracle figure: one spawned process per realization, the
+    clock started together after every worker has prepared its TI."""
+    from workloads import synth
+    ti = synth.ribbon_ti(120, 120, n_ribbons=6, seed=4, target=0.3, tol=0.2)
+    w = dict(ti=ti, F=2, J=1, grid=(100, 90), T=16, O=4, K=3, hd=None, seed=3)
+    wall = bench.oracle_parallel(w, 12, 2)
+    assert 0.0 < wall < 60.0
+    assert bench.host_cores() >= 1
