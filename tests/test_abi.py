@@ -64,3 +64,31 @@ def test_validation_errors_without_gpu(lib):
     # NULL handles
     assert lib.ccw_simulate(None, None, None, None, 0, C.c_uint64(0), None, None, None) == -1
     assert lib.ccw_ti_free(None) is None or True
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    that a C compiler gives the header's structs (gcc on this host)."""
+    import subprocess
+    from paper_2404_00441_gb300 import ccw as binding
+    pairs = [("ccw_params", binding._Params), ("ccw_group", binding._Group),
+             ("ccw_ti_desc", binding._Desc)]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ccw.h"', 'int main(void) {']
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                           str(exe)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
