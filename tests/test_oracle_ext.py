@@ -266,3 +266,21 @@ def test_virtual_template_improves_conditioning():
                 total += int(np.sum(nb != hd[y, x]))
         return total
     assert conflicts(4) < conflicts(0)
+
+
+def test_boundary_cut_keeps_channels_connected():
+    """The purpose of the quilting cut: seams between patches break fewer
+    channels, so the E-W probability of connection (Sec. 5.3) of the
+    ribbon workload's channels at long lags is higher than with the full
+    paste (4 realizations of the 250 x 250 workload, T 40, OR 10, J 1, K 3)."""
+    from workloads import configs, stats
+    w = configs.workload("c1")
+    t = O.OracleTI(w["ti"], w["F"], w["J"])
+
+    def conn(cut):
+        reals = [t.simulate(w["grid"], w["T"], w["O"], K=3, seed=21, r=r, cut=cut,
+                            want_log=False)[0] for r in range(4)]
+        return np.nanmean([stats.connection_probability(x, 1, (64, 128), axis=1)
+                           for x in reals], 0)
+    plain, cut = conn(0), conn(1)
+    assert np.all(cut > plain)
