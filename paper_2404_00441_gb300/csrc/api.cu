@@ -1366,7 +1366,9 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if (status & kStatusBadCode)
     return fail(CCW_EINVAL, "hard data out of the grid or with a code >= n_facies");
   if (status & kStatusHdOverflow)
-    return fail(CCW_EINVAL, "more than %d hard data in one template window", kMaxHd);
+    return fail(CCW_EINVAL,
+                "more than %d hard data in one template window (virtual template included)",
+                kMaxHd);
   if (status & kStatusTimeout) return fail(CCW_ETIMEOUT, "a bounded device wait gave up");
   return CCW_OK;
 }
