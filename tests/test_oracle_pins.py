@@ -392,3 +392,47 @@ def test_hard_data_are_honoured_in_realizations():
     assert np.array_equal(out[cells[:, 1], cells[:, 0]], vals)
     assert np.all(out < 3)
     assert np.all(log[:, 3] & 2)
+
+
+@pytest.mark.parametrize("path_random", [0, 1])
+def test_first_patch_core_is_a_ti_crop_3d(path_random):
+    """The 3D form of the first-patch pin: a uniform TI patch pasted,
+    unmirrored, at the path's origin corner; the part no later patch
+    overlaps ([0, T - OR) along each forward axis, [OR, T) along a mirrored
+    one) survives in the realization."""
+    ti = synth.tube_lobe_ti_3d(48, 40, 36, seed=5)
+    T, Ov, J = 8, 2, 1
+    t = O.OracleTI(ti, 4, J)
+    grid = (20, 14, 14)                  # T + k (T - OR) on every axis: no padding
+    seed = 77
+    seen = set()
+    for r in range(8):
+        out, log = t.simulate(grid, T, Ov, K=3, path_random=path_random, seed=seed, r=r)
+        assert log[0, 3] & 1
+        pat = t.reconstruct(T, int(log[0, 0]))          # [qz, qy, qx]
+        flips = O.path_flips(3, seed, r, path_random)
+        seen.add(flips)
+        rq, org = [], []
+        for a in range(3):
+            if (flips >> a) & 1:
+                rq.append(np.arange(Ov, T))
+                org.append(grid[a] - T)
+            else:
+                rq.append(np.arange(0, T - Ov))
+                org.append(0)
+        qz, qy, qx = np.meshgrid(rq[2], rq[1], rq[0], indexing="ij")
+        got = out[qz + org[2], qy + org[1], qx + org[0]]
+        assert np.array_equal(got, pat[qz, qy, qx])
+    assert (len(seen) > 1) == bool(path_random)
+
+
+def test_hard_data_are_honoured_in_3d_realizations():
+    """Sec. 5.2 in 3D: every hard datum is reproduced."""
+    ti = synth.tube_lobe_ti_3d(48, 40, 36, seed=5)
+    field = synth.tube_lobe_ti_3d(26, 22, 18, seed=6)
+    cells, vals = synth.sample_hard_data(field, 80, seed=7)
+    t = O.OracleTI(ti, 4, 1)
+    out, log = t.simulate((26, 22, 18), 8, 2, K=4, hd_cells=cells, hd_vals=vals, seed=3,
+                          path_random=1)
+    assert np.array_equal(out[cells[:, 2], cells[:, 1], cells[:, 0]], vals)
+    assert np.all(out < 4) and np.all(log[:, 3] & 2)
