@@ -34,6 +34,12 @@
  *     but outside the template add to the mismatch count, a datum whose TI
  *     position falls outside the TI counting as a mismatch. The score and
  *     the empty-event rule use the template alone.
+ *   - All-shift (polyphase) candidates, an option: every fine origin c of
+ *     the cropped TI with c + T <= n on every axis instead of the multiples
+ *     of s (decimation keeps one position in s^d per level, Sec. 3.2); the
+ *     level-J approximation of the window at c is its s^d block sums, the
+ *     ranking index is c's raster index over the fine candidate grid and the
+ *     pasted pattern is the TI crop at c.
  *   - Minimum-error boundary cut (the image-quilting paste of Sec. 2, 2D):
  *     in the path frame, a vertical cut through the left overlap strip and
  *     a horizontal one through the top strip, each the cheapest 8-connected
@@ -618,6 +624,152 @@ int orc_search_virtual(const orc_ti* t, int T, const uint8_t* de, const uint8_t*
                      topk_idx, topk_score, topk_mis, pick_out);
 }
 
+/* All-shift candidates (the polyphase reading in the header): the search of
+ * search_core over every fine origin c = (cx, cy, cz) of the cropped TI with
+ * c + T <= n. The approximation of the TI window at c is computed from its
+ * definition, the s^d block sums of the indicator (one-hot) or of the codes
+ * (literal) starting at c + s u. */
+static int allshift_core(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd,
+                         const int32_t* vhd, int n_vhd, int K, int score_mode, uint64_t seed,
+                         uint32_t r, uint32_t p, int64_t* scores, int32_t* mis,
+                         int32_t* topk_idx, int64_t* topk_score, int32_t* topk_mis,
+                         int32_t* pick_out) {
+  const int d = t->ndim, s = t->s, J = t->J, F = t->F;
+  if (T <= 0 || T % s != 0 || K < 1 || (score_mode != 0 && score_mode != 1)) return ORC_EINVAL;
+  int32_t fd[3];
+  for (int a = 0; a < 3; ++a) {
+    fd[a] = (a < d) ? t->n[a] - T + 1 : 1;
+    if (fd[a] <= 0) return ORC_EINVAL;
+  }
+  const int tj = T / s;
+  const int32_t tw[3] = {T, d > 1 ? T : 1, d > 2 ? T : 1};
+  const int32_t tc[3] = {tj, d > 1 ? tj : 1, d > 2 ? tj : 1};
+  const int32_t sb[3] = {s, d > 1 ? s : 1, d > 2 ? s : 1};
+  const int64_t tv = vol32(tw), tcv = vol32(tc), P = vol32(fd);
+  int64_t known = 0;
+  for (int64_t q = 0; q < tv; ++q) {
+    if (de[q] != UNKNOWN && de[q] >= F) return ORC_EINVAL;
+    if (de[q] != UNKNOWN) ++known;
+  }
+  uint32_t u = draw_u32(seed, r, p, 0u);
+  if (known == 0) {
+    *pick_out = (int32_t)scale_u32(u, P);
+    if (scores)
+      for (int64_t c = 0; c < P; ++c) scores[c] = 0;
+    if (mis)
+      for (int64_t c = 0; c < P; ++c) mis[c] = 0;
+    return 0;
+  }
+  int nch = (score_mode == 0) ? F : 1;
+  int64_t* img = (int64_t*)malloc(sizeof(int64_t) * tv);
+  int64_t* pyr = (int64_t*)malloc(sizeof(int64_t) * tv);
+  int64_t* cor = (int64_t*)malloc(sizeof(int64_t) * tcv * nch);
+  orc_cand* best = (orc_cand*)malloc(sizeof(orc_cand) * K);
+  if (!img || !pyr || !cor || !best) {
+    free(img); free(pyr); free(cor); free(best);
+    return ORC_ENOMEM;
+  }
+  /* the data event's level-J approximation, as in search_core */
+  int64_t aoff = pyr_approx_offset(d, (int64_t[3]){tw[0], tw[1], tw[2]}, J);
+  for (int ch = 0; ch < nch; ++ch) {
+    for (int64_t q = 0; q < tv; ++q) {
+      if (de[q] == UNKNOWN) img[q] = 0;
+      else img[q] = (score_mode == 0) ? (de[q] == ch ? 1 : 0) : (int64_t)de[q];
+    }
+    orc_dwt(img, d, tw, J, pyr);
+    memcpy(cor + ch * tcv, pyr + aoff, sizeof(int64_t) * tcv);
+  }
+  int nbest = 0;
+  const int kk = (int)((K < P) ? K : P);
+  for (int32_t cz = 0; cz < fd[2]; ++cz)
+    for (int32_t cy = 0; cy < fd[1]; ++cy)
+      for (int32_t cx = 0; cx < fd[0]; ++cx) {
+        const int64_t c = cx + (int64_t)fd[0] * (cy + (int64_t)fd[1] * cz);
+        int64_t sc = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+          const int64_t* w = cor + ch * tcv;
+          for (int32_t uz = 0; uz < tc[2]; ++uz)
+            for (int32_t uy = 0; uy < tc[1]; ++uy)
+              for (int32_t ux = 0; ux < tc[0]; ++ux) {
+                const int64_t wv = w[ux + (int64_t)tc[0] * (uy + (int64_t)tc[1] * uz)];
+                if (wv == 0) continue;
+                int64_t a = 0;   /* block sum of the TI window at c, block u */
+                for (int32_t bz = 0; bz < sb[2]; ++bz)
+                  for (int32_t by = 0; by < sb[1]; ++by)
+                    for (int32_t bx = 0; bx < sb[0]; ++bx) {
+                      const int64_t fx = cx + (int64_t)s * ux + bx;
+                      const int64_t fy = cy + (int64_t)sb[1] * uy + by;
+                      const int64_t fz = cz + (int64_t)sb[2] * uz + bz;
+                      const uint8_t v = t->ti[fx + (int64_t)t->n[0] * (fy + (int64_t)t->n[1] * fz)];
+                      a += (score_mode == 0) ? (v == ch) : v;
+                    }
+                sc += wv * a;
+              }
+        }
+        int32_t mm = 0;
+        if (hd)
+          for (int32_t qz = 0; qz < tw[2]; ++qz)
+            for (int32_t qy = 0; qy < tw[1]; ++qy)
+              for (int32_t qx = 0; qx < tw[0]; ++qx) {
+                const uint8_t h = hd[qx + (int64_t)tw[0] * (qy + (int64_t)tw[1] * qz)];
+                if (h == UNKNOWN) continue;
+                if (t->ti[(cx + qx) + (int64_t)t->n[0] * ((cy + qy) + (int64_t)t->n[1] * (cz + qz))] != h)
+                  ++mm;
+              }
+        for (int v = 0; v < n_vhd; ++v) {
+          const int32_t* e = vhd + 4 * v;
+          const int64_t fx = (int64_t)cx + e[0], fy = (int64_t)cy + e[1], fz = (int64_t)cz + e[2];
+          if (fx < 0 || fy < 0 || fz < 0 || fx >= t->n[0] || fy >= t->n[1] || fz >= t->n[2] ||
+              t->ti[fx + (int64_t)t->n[0] * (fy + (int64_t)t->n[1] * fz)] != (uint8_t)e[3])
+            ++mm;
+        }
+        if (scores) scores[c] = sc;
+        if (mis) mis[c] = mm;
+        orc_cand e = {mm, sc, (int32_t)c};
+        if (nbest < kk || cand_before(&e, &best[nbest - 1])) {
+          int pos = (nbest < kk) ? nbest : kk - 1;
+          while (pos > 0 && cand_before(&e, &best[pos - 1])) {
+            best[pos] = best[pos - 1];
+            --pos;
+          }
+          best[pos] = e;
+          if (nbest < kk) ++nbest;
+        }
+      }
+  for (int i = 0; i < nbest; ++i) {
+    topk_idx[i] = best[i].idx;
+    topk_score[i] = best[i].score;
+    topk_mis[i] = best[i].mis;
+  }
+  *pick_out = best[scale_u32(u, nbest)].idx;
+  free(img); free(pyr); free(cor); free(best);
+  return nbest;
+}
+
+/* Number of all-shift candidates of a template of edge T, or -1. */
+int64_t orc_num_candidates_allshift(const orc_ti* t, int T) {
+  if (T <= 0 || T % t->s != 0) return -1;
+  int64_t P = 1;
+  for (int a = 0; a < t->ndim; ++a) {
+    if (t->n[a] - T + 1 <= 0) return -1;
+    P *= t->n[a] - T + 1;
+  }
+  return P;
+}
+
+/* orc_search_virtual over the all-shift candidates (vhd may be NULL). */
+int orc_search_allshift(const orc_ti* t, int T, const uint8_t* de, const uint8_t* hd,
+                        const int32_t* vhd, int n_vhd, int K, int score_mode, uint64_t seed,
+                        uint32_t r, uint32_t p, int64_t* scores, int32_t* mis,
+                        int32_t* topk_idx, int64_t* topk_score, int32_t* topk_mis,
+                        int32_t* pick_out) {
+  if (n_vhd < 0 || (n_vhd > 0 && !vhd)) return ORC_EINVAL;
+  for (int v = 0; v < n_vhd; ++v)
+    if (vhd[4 * v + 3] < 0 || vhd[4 * v + 3] >= t->F) return ORC_EINVAL;
+  return allshift_core(t, T, de, hd, vhd, n_vhd, K, score_mode, seed, r, p, scores, mis,
+                       topk_idx, topk_score, topk_mis, pick_out);
+}
+
 /* Minimum-error boundary cut of image quilting (Efros and Freeman, the IQ
  * method of Sec. 2) through an overlap strip of `rows` x `cols` cells with
  * 0/1 costs err[y * cols + x]: the cumulative cost
@@ -743,16 +895,20 @@ uint32_t orc_path_flips(int ndim, uint64_t seed, uint32_t r, int path_random) {
  * with flags bit0 = uniform pick (empty data event), bit1 = patch done, and
  * unused topk slots = -1. Stops after max_patches patches when >= 0.
  * vt_ext (0..T) grows the virtual template of the non-causal conditioning;
- * cut = 1 pastes through the minimum-error boundary cuts (2D only). Both
- * follow the readings in the header; orc_simulate is vt_ext = cut = 0.
+ * cut = 1 pastes through the minimum-error boundary cuts (2D only);
+ * all_shift = 1 searches the all-shift candidates (pick and log indices are
+ * then fine-grid indices). All follow the readings in the header;
+ * orc_simulate is vt_ext = cut = all_shift = 0.
  */
 int orc_simulate_ext(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
-                     int score_mode, int path_random, int vt_ext, int cut, int n_hd,
-                     const int32_t* hd_cells, const uint8_t* hd_vals, uint64_t seed, uint32_t r,
-                     int64_t max_patches, uint8_t* out, int32_t* log) {
+                     int score_mode, int path_random, int vt_ext, int cut, int all_shift,
+                     int n_hd, const int32_t* hd_cells, const uint8_t* hd_vals, uint64_t seed,
+                     uint32_t r, int64_t max_patches, uint8_t* out, int32_t* log) {
   const int d = t->ndim;
   if (T % t->s != 0 || O % t->s != 0 || O < 0 || T < 2 * O || K < 1) return ORC_EINVAL;
   if (vt_ext < 0 || vt_ext > T || (cut != 0 && cut != 1) || (cut && d != 2)) return ORC_EINVAL;
+  if (all_shift != 0 && all_shift != 1) return ORC_EINVAL;
+  if (all_shift && orc_num_candidates_allshift(t, T) < 0) return ORC_EINVAL;
   int32_t np[3], gp[3], cd[3];
   if (orc_lattice(d, grid, T, O, np, gp) != ORC_OK) return ORC_EINVAL;
   if (cand_dims(t, T, cd) != ORC_OK) return ORC_EINVAL;
@@ -855,15 +1011,29 @@ int orc_simulate_ext(const orc_ti* t, const int32_t grid[3], int T, int O, int K
           ++n_vhd;
         }
     int32_t pick = -1;
-    int nk = search_core(t, T, de, hw, vhd, n_vhd, K, score_mode, seed, r, (uint32_t)p, scores,
-                         mism, ti_idx, ti_sc, ti_mm, &pick);
+    int nk = all_shift
+                 ? allshift_core(t, T, de, hw, vhd, n_vhd, K, score_mode, seed, r, (uint32_t)p,
+                                 scores, mism, ti_idx, ti_sc, ti_mm, &pick)
+                 : search_core(t, T, de, hw, vhd, n_vhd, K, score_mode, seed, r, (uint32_t)p,
+                               scores, mism, ti_idx, ti_sc, ti_mm, &pick);
     if (nk < 0) {
       rc = nk;
       goto done;
     }
-    /* Algorithm 1, lines 13-14: reconstruct and paste; hard data stay */
-    rc = orc_reconstruct(t, T, pick, pat);
-    if (rc != ORC_OK) goto done;
+    /* Algorithm 1, lines 13-14: reconstruct and paste; hard data stay. An
+     * all-shift candidate's pattern is the TI crop at its fine origin. */
+    if (all_shift) {
+      const int32_t fd0 = t->n[0] - T + 1, fd1 = d > 1 ? t->n[1] - T + 1 : 1;
+      const int32_t c3[3] = {pick % fd0, (pick / fd0) % fd1, pick / (fd0 * fd1)};
+      for (int32_t qz = 0; qz < tw[2]; ++qz)
+        for (int32_t qy = 0; qy < tw[1]; ++qy)
+          for (int32_t qx = 0; qx < tw[0]; ++qx)
+            pat[qx + (int64_t)tw[0] * (qy + (int64_t)tw[1] * qz)] =
+                t->ti[(c3[0] + qx) + (int64_t)t->n[0] * ((c3[1] + qy) + (int64_t)t->n[1] * (c3[2] + qz))];
+    } else {
+      rc = orc_reconstruct(t, T, pick, pat);
+      if (rc != ORC_OK) goto done;
+    }
     if (cut && O > 0) {
       /* boundary cuts in the path frame: column cut through the left strip
        * (rows y', columns x' < O), row cut through the top strip (rows x',
@@ -934,6 +1104,6 @@ int orc_simulate(const orc_ti* t, const int32_t grid[3], int T, int O, int K,
                  int score_mode, int path_random, int n_hd, const int32_t* hd_cells,
                  const uint8_t* hd_vals, uint64_t seed, uint32_t r, int64_t max_patches,
                  uint8_t* out, int32_t* log) {
-  return orc_simulate_ext(t, grid, T, O, K, score_mode, path_random, 0, 0, n_hd, hd_cells,
+  return orc_simulate_ext(t, grid, T, O, K, score_mode, path_random, 0, 0, 0, n_hd, hd_cells,
                           hd_vals, seed, r, max_patches, out, log);
 }

@@ -63,7 +63,12 @@ def _load():
     lib.orc_simulate.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.c_int, P, P, u64, u32, i64, P, P]
     lib.orc_simulate_ext.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                     C.c_int, C.c_int, C.c_int, P, P, u64, u32, i64, P, P]
+                                     C.c_int, C.c_int, C.c_int, C.c_int, P, P, u64, u32, i64, P,
+                                     P]
+    lib.orc_search_allshift.argtypes = [P, C.c_int, P, P, P, C.c_int, C.c_int, C.c_int, u64,
+                                        u32, u32, P, P, P, P, P, P]
+    lib.orc_num_candidates_allshift.argtypes = [P, C.c_int]
+    lib.orc_num_candidates_allshift.restype = i64
     lib.orc_search_virtual.argtypes = [P, C.c_int, P, P, P, C.c_int, C.c_int, C.c_int, u64,
                                        u32, u32, P, P, P, P, P, P]
     lib.orc_min_cut.argtypes = [P, C.c_int, C.c_int, P]
@@ -186,24 +191,34 @@ class OracleTI:
         return tuple(n - tj + 1 for n in self.cshape)
 
     def search(self, T, de, hd=None, K=1, score_mode=0, seed=0, r=0, p=0, maps=False,
-               vhd=None):
+               vhd=None, all_shift=False):
         """Best-match search for one data event (numpy [T]*d u8, 255 = unknown).
         vhd: hard data of a virtual template, int [n][4] rows (qx, qy, qz, code)
-        of fine offsets from the window origin (any sign).
+        of fine offsets from the window origin (any sign). all_shift: every
+        fine origin is a candidate (indices over the fine candidate grid).
         Returns dict(topk_idx, topk_score, topk_mis, pick[, scores, mis])."""
         de = np.ascontiguousarray(de, dtype=np.uint8)
         hdp = None
         if hd is not None:
             hd = np.ascontiguousarray(hd, dtype=np.uint8)
             hdp = _p(hd)
-        P = self.num_candidates(T)
+        P = (int(self._lib.orc_num_candidates_allshift(self.h, T)) if all_shift
+             else self.num_candidates(T))
         sc = np.zeros(P, dtype=np.int64) if maps else None
         mm = np.zeros(P, dtype=np.int32) if maps else None
         ti_idx = np.full(K, -1, dtype=np.int32)
         ti_sc = np.zeros(K, dtype=np.int64)
         ti_mm = np.zeros(K, dtype=np.int32)
         pick = np.zeros(1, dtype=np.int32)
-        if vhd is None:
+        if all_shift:
+            v = np.ascontiguousarray(np.asarray([] if vhd is None else vhd,
+                                                dtype=np.int32).reshape(-1, 4))
+            nk = self._lib.orc_search_allshift(self.h, T, _p(de), hdp, _p(v) if len(v) else None,
+                                               len(v), K, score_mode, seed, r, p,
+                                               _p(sc) if maps else None,
+                                               _p(mm) if maps else None, _p(ti_idx), _p(ti_sc),
+                                               _p(ti_mm), _p(pick))
+        elif vhd is None:
             nk = self._lib.orc_search(self.h, T, _p(de), hdp, K, score_mode, seed, r, p,
                                       _p(sc) if maps else None, _p(mm) if maps else None,
                                       _p(ti_idx), _p(ti_sc), _p(ti_mm), _p(pick))
@@ -231,10 +246,12 @@ class OracleTI:
         return pat.reshape((T,) * self.ndim)
 
     def simulate(self, grid, T, O, K=1, score_mode=0, path_random=0, hd_cells=None,
-                 hd_vals=None, seed=0, r=0, max_patches=-1, want_log=True, vt_ext=0, cut=0):
+                 hd_vals=None, seed=0, r=0, max_patches=-1, want_log=True, vt_ext=0, cut=0,
+                 all_shift=0):
         """One realization along the raster path (Algorithm 1). grid = (nx, ny[, nz]).
         vt_ext grows the virtual template of the non-causal conditioning; cut = 1
-        pastes through the minimum-error boundary cuts (2D).
+        pastes through the minimum-error boundary cuts (2D); all_shift = 1
+        searches every fine origin of the TI (log indices over the fine grid).
         Returns (realization numpy array, patch log [n_patches, 4+K] or None)."""
         g = _dims3(grid)
         npch, gp = lattice(self.ndim, grid, T, O)
@@ -248,7 +265,8 @@ class OracleTI:
             hv = np.ascontiguousarray(hd_vals, dtype=np.uint8)
             n_hd = len(hv)
         rc = self._lib.orc_simulate_ext(self.h, _p(g), T, O, K, score_mode, path_random,
-                                        vt_ext, cut, n_hd, _p(hc) if n_hd else None,
+                                        vt_ext, cut, all_shift, n_hd,
+                                        _p(hc) if n_hd else None,
                                         _p(hv) if n_hd else None, seed, r, max_patches,
                                         _p(out), _p(log) if want_log else None)
         if rc != 0:
