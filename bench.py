@@ -93,8 +93,11 @@ def parse_args():
     ap.add_argument("--precision", type=int, default=None,
                     help="0 FP32 FMA lanes, 1 FP16 tensor cores, 2 BF16 tensor cores "
                          "(default: 1 for 2D workloads, 0 for 3D)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the CCF tiling by timing every accepted one (outside the timed "
+                         "region) instead of the committed per-workload table")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="skip the CCF tiling autotuner (library heuristic, --precision or 1/0)")
+                    help="the library's own tiling heuristic (ccf_tile 0)")
     ap.add_argument("--ccf-tile", type=lambda v: int(v, 0), default=None,
                     help="force this ccw_params.ccf_tile (implies --no-autotune)")
     ap.add_argument("--vt-ext", type=int, default=0,
@@ -515,7 +518,8 @@ def run_ours(args, rank, world, local_rank):
             hd_vals=None if hd is None else torch.from_numpy(hd[1]).cuda(),
             hd_host=hd))
     ndim = len(groups[0]["grid"])
-    precision = args.precision if args.precision is not None else 1
+    bench_prec, bench_tile = configs.bench_tile(args.workload)
+    precision = args.precision if args.precision is not None else bench_prec
     cells_per_step = sum(gr["n_real"] * cells_of(gr["grid"]) for gr in groups)
     learned_info = None
     if args.learned:
@@ -525,7 +529,15 @@ def run_ours(args, rank, world, local_rank):
     tile, tune_info = 0, None
     if args.ccf_tile is not None:
         tile = args.ccf_tile
-    elif not args.no_autotune:
+    elif args.no_autotune:
+        tile = 0
+    elif not args.autotune:
+        # the committed table (what the parity tests run)
+        tile = bench_tile if precision == bench_prec else 0
+        tune_info = {"chosen": f"p{precision}/{tile:#x}",
+                     "source": "committed per-workload table (workloads/configs.py BENCH_TILE), "
+                               "parity-tested at full size"}
+    else:
         from paper_2404_00441_gb300 import autotune
         precs = ((precision,) if args.precision is not None
                  else (0, 1, 2))

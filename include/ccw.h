@@ -277,7 +277,9 @@ int ccw_ccf_search(const ccw_ti* ti, int32_t B, const uint8_t* de_dev, const uin
  *    ordering between them) race on the array and give wrong results:
  *    order them on one stream.
  * The paper has no counterpart of this entry point; it only changes where
- * the scratch memory comes from. Asynchronous. Errors: CCW_EINVAL (as
+ * the scratch memory comes from. Its launches are never timed or counted by
+ * the profiler (ccw_profile_enable), whose events and counters would need
+ * allocations. Asynchronous. Errors: CCW_EINVAL (as
  * ccw_ccf_search, or the batch needs more scratch than the array holds),
  * CCW_ECUDA.
  */
@@ -443,6 +445,23 @@ const char* ccw_eval_last_error(void);
 
 /* ccw_last_error -- text of the last failure on the calling host thread. */
 const char* ccw_last_error(void);
+
+/*
+ * The random-number generator of every draw above (Algorithm 1: the random
+ * pattern of an empty data event, line 6; the draw among the K best, line
+ * 12; the path mirroring, line 3): Philox4x32-10 (Salmon et al., SC'11),
+ * compiled from the same source as the kernels' own. With it a caller can
+ * reproduce a draw: the draw of patch p of realization r under `seed` is
+ * word 0 of counter (r, p, 0, 0) with key (seed low word, seed high word).
+ *  ctr  uint32 [n][4] counters; out uint32 [n][4] output blocks; key [2].
+ * ccw_philox_host -- host arrays, computed on the calling thread.
+ * ccw_philox_dev  -- device arrays (16-byte aligned), asynchronous on
+ *                    `stream`; key is a host array.
+ * Errors: CCW_EINVAL (n < 0, NULL or misaligned arrays), CCW_ECUDA.
+ */
+int ccw_philox_host(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out);
+int ccw_philox_dev(int64_t n, const uint32_t* ctr_dev, const uint32_t key[2], uint32_t* out_dev,
+                   void* stream);
 
 /*
  * Profiling. When enabled, every launch of the search kernel is bracketed by

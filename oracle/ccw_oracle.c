@@ -91,6 +91,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
   out[3] = c3;
 }
 
+/* n blocks of Philox4x32-10 under one key: ctr and out are [n][4]. */
+void orc_philox_many(int64_t n, const uint32_t* ctr, const uint32_t key[2], uint32_t* out) {
+  for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 static uint32_t draw_u32(uint64_t seed, uint32_t a, uint32_t b, uint32_t purpose) {
   uint32_t ctr[4] = {a, b, purpose, 0u};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

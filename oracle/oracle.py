@@ -44,6 +44,7 @@ def _load():
     P = C.c_void_p
     i32, i64, u32, u64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64
     lib.orc_philox4x32_10.argtypes = [P, P, P]
+    lib.orc_philox_many.argtypes = [C.c_int64, P, P, P]
     lib.orc_dwt.argtypes = [P, C.c_int, P, C.c_int, P]
     lib.orc_idwt.argtypes = [P, C.c_int, P, C.c_int, P]
     lib.orc_dwt_orth.argtypes = [P, C.c_int, P, C.c_int, P]
@@ -92,6 +93,15 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     k = np.asarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     _load().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox_many(ctr, key) -> np.ndarray:
+    """Philox4x32-10 blocks of the counters ctr [n, 4] under one key: [n, 4]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    _load().orc_philox_many(c.shape[0], _p(c), _p(k), _p(out))
     return out
 
 

@@ -95,6 +95,8 @@ def load():
     lib.ccw_proposal_query.argtypes = [P, P, i32, P, P, P, P]
     lib.ccw_proposal_inputs.argtypes = [P, i32, P, P, P, i32, P, P]
     lib.ccw_proposal_stats.argtypes = [P, C.POINTER(i64), P]
+    lib.ccw_philox_host.argtypes = [i64, P, P, P]
+    lib.ccw_philox_dev.argtypes = [i64, P, P, P, P]
     _lib = lib
     return lib
 
@@ -384,6 +386,32 @@ def profile_read_phases():
     v = (C.c_double * 3)()
     _check(load().ccw_profile_read_phases(v))
     return tuple(float(x) for x in v)
+
+
+def philox_host(ctr, key):
+    """``ccw_philox_host``: Philox4x32-10 blocks of the counters ``ctr``
+    (uint32 array [n, 4]) under ``key`` (2 words), computed on the host by the
+    library's own generator; returns a uint32 array [n, 4]."""
+    import numpy as np
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty_like(c)
+    _check(load().ccw_philox_host(c.shape[0], c.ctypes.data_as(C.c_void_p),
+                                  k.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def philox_dev(ctr: torch.Tensor, key, stream=None) -> torch.Tensor:
+    """``ccw_philox_dev``: the same blocks computed on the GPU; ``ctr`` is a
+    CUDA int32/uint32-valued tensor [n, 4] (int32 storage), returns [n, 4]."""
+    import numpy as np
+    if ctr.dim() != 2 or ctr.shape[1] != 4 or ctr.dtype != torch.int32:
+        raise ValueError("ctr must be an int32 CUDA tensor [n, 4]")
+    out = torch.empty_like(ctr)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    _check(load().ccw_philox_dev(ctr.shape[0], _ptr(ctr), k.ctypes.data_as(C.c_void_p),
+                                 _ptr(out), _stream(stream)))
+    return out
 
 
 def launch_count() -> int:

@@ -467,12 +467,15 @@ cudaError_t launch_ccf(const ccw_ti* t, int mode, const CcfPlan& cp, const WaveA
 
 // Phases A, B (and C when searching) on explicit data events, in chunks of
 // at most 65535 items. Scratch comes from the caller (sizes from plan_ccf).
+// `profiled` = false keeps the launches out of the profiler, whose counters
+// and per-launch events would otherwise be allocated here.
 int run_explicit(const ccw_ti* t, int mode, WaveArgs a, int B, const CcfPlan& cp,
-                 unsigned char* ev_base, unsigned long long* part, void* bmat, cudaStream_t st) {
+                 unsigned char* ev_base, unsigned long long* part, void* bmat, cudaStream_t st,
+                 bool profiled = true) {
   const int64_t tv = ipow(t->T, t->ndim);
   unsigned long long* work = nullptr;
-  bool prof;
-  {
+  bool prof = false;
+  if (profiled) {
     std::lock_guard<std::mutex> g(g_prof.mu);
     prof = g_prof.enabled;
     if (prof) work = profiling_counters();
@@ -977,8 +980,10 @@ int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
   a.pick = pick_dev;
   // event records, ranking keys, weight matrix; every slot read is written
   // first in the same call, so nothing needs clearing
+  // never profiled: the profiler's counters and timing events are allocated
   return run_explicit(t, kModeSearch, a, B, cp, b, (unsigned long long*)(b + part_off),
-                      cp.bmat_bytes ? b + bmat_off : nullptr, (cudaStream_t)stream);
+                      cp.bmat_bytes ? b + bmat_off : nullptr, (cudaStream_t)stream,
+                      /*profiled=*/false);
 }
 
 int ccw_ccf_map(const ccw_ti* t, int32_t B, const uint8_t* de_dev, const uint8_t* hd_dev,

@@ -91,54 +91,6 @@ def test_many_realizations_one_call(ccw):
     run_pair(ccw, ti, 2, 2, 32, 8, (100, 84), 4, n_real=6, real_base=100, seed=21)
 
 
-def test_full_size_c2_sampled(ccw):
-    """The 2000x2000 3-facies workload in the launch configuration the
-    benchmark times. Checked at full size:
-      * every hard datum is honoured;
-      * every cell equals the pattern of the last patch that covers it (the
-        Inverse-DWT paste), unless it holds a hard datum;
-      * for sampled patches, the data event rebuilt by replaying the logged
-        pastes of all earlier patches gives, in the oracle's search, exactly
-        the logged ranking, scores, mismatches and pick."""
-    w = configs.workload("c2")
-    ti, F, J, T, Ov, K, grid = w["ti"], w["F"], w["J"], w["T"], w["O"], w["K"], w["grid"]
-    cells, vals = w["hd"]
-    g = ccw.TI(dev(ti), F, J, T, Ov)
-    out, log = ccw.simulate(g, grid, n_real=1, topk=K, seed=w["seed"], hd_cells=dev(cells),
-                            hd_vals=dev(vals), want_log=True)
-    out, log = out.cpu().numpy()[0], log.cpu().numpy()[0]
-    assert np.array_equal(out[cells[:, 1], cells[:, 0]], vals)
-    o = O.OracleTI(ti, F, J)
-    npch, gp = O.lattice(2, grid, T, Ov)
-    S = T - Ov
-    hd_img = np.full((gp[1], gp[0]), 255, np.uint8)
-    hd_img[cells[:, 1], cells[:, 0]] = vals
-    # replay the pastes in raster order
-    state = np.full((gp[1], gp[0]), 255, np.uint8)
-    rng = np.random.default_rng(0)
-    n_patches = npch[0] * npch[1]
-    sample = set(rng.choice(n_patches, 24, replace=False).tolist()) | {0, 1, npch[0], n_patches - 1}
-    for p in range(n_patches):
-        iy, ix = divmod(p, npch[0])
-        oy, ox = S * iy, S * ix
-        win = (slice(oy, oy + T), slice(ox, ox + T))
-        hw = hd_img[win]
-        if p in sample:
-            de = np.where(hw != 255, hw, state[win])
-            ref = o.search(T, de, hw, K=K, seed=w["seed"], r=0, p=p)
-            e = log[p]
-            assert e[0] == ref["pick"], f"pick of patch {p}"
-            n = ref["n"]
-            if n:
-                assert np.array_equal(e[4:4 + n], ref["topk_idx"]), f"ranking of patch {p}"
-                sel = list(ref["topk_idx"]).index(ref["pick"])
-                assert e[1] == ref["topk_score"][sel] and e[2] == ref["topk_mis"][sel]
-        assert log[p, 3] & 2
-        pat = o.reconstruct(T, int(log[p, 0]))
-        state[win] = np.where(hw != 255, hw, pat)
-    assert np.array_equal(state[:grid[1], :grid[0]], out)
-
-
 @pytest.mark.parametrize("precision", [0, 1])
 def test_mixed_grid_sizes_in_one_batch(ccw, precision):
     """Several grid sizes advance in one batch (ccw_simulate_groups); every

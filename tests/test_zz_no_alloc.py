@@ -91,3 +91,30 @@ def test_noalloc_rejects_batches_beyond_the_scratch_array(env):
                                     _p(outs[1]), _p(outs[2]), _p(pick), None)
     assert rc == -1
     assert b"scratch" in lib.ccw_last_error()
+
+
+def test_noalloc_search_stays_out_of_the_profiler(env):
+    """With profiling on, the search that allocates nothing still gives the
+    search's results and adds no timed launch: the profiler's events and
+    counters would need allocations."""
+    ccw, lib = env
+    rng = np.random.default_rng(5)
+    ti = configs.ribbon_ti_250()
+    F, J, T, Ov, K = 2, 1, 40, 10, 3
+    g = ccw.TI(torch.from_numpy(ti).cuda(), F, J, T, Ov)
+    B = 9
+    de, hd = configs.structured_events(ti, T, Ov, B, rng, n_hd=2, F=F)
+    ctr = torch.from_numpy(np.stack([np.arange(B), np.arange(B) + 3], 1).astype(np.int32)).cuda()
+    de_t, hd_t = torch.from_numpy(de).cuda(), torch.from_numpy(hd).cuda()
+    ref = _call(lib, "ccw_ccf_search", g, de_t, hd_t, K, 17, ctr)
+    ccw.profile_enable(True)
+    try:
+        ccw.profile_read()
+        for _ in range(2):
+            got = _call(lib, "ccw_ccf_search_noalloc", g, de_t, hd_t, K, 17, ctr)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b)
+        launches = ccw.profile_read()[0]
+    finally:
+        ccw.profile_enable(False)
+    assert launches == 0
