@@ -697,8 +697,24 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def rank_command(argv, n):
+    """The torchrun command that runs this benchmark on n local ranks (one per
+    GPU, rendezvous on 127.0.0.1 at a free port) with the same arguments."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={n}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+            os.path.abspath(__file__)] + list(argv)
+
+
 def main():
     args = parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # `--gpus N` without a launcher: start the N ranks here (rank 0 prints
+        # the line; n_gpus is the number of ranks that ran)
+        sys.exit(subprocess.call(rank_command(sys.argv[1:], args.gpus)))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -98,7 +98,12 @@ typedef struct {
                           stages (always so in 3D; K <= 8), bit 26: three
                           stages instead of two, bit 29: four (not with bit
                           26), bits 27-28 = v: stages of Tj / 2^v template
-                          rows (v <= 2). An autotuner
+                          rows (v <= 2). Bit 30 alone among bits 24-31
+                          (2D, K <= 8, no vt_ext, boundary_cut or learned):
+                          every wavefront of the call in one cooperative
+                          kernel, nt in {16, 32, 64, 128, 256} items per
+                          N-tile, mt = 0 picks the M-tiles per CTA so that
+                          every M-group has its own CTA. An autotuner
                           picks it by timing
                           (paper_2404_00441_gb300.autotune). */
   int32_t vt_ext;      /* non-causal conditioning (Sec. 4.4), 0..templ: the
@@ -473,6 +478,12 @@ int ccw_philox_dev(int64_t n, const uint32_t* ctr_dev, const uint32_t key[2], ui
  * in the process.
  */
 int ccw_profile_enable(int32_t enable);
+/* ccw_set_barrier_polls -- how many times a CTA of the one-kernel simulation
+ * (ccw_params.ccf_tile bit 30) polls a grid-wide barrier before it gives up;
+ * the call then returns CCW_ETIMEOUT and leaves the device usable. 0 restores
+ * the default (2^22 polls, seconds). Small values exist to test that error
+ * path; they make calls fail. Applies to calls made after it. */
+int ccw_set_barrier_polls(int64_t polls);
 int ccw_profile_read(int64_t* launches, double* total_ms, double* cand_evals, double* macs);
 /* ccw_profile_read_phases -- summed durations (ms, stream-ordered CUDA events
  * recorded inside the captured simulation graph) of the three phases of

@@ -29,6 +29,11 @@ cudaError_t launch_ccf_tc(int mode, const WaveArgs& a, int smem, bool pdl, cudaS
 // tcs.cu
 int tcs_smem_bytes(int mt, int nt, int R, int px8, int k16n, int stages);
 cudaError_t launch_ccf_tcs(int mode, const WaveArgs& a, int smem, bool pdl, cudaStream_t st);
+// persist.cu
+int persist_smem_bytes(int nch, int a_nq, int mt, int nt, int ksteps, int F, int ncells, int T,
+                       int gw);
+int persist_grid(int smem, bool bf16);
+cudaError_t launch_persist(const WaveArgs& a, int smem, int grid, cudaStream_t st);
 // prepare.cu
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
                       int64_t nq, int nplanes, void* z8_f16, void* z8_bf16, cudaStream_t st);
@@ -85,6 +90,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<uint32_t> g_barrier_polls{1u << 22};   // grid-barrier polls before giving up
 
 int64_t ipow(int64_t b, int e) {
   int64_t r = 1;
@@ -164,6 +170,10 @@ struct SimPlan {
   void* enc_act = nullptr;
   CallDev* call = nullptr;
   SimGroup* dgroups = nullptr;
+  int64_t* wave_off_d = nullptr;            // persistent kernel: wavefront offsets
+  unsigned* gbar = nullptr;                 // persistent kernel: barrier words
+  unsigned long long* phase_ns = nullptr;   // persistent kernel: profiled phase times
+  cudaEvent_t pev[2] = {nullptr, nullptr};  // persistent kernel: profiled launch
   EvDev evl;
   void* cp = nullptr;   // CcfPlan (defined with the kernels' host helpers)
   cudaStream_t cap = nullptr;
@@ -179,6 +189,11 @@ struct SimPlan {
         cudaEventDestroy(pr.second);
       }
     if (cap) cudaStreamDestroy(cap);
+    for (auto& e : pev)
+      if (e) cudaEventDestroy(e);
+    cudaFree(wave_off_d);
+    cudaFree(gbar);
+    cudaFree(phase_ns);
     for (auto& g : groups) {
       cudaFree(g.sg);
       cudaFree(g.overlay);
@@ -397,6 +412,9 @@ struct CcfPlan {
   WaveArgs tc;                       // tensor-core tiling fields
   int n_parts = 0;                   // partial key lists per item
   int64_t ev_bytes = 0, part_bytes = 0, bmat_bytes = 0;
+  // one cooperative kernel for every wavefront of a call (persist.cu)
+  bool persist = false;
+  int p_grid = 0, p_gw = 32;
 };
 
 }  // namespace
@@ -412,9 +430,65 @@ bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
     return t->ndim == 2 ? (hint == 1 || hint == 2 || hint == 4 || hint == 8)
                         : (hint == 1 || hint == 2 || hint == 4);
   const int nt = hint & 0xFFFF, mt = (hint >> 16) & 0xFF, flags = hint >> 24;
+  if (flags == kTilePersist >> 24)   // persistent kernel: nt up to 256, mt 0 = automatic
+    return (nt == 16 || nt == 32 || nt == 64 || nt == 128 || nt == 256) && mt <= kTcMaxMt &&
+           mt * nt <= 512;
   return (nt == 16 || nt == 32 || nt == 64 || nt == 128) && mt >= 1 && mt <= kTcMaxMt &&
          mt * nt <= 512 && flags >= 0 && flags <= 63 && ((flags >> 3) & 3) != 3 &&
          !((flags >> 5) & 1 && (flags >> 2) & 1);
+}
+
+bool tile_is_persist(int precision, int hint) {
+  return precision != 0 && (hint >> 24) == (kTilePersist >> 24);
+}
+
+// The persistent form of a simulation plan: M-tiles per CTA so that every
+// M-group has a CTA of the cooperative grid, threads per item in the gather
+// and paste phases from the widest wavefront. Returns CCW_OK or a refusal.
+int plan_persist(const ccw_ti* t, int nch, int K, int max_items, int hint, int vt_ext, int cut,
+                 int learned, CcfPlan& cp) {
+  if (t->ndim != 2) return fail(CCW_EINVAL, "the persistent kernel is 2D only");
+  if (K > 8) return fail(CCW_EINVAL, "the persistent kernel needs K <= 8");
+  if (vt_ext || cut || learned)
+    return fail(CCW_EINVAL,
+                "the persistent kernel does not run the virtual template, the boundary cut or "
+                "the learned proposal");
+  WaveArgs& a = cp.tc;
+  memset(&a, 0, sizeof(a));
+  a.nt = hint & 0xFFFF;
+  a.ks = t->ks;
+  a.ksteps = nch * t->rows * (t->ks / 16);
+  a.px8 = t->px8;
+  a.mtiles = t->mtiles;
+  a.z8_nq = t->z8_nq;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    return fail(CCW_ECUDA, "multiprocessor count");
+  int mt = (hint >> 16) & 0xFF;
+  if (mt == 0) mt = (t->mtiles + sms - 1) / sms;
+  if (mt > kTcMaxMt || mt * a.nt > 512)
+    return fail(CCW_EINVAL, "persistent kernel: %d M-tiles per CTA needed (at most %d, mt x nt "
+                "<= 512)", mt, kTcMaxMt);
+  a.mt = mt;
+  a.n_mgroups = (t->mtiles + mt - 1) / mt;
+  a.a_nq = tc_a_nq(t, mt);
+  const int gw = max_items <= sms ? 256 : max_items <= 2 * sms ? 128 : max_items <= 4 * sms ? 64
+                                                                                            : 32;
+  cp.p_gw = gw;
+  cp.smem = persist_smem_bytes(nch, a.a_nq, mt, a.nt, a.ksteps, t->F, t->Tj * t->Tj, t->T, gw);
+  if (cp.smem > 227 * 1024)
+    return fail(CCW_EINVAL, "persistent kernel: %d bytes of shared memory needed", cp.smem);
+  cp.p_grid = persist_grid(cp.smem, cp.precision == 2);
+  if (cp.p_grid < a.n_mgroups)
+    return fail(CCW_EINVAL, "persistent kernel: %d M-groups for %d resident CTAs", a.n_mgroups,
+                cp.p_grid);
+  cp.persist = true;
+  cp.streamed = false;
+  cp.n_parts = a.n_mgroups;
+  cp.bmat_bytes = ((max_items + a.nt - 1) / a.nt) * (int64_t)a.ksteps * 32 * a.nt;
+  cp.part_bytes = (int64_t)max_items * cp.n_parts * K * 8;
+  return CCW_OK;
 }
 
 void plan_ccf(const ccw_ti* t, int precision, int nch, int K, int n_items, const EvDev& ev,
@@ -628,6 +702,12 @@ extern "C" {
 const char* ccw_last_error(void) { return g_err; }
 
 int64_t ccw_launch_count(void) { return g_launches.load(); }
+
+int ccw_set_barrier_polls(int64_t polls) {
+  if (polls < 0 || polls > 0xFFFFFFFFll) return fail(CCW_EINVAL, "polls out of range");
+  g_barrier_polls.store(polls == 0 ? (1u << 22) : (uint32_t)polls);
+  return CCW_OK;
+}
 
 int ccw_profile_enable(int32_t enable) {
   std::lock_guard<std::mutex> g(g_prof.mu);
@@ -1094,8 +1174,18 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   event_layout(nch, t->rows, t->TjP, hd_capacity(t, p->vt_ext), t->F, t->rows * t->Tj, pl->evl);
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
-  plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
-  if (cp->smem > 220 * 1024) {
+  if (tile_is_persist(p->precision, p->ccf_tile)) {
+    cp->precision = p->precision;
+    if (int rc = plan_persist(t, nch, pl->K, pl->max_items, p->ccf_tile, p->vt_ext,
+                              p->boundary_cut, p->learned, *cp)) {
+      delete pl;
+      return rc;
+    }
+    cp->ev_bytes = (int64_t)pl->max_items * pl->evl.stride;
+  } else {
+    plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
+  }
+  if (!cp->persist && cp->smem > 220 * 1024) {
     const int need = cp->smem;   // the plan owns cp
     delete pl;
     return fail(CCW_EINVAL, "ccf_tile 0x%x needs %d bytes of shared memory", p->ccf_tile, need);
@@ -1123,12 +1213,21 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
         (e = cudaMalloc(&pl->enc_act, sizeof(float) * (size_t)infer_act_floats(t->F, t->Tj) *
                                           pl->max_items)) != cudaSuccess)) ||
       (e = cudaMalloc((void**)&pl->call, sizeof(CallDev))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&pl->dgroups, sizeof(SimGroup) * n_groups)) != cudaSuccess) {
+      (e = cudaMalloc((void**)&pl->dgroups, sizeof(SimGroup) * n_groups)) != cudaSuccess ||
+      (cp->persist &&
+       ((e = cudaMalloc((void**)&pl->wave_off_d, sizeof(int64_t) * (pl->n_waves + 1))) !=
+            cudaSuccess ||
+        (e = cudaMalloc((void**)&pl->gbar, 2 * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&pl->phase_ns, 3 * sizeof(unsigned long long))) !=
+            cudaSuccess))) {
     delete pl;
     return fail(CCW_ENOMEM, "simulation workspace: %s", cudaGetErrorString(e));
   }
   pl->evl.base = (unsigned char*)pl->ev;
-  if ((e = cudaMemcpy(pl->items, items.data(), sizeof(int4) * items.size(),
+  if ((cp->persist &&
+       (e = cudaMemcpy(pl->wave_off_d, pl->wave_off.data(), sizeof(int64_t) * (pl->n_waves + 1),
+                       cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemcpy(pl->items, items.data(), sizeof(int4) * items.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     delete pl;
@@ -1224,6 +1323,54 @@ int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
   e = cudaGraphInstantiate(&pl->exec[prof ? 1 : 0], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+  return CCW_OK;
+}
+
+// The whole call as one cooperative kernel (persist.cu), launched on `st`.
+int launch_persist_call(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
+  const CcfPlan& cp = *static_cast<const CcfPlan*>(pl->cp);
+  WaveArgs a;
+  fill_ti(t, pl->score_mode, a);
+  a.ev = pl->evl;
+  a.groups = pl->dgroups;
+  a.S = t->T - t->O;
+  a.call = pl->call;
+  a.K = pl->K;
+  a.part = (unsigned long long*)pl->part;
+  a.items = (const int4*)pl->items;
+  a.precision = cp.precision;
+  a.z8 = cp.precision == 2 ? t->z8_bf16 : t->z8_f16;
+  a.z8_nq = cp.tc.z8_nq;
+  a.px8 = cp.tc.px8;
+  a.ks = cp.tc.ks;
+  a.ksteps = cp.tc.ksteps;
+  a.mtiles = cp.tc.mtiles;
+  a.mt = cp.tc.mt;
+  a.n_mgroups = cp.tc.n_mgroups;
+  a.nt = cp.tc.nt;
+  a.a_nq = cp.tc.a_nq;
+  a.bmat = pl->bmat;
+  a.n_parts = cp.n_parts;
+  a.wave_off = pl->wave_off_d;
+  a.n_waves = pl->n_waves;
+  a.gbar = pl->gbar;
+  a.spin_limit = g_barrier_polls.load();
+  a.gw = cp.p_gw;
+  a.phase_ns = prof ? pl->phase_ns : nullptr;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(pl->gbar, 0, 2 * sizeof(unsigned), st)) != cudaSuccess ||
+      (prof && (e = cudaMemsetAsync(pl->phase_ns, 0, 3 * sizeof(unsigned long long), st)) !=
+                   cudaSuccess))
+    return cuda_fail(e, "persistent kernel setup");
+  if (prof) {
+    for (auto& ev : pl->pev)
+      if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "event");
+    cudaEventRecord(pl->pev[0], st);
+  }
+  if ((e = launch_persist(a, cp.smem, cp.p_grid, st)) != cudaSuccess)
+    return cuda_fail(e, "persistent kernel launch");
+  ++g_launches;
+  if (prof) cudaEventRecord(pl->pev[1], st);
   return CCW_OK;
 }
 
@@ -1330,15 +1477,21 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
                              st)) != cudaSuccess)
       return cuda_fail(e, "log clear");
   }
-  const int gi = prof ? 1 : 0;
-  if (!pl->exec[gi])
-    if (int rc = capture_waves(t, pl, prof)) return rc;
-  if ((e = cudaGraphLaunch(pl->exec[gi], st)) != cudaSuccess) return cuda_fail(e, "graph launch");
-  int64_t wave_launches = 0;
-  for (int w = 0; w < pl->n_waves; ++w)
-    wave_launches += (pl->learned ? 11 : 3) *
-                     ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
-  g_launches += wave_launches;
+  const bool persist = static_cast<const CcfPlan*>(pl->cp)->persist;
+  if (persist) {
+    if (int rc = launch_persist_call(t, pl, prof, st)) return rc;
+  } else {
+    const int gi = prof ? 1 : 0;
+    if (!pl->exec[gi])
+      if (int rc = capture_waves(t, pl, prof)) return rc;
+    if ((e = cudaGraphLaunch(pl->exec[gi], st)) != cudaSuccess)
+      return cuda_fail(e, "graph launch");
+    int64_t wave_launches = 0;
+    for (int w = 0; w < pl->n_waves; ++w)
+      wave_launches += (pl->learned ? 11 : 3) *
+                       ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
+    g_launches += wave_launches;
+  }
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
     if ((e = launch_crop_out((const uint8_t*)g.sg, g.gp_vol, g.gp, groups[i].out_dev, g.g, d,
@@ -1352,7 +1505,18 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
           cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_fail(e, "simulation");
-  if (prof) {
+  if (prof && persist) {
+    // the persistent kernel's launch time; its phases from the device clock
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pl->pev[0], pl->pev[1]) == cudaSuccess) {
+      g_prof.total_ms += ms;
+      ++g_prof.launches;
+    }
+    unsigned long long ns[3] = {0, 0, 0};
+    if (cudaMemcpy(ns, pl->phase_ns, sizeof(ns), cudaMemcpyDeviceToHost) == cudaSuccess)
+      for (int i = 0; i < 3; ++i) g_prof.phase_ms[i] += 1e-6 * (double)ns[i];
+  } else if (prof) {
     std::lock_guard<std::mutex> g(g_prof.mu);
     for (size_t i = 0; i < pl->prof_events.size(); ++i) {
       const auto& pr = pl->prof_events[i];

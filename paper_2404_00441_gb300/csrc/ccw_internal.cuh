@@ -25,6 +25,7 @@ constexpr int kMaxCutTempl = 128; // largest template of the boundary-cut paste
 constexpr int kMaxLevel2D = 4;
 constexpr int kMaxLevel3D = 2;
 constexpr int kTcMaxMt = 4;       // M-tiles per CTA of the tensor-core CCF
+constexpr int kTilePersist = 1 << 30;   // ccf_tile flag: one cooperative kernel per call
 constexpr int kMaxChunks = 32;    // 4-wide tap chunks per template row (Tj <= 128)
 
 // ---------------------------------------------------------------------------
@@ -217,6 +218,13 @@ struct WaveArgs {
   // paste and conditioning variants (simulation mode)
   int vt_ext;               // cells the virtual template extends the window forward
   int cut;                  // 1: minimum-error boundary cut at paste (2D)
+  // one cooperative kernel for all wavefronts of a call (persist.cu)
+  const int64_t* wave_off;  // [n_waves + 1] first item of every wavefront in `items`
+  int n_waves;
+  unsigned* gbar;           // [2]: grid-barrier arrivals, abort flag (zeroed per call)
+  uint32_t spin_limit;      // polls of a grid-barrier wait before it gives up
+  int gw;                   // threads per item in the gather and paste phases
+  unsigned long long* phase_ns;  // [3] summed phase durations (profiling) or NULL
 };
 
 }  // namespace ccw

@@ -122,12 +122,14 @@ struct PasteGeom {
 
 // Visit the cells (qx, qy, qz) of a T^d window with consecutive threads on
 // consecutive x (coalesced rows); indices advance without divisions.
+// `lt` is the calling thread's index among the nthreads that share the work
+// (threadIdx.x when the whole CTA does).
 template <int D, typename Fn>
-__device__ __forceinline__ void for_window(int T, int nthreads, Fn&& fn) {
+__device__ __forceinline__ void for_window(int T, int nthreads, int lt, Fn&& fn) {
   const int nrows = (D == 3) ? T * T : T;
   if (T <= nthreads) {
     const int rpi = nthreads / T;
-    const int qx = threadIdx.x % T, r0 = threadIdx.x / T;
+    const int qx = lt % T, r0 = lt / T;
     if (r0 >= rpi) return;
     int qy = r0, qz = 0;
     while (qy >= T) {
@@ -144,7 +146,7 @@ __device__ __forceinline__ void for_window(int T, int nthreads, Fn&& fn) {
     }
   } else {
     for (int row = 0; row < nrows; ++row)
-      for (int qx = threadIdx.x; qx < T; qx += nthreads) fn(qx, row % T, row / T);
+      for (int qx = lt; qx < T; qx += nthreads) fn(qx, row % T, row / T);
   }
 }
 
@@ -152,7 +154,8 @@ __device__ __forceinline__ void for_window(int T, int nthreads, Fn&& fn) {
 // coefficients, one contiguous run of Tj blocks per coarse row) into shared
 // memory, ordered (ux fastest, then uy, uz). Needs a following barrier.
 template <int D>
-__device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, int nthreads) {
+__device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, int nthreads,
+                             int lt) {
   const int s = 1 << J;
   const int sd = (D == 3) ? s * s * s : s * s;
   const int pcx = pick % p.cd0;
@@ -166,7 +169,7 @@ __device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, i
     // r0 + rpp, ... (one division per thread)
     const int run4 = run / 4;
     const int rpp = nthreads / run4;
-    const int r0 = threadIdx.x / run4, k = threadIdx.x % run4;
+    const int r0 = lt / run4, k = lt % run4;
     if (r0 < rpp) {
       int uy = r0 % Tj, uz = r0 / Tj;
       for (int row = r0; row < nrows; row += rpp) {
@@ -184,7 +187,7 @@ __device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, i
     }
   } else if (sd % 4 == 0) {
     const int run4 = run / 4;
-    for (int i = threadIdx.x; i < nrows * run4; i += nthreads) {
+    for (int i = lt; i < nrows * run4; i += nthreads) {
       const int row = i / run4, k = i % run4;
       const int uy = row % Tj, uz = row / Tj;
       const int16_t* src =
@@ -193,7 +196,7 @@ __device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, i
           __ldg(reinterpret_cast<const uint2*>(src) + k);
     }
   } else {
-    for (int i = threadIdx.x; i < nrows * run; i += nthreads) {
+    for (int i = lt; i < nrows * run; i += nthreads) {
       const int row = i / run, k = i % run;
       const int uy = row % Tj, uz = row / Tj;
       const int16_t* src =
@@ -215,7 +218,7 @@ __device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, i
 // given, else from global memory. Cells outside the grid are skipped. The
 // caller re-imposes hard data afterwards (after a barrier).
 template <int D>
-__device__ void paste_pixels(const PasteGeom& p, int pick, int J, int nthreads,
+__device__ void paste_pixels(const PasteGeom& p, int pick, int J, int nthreads, int lt,
                              const int16_t* staged = nullptr) {
   const int s = 1 << J;
   const int sd = (D == 3) ? s * s * s : s * s;
@@ -224,7 +227,7 @@ __device__ void paste_pixels(const PasteGeom& p, int pick, int J, int nthreads,
   const int pcz = pick / (p.cd0 * p.cd1);
   const int Tj = p.Tj;
   const int T = Tj * s;
-  for_window<D>(T, nthreads, [&](int qx, int qy, int qz) {
+  for_window<D>(T, nthreads, lt, [&](int qx, int qy, int qz) {
     const int gx = p.o[0] + qx, gy = p.o[1] + qy, gz = p.o[2] + qz;
     if (gx < 0 || gy < 0 || gz < 0 || gx >= p.g[0] || gy >= p.g[1] || gz >= p.g[2]) return;
     const int ux = qx >> J, uy = qy >> J, uz = qz >> J;
@@ -287,13 +290,13 @@ __device__ __forceinline__ void haar_block_inverse(int (&v)[(D == 3) ? S * S * S
 // (S-byte words when `aligned`: window origin and grid pitch multiples of S).
 // For windows that lie inside the grid (simulation lattice).
 template <int D, int S>
-__device__ void paste_blocks(const PasteGeom& p, const int16_t* staged, int nthreads,
+__device__ void paste_blocks(const PasteGeom& p, const int16_t* staged, int nthreads, int lt,
                              bool aligned) {
   constexpr int SD = (D == 3) ? S * S * S : S * S;
   constexpr int SZ = (D == 3) ? S : 1;
   const int Tj = p.Tj;
   const int nblk = (D == 3) ? Tj * Tj * Tj : Tj * Tj;
-  for (int u = threadIdx.x; u < nblk; u += nthreads) {
+  for (int u = lt; u < nblk; u += nthreads) {
     const int ux = u % Tj, uy = (u / Tj) % Tj, uz = (D == 3) ? u / (Tj * Tj) : 0;
     int v[SD];
     const int16_t* blk = staged + u * SD;
@@ -328,8 +331,8 @@ __device__ void paste_blocks(const PasteGeom& p, const int16_t* staged, int nthr
 // after a barrier that follows the paste.
 template <int D>
 __device__ void paste_hard_data(const PasteGeom& p, const int2* hdl, int n_hd, int T,
-                                int nthreads) {
-  for (int k = threadIdx.x; k < n_hd; k += nthreads) {
+                                int nthreads, int lt) {
+  for (int k = lt; k < n_hd; k += nthreads) {
     const int e = hdl[k].y;
     if (e < 0) continue;   // kHdVirtual: outside the window
     const int q = e >> 8;

@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
                                     : (tid < 3 ? 0 : -1));
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
-  paste_pixels<D>(g, pk, t.J, nth);
+  paste_pixels<D>(g, pk, t.J, nth, tid);
   __syncthreads();
-  paste_hard_data<D>(g, hdl, min(cnt[3], a.ev.hd_cap), T, nth);
+  paste_hard_data<D>(g, hdl, min(cnt[3], a.ev.hd_cap), T, nth, tid);
 }
 
 // Standalone Inverse-DWT paste (ccw_idwt_paste): one CTA per batch element.
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kThreads)
   g.o[0] = origins[3 * b];
   g.o[1] = origins[3 * b + 1];
   g.o[2] = (D == 3) ? origins[3 * b + 2] : 0;
-  paste_pixels<D>(g, pk, J, kThreads);
+  paste_pixels<D>(g, pk, J, kThreads, threadIdx.x);
 }
 
 cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3], const int cd[3],

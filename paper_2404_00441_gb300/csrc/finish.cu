@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     // the pattern into shared memory, then the boundary-cut paste (the
     // launch guarantees staged_bytes > 0 and the cut buffers behind it)
     unsigned char* pat = reinterpret_cast<unsigned char*>(staged) + ((staged_bytes + 15) & ~15);
-    stage_blocks<D>(g, pk, t.J, staged, nth);
+    stage_blocks<D>(g, pk, t.J, staged, nth, tid);
     __syncthreads();
     PasteGeom gl = g;
     gl.grid = pat;
@@ -261,31 +261,31 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     gl.g[2] = 1;
     gl.o[0] = gl.o[1] = gl.o[2] = 0;
     if (t.J == 2)
-      paste_blocks<D, 4>(gl, staged, nth, true);
+      paste_blocks<D, 4>(gl, staged, nth, tid, true);
     else if (t.J == 1)
-      paste_blocks<D, 2>(gl, staged, nth, true);
+      paste_blocks<D, 2>(gl, staged, nth, tid, true);
     else
-      paste_pixels<D>(gl, pk, t.J, nth, staged);
+      paste_pixels<D>(gl, pk, t.J, nth, tid, staged);
     __syncthreads();
     quilt_paste(g, pat, t.T, a.Oj * t.s, it.flips, pat + ((t.T * t.T + 15) & ~15), nth);
   } else if (staged_bytes > 0) {
-    stage_blocks<D>(g, pk, t.J, staged, nth);
+    stage_blocks<D>(g, pk, t.J, staged, nth, tid);
     __syncthreads();
     // block-wise inverse in registers for the common levels, else per cell
     const bool aligned = (g.o[0] % t.s) == 0 && (g.g[0] % t.s) == 0;
     if (D == 2 && t.J == 2)
-      paste_blocks<D, 4>(g, staged, nth, aligned);
+      paste_blocks<D, 4>(g, staged, nth, tid, aligned);
     else if (t.J == 1)
-      paste_blocks<D, 2>(g, staged, nth, aligned);
+      paste_blocks<D, 2>(g, staged, nth, tid, aligned);
     else
-      paste_pixels<D>(g, pk, t.J, nth, staged);
+      paste_pixels<D>(g, pk, t.J, nth, tid, staged);
   } else {
-    paste_pixels<D>(g, pk, t.J, nth);
+    paste_pixels<D>(g, pk, t.J, nth, tid);
   }
   __syncthreads();
   paste_hard_data<D>(g, reinterpret_cast<const int2*>(a.ev.base + (int64_t)item * a.ev.stride +
                                                       a.ev.hd_off),
-                     em[kEvNHd], t.T, nth);
+                     em[kEvNHd], t.T, nth, tid);
 }
 
 template <int D, int MODE>

@@ -65,3 +65,13 @@ def test_realization_parallel_oracle_baseline():
     wall = bench.oracle_parallel(w, 12, 2)
     assert 0.0 < wall < 60.0
     assert bench.host_cores() >= 1
+
+
+def test_gpus_flag_starts_that_many_ranks():
+    """`bench.py --gpus N` outside a launcher runs N ranks under
+    torch.distributed.run on 127.0.0.1 with the same arguments."""
+    cmd = bench.rank_command(["--gpus", "4", "--steps", "2"], 4)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert "--nproc-per-node=4" in cmd
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "2"]
