@@ -51,6 +51,8 @@ extern "C" {
 #define CCW_EUNSUPPORTED (-5)/* valid request this build does not handle */
 
 #define CCW_UNKNOWN 255
+#define CCW_PRECISION_INEXACT 4 /* ccw_params.precision flag: FP16/BF16 past the
+                                   format's exact integer range (see there) */
 #define CCW_MAX_TOPK 64
 #define CCW_LOG_FLAG_UNIFORM 1  /* patch log: empty data event, uniform pick */
 #define CCW_LOG_FLAG_DONE 2     /* patch log: the patch was simulated */
@@ -80,7 +82,14 @@ typedef struct {
                           when an operand could exceed the format's exact
                           integer range (2048 for FP16, 256 for BF16; the
                           operands are at most 2^(d J) in the one-hot score,
-                          (F - 1) 2^(d J) in the literal one). */
+                          (F - 1) 2^(d J) in the literal one), unless
+                          CCW_PRECISION_INEXACT is or'ed in: the operands
+                          are then rounded to the format (round to nearest
+                          even) and scores, rankings and picks are
+                          approximate: a score is off by at most 2^-7
+                          (BF16) or 2^-10 (FP16) of the sum of the absolute
+                          products of its taps, plus FP32 accumulation and
+                          the rounding to an integer. */
   int32_t learned;     /* 0: full search for every patch; 1: learned proposal
                           first (an addition of this library, see
                           ccw_ti_attach_proposal): 2D, one-hot score only,
@@ -177,6 +186,9 @@ void ccw_ti_free(ccw_ti* ti);
  *             the difference goes to the upper one), so entry 0 is the
  *             block's approximation.
  *   what = 3: the cropped TI, uint8 [dims].
+ *   what = 4: the attached learned proposal's window tables, bfloat16
+ *             [16 mask types][P_c][64] (ccw_ti_attach_proposal; rows of
+ *             unused mask types are zero); CCW_EINVAL when none is attached.
  */
 int ccw_ti_export(const ccw_ti* ti, int32_t what, void* dst_dev, void* stream);
 
@@ -240,7 +252,7 @@ int ccw_simulate_groups(const ccw_ti* ti, const ccw_params* params, const ccw_gr
  *  hd_dev     uint8 [B][T^d]: hard data of each window (255 = none), or NULL.
  *  k          K in [1, CCW_MAX_TOPK].
  *  score_mode bits 0-3: 0 one-hot, 1 literal score; bits 4-7: precision
- *             (as ccw_params.precision).
+ *             (as ccw_params.precision, CCW_PRECISION_INEXACT included).
  *  ctr_dev    uint32 [B][2]: (realization r, patch p) Philox counter words.
  *  topk_*_dev int32 [B][k]: ranked candidates with their score and mismatch
  *             count; slots past min(k, P_c), and all slots of an empty data

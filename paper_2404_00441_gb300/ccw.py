@@ -190,6 +190,8 @@ class TI:
             out = torch.empty(cshape + (sd,), dtype=torch.int16, device="cuda")
         elif what == 3:
             out = torch.empty(self.dims[::-1], dtype=torch.uint8, device="cuda")
+        elif what == 4:
+            out = torch.empty((16, self.n_cand, 64), dtype=torch.bfloat16, device="cuda")
         else:
             raise ValueError(what)
         _check(self._lib.ccw_ti_export(self._h, what, _ptr(out), _stream(stream)))

@@ -325,11 +325,16 @@ int hd_capacity(const ccw_ti* t, int vt_ext = 0) {
 // the 16-bit format exactly (FP16: |v| <= 2048, BF16: |v| <= 256).
 int check_precision(const ccw_ti* t, int precision, int score_mode, int K = 1, int hint = 0) {
   if (precision == 0) return CCW_OK;
-  if (precision != 1 && precision != 2) return fail(CCW_EINVAL, "precision must be 0, 1 or 2");
+  if (precision != 1 && precision != 2 && precision != (1 | CCW_PRECISION_INEXACT) &&
+      precision != (2 | CCW_PRECISION_INEXACT))
+    return fail(CCW_EINVAL, "precision must be 0, 1 or 2, optionally with CCW_PRECISION_INEXACT");
   // the streamed tensor-core kernel (3D, or 2D on request) keeps the K best
   // keys of each thread in registers: K <= 8
   if ((t->ndim == 3 || ((hint >> 25) & 1)) && K > 8)
     return fail(CCW_EUNSUPPORTED, "the streamed tensor-core CCF supports K <= 8");
+  // beyond the format's exact integers only on request: operands are then
+  // rounded to it and the scores are approximate
+  if (precision & CCW_PRECISION_INEXACT) return CCW_OK;
   const int64_t vmax = (int64_t)(score_mode == 0 ? 1 : t->F - 1) * t->sd;
   const int64_t lim = precision == 1 ? 2048 : 256;
   if (vmax > lim)
@@ -618,6 +623,7 @@ int search_common(const ccw_ti* t, int mode, int32_t B, const uint8_t* de, const
   if (int rc = split_mode(score_arg, score_mode, precision)) return rc;
   if (int rc = check_score_bound(t, score_mode)) return rc;
   if (int rc = check_precision(t, precision, score_mode, mode == kModeSearch ? k : 1)) return rc;
+  precision &= 3;   // the format; checked above
   if (mode == kModeSearch && (k < 1 || k > CCW_MAX_TOPK))
     return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
   if (B == 0) return CCW_OK;
@@ -989,6 +995,11 @@ int ccw_ti_export(const ccw_ti* t, int32_t what, void* dst, void* stream) {
       e = cudaMemcpyAsync(dst, t->d_ti, (size_t)t->n[0] * t->n[1] * t->n[2],
                           cudaMemcpyDeviceToDevice, st);
       break;
+    case 4:
+      if (!t->d_tables) return fail(CCW_EINVAL, "no proposal attached");
+      e = cudaMemcpyAsync(dst, t->d_tables, sizeof(__nv_bfloat16) * 16 * 64 * (size_t)t->P,
+                          cudaMemcpyDeviceToDevice, st);
+      break;
     default:
       return fail(CCW_EINVAL, "unknown export %d", what);
   }
@@ -1029,6 +1040,7 @@ int ccw_ccf_search_noalloc(const ccw_ti* t, int32_t B, const uint8_t* de_dev,
   if (int rc = split_mode(score_mode, sm, precision)) return rc;
   if (int rc = check_score_bound(t, sm)) return rc;
   if (int rc = check_precision(t, precision, sm, k)) return rc;
+  precision &= 3;   // the format; checked above
   if (k < 1 || k > CCW_MAX_TOPK) return fail(CCW_EINVAL, "k must be in [1, %d]", CCW_MAX_TOPK);
   if (B == 0) return CCW_OK;
   if (!de_dev || !ctr_dev || !topk_idx_dev || !topk_score_dev || !topk_mis_dev || !pick_dev)
@@ -1174,8 +1186,9 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   event_layout(nch, t->rows, t->TjP, hd_capacity(t, p->vt_ext), t->F, t->rows * t->Tj, pl->evl);
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
-  if (tile_is_persist(p->precision, p->ccf_tile)) {
-    cp->precision = p->precision;
+  const int fmt = p->precision & 3;   // the format (the exactness flag was checked)
+  if (tile_is_persist(fmt, p->ccf_tile)) {
+    cp->precision = fmt;
     if (int rc = plan_persist(t, nch, pl->K, pl->max_items, p->ccf_tile, p->vt_ext,
                               p->boundary_cut, p->learned, *cp)) {
       delete pl;
@@ -1183,7 +1196,7 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
     }
     cp->ev_bytes = (int64_t)pl->max_items * pl->evl.stride;
   } else {
-    plan_ccf(t, p->precision, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
+    plan_ccf(t, fmt, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
   }
   if (!cp->persist && cp->smem > 220 * 1024) {
     const int need = cp->smem;   // the plan owns cp
@@ -1384,7 +1397,7 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if (int rc = check_precision(t, p->precision, p->score_mode, p->topk, p->ccf_tile)) return rc;
   if (p->path_random != 0 && p->path_random != 1) return fail(CCW_EINVAL, "bad path_random");
   if (p->learned != 0 && p->learned != 1) return fail(CCW_EINVAL, "bad learned flag");
-  if (!valid_tile_hint(t, p->precision, p->ccf_tile))
+  if (!valid_tile_hint(t, p->precision & 3, p->ccf_tile))
     return fail(CCW_EINVAL, "ccf_tile 0x%x is not a valid tiling for precision %d", p->ccf_tile,
                 p->precision);
   if (p->learned) {

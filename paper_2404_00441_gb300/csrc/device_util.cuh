@@ -171,29 +171,58 @@ __device__ void stage_blocks(const PasteGeom& p, int pick, int J, int16_t* sm, i
     const int rpp = nthreads / run4;
     const int r0 = lt / run4, k = lt % run4;
     if (r0 < rpp) {
+      // up to 4 rows' words loaded before any is stored (latencies overlap)
       int uy = r0 % Tj, uz = r0 / Tj;
-      for (int row = r0; row < nrows; row += rpp) {
-        const int16_t* src =
-            p.pyr +
-            ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
-        reinterpret_cast<uint2*>(sm + (int64_t)row * run)[k] =
-            __ldg(reinterpret_cast<const uint2*>(src) + k);
-        uy += rpp;
-        while (uy >= Tj) {
-          uy -= Tj;
-          ++uz;
+      for (int row = r0; row < nrows; row += 4 * rpp) {
+        uint2 v[4];
+        int rows_done = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (row + b * rpp < nrows) {
+            const int16_t* src =
+                p.pyr +
+                ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
+            v[b] = __ldg(reinterpret_cast<const uint2*>(src) + k);
+            rows_done = b + 1;
+          }
+          uy += rpp;
+          while (uy >= Tj) {
+            uy -= Tj;
+            ++uz;
+          }
         }
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (b < rows_done)
+            reinterpret_cast<uint2*>(sm + (int64_t)(row + b * rpp) * run)[k] = v[b];
       }
     }
   } else if (sd % 4 == 0) {
     const int run4 = run / 4;
-    for (int i = lt; i < nrows * run4; i += nthreads) {
-      const int row = i / run4, k = i % run4;
-      const int uy = row % Tj, uz = row / Tj;
-      const int16_t* src =
-          p.pyr + ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
-      reinterpret_cast<uint2*>(sm + (int64_t)row * run)[k] =
-          __ldg(reinterpret_cast<const uint2*>(src) + k);
+    // fewer threads than 8-byte words per row: kBatch words per thread are
+    // loaded before any is stored, so their latencies overlap
+    constexpr int kBatch = 8;
+    const int total = nrows * run4;
+    for (int i0 = lt; i0 < total; i0 += kBatch * nthreads) {
+      uint2 v[kBatch];
+      int dst[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        const int i = i0 + b * nthreads;
+        dst[b] = -1;
+        if (i < total) {
+          const int row = i / run4, k = i % run4;
+          const int uy = row % Tj, uz = row / Tj;
+          const int16_t* src =
+              p.pyr +
+              ((int64_t)pcx + (int64_t)p.nc0 * ((pcy + uy) + (int64_t)p.nc1 * (pcz + uz))) * sd;
+          v[b] = __ldg(reinterpret_cast<const uint2*>(src) + k);
+          dst[b] = row * run4 + k;
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (dst[b] >= 0) reinterpret_cast<uint2*>(sm)[dst[b]] = v[b];
     }
   } else {
     for (int i = lt; i < nrows * run; i += nthreads) {

@@ -34,6 +34,7 @@ constexpr int kPThreads = 256;
 constexpr int kPRegK = 8;              // K <= 8: per-thread K-lists in registers
 constexpr int kPCntInts = 12;          // per-item counters ahead of the block counts
 constexpr int kPMinSmem = 120 * 1024;  // dynamic shared memory floor: one CTA per SM
+constexpr int kPHdStage = 512;         // hard data of a chunk staged in shared memory
 
 // ---------------------------------------------------------------------------
 // Shared-memory layout (host and device)
@@ -41,7 +42,7 @@ constexpr int kPMinSmem = 120 * 1024;  // dynamic shared memory floor: one CTA p
 struct PLayout {
   int bar, meta, cand, a, u;   // byte offsets; u = phase-local union region
   int grp_a, grp_c;            // per-group bytes in phases A and C
-  int b, s, w, m;              // phase B offsets inside u
+  int b, s, w, m, h;           // phase B offsets inside u
   int bytes;
 };
 
@@ -69,7 +70,8 @@ __host__ __device__ inline PLayout p_layout(int nch, int a_nq, int mt, int nt, i
   const int sb = 128 * (ntc + 4) * 4, lb = kPThreads * kPRegK * 8;
   L.w = L.s + p_align(sb > lb ? sb : lb, 128);
   L.m = L.w + kPThreads * 8;
-  const int ub = L.m + p_align(128 * (ntc + 2) * 2, 128);
+  L.h = L.m + p_align(128 * (ntc + 2) * 2, 128);   // hd offsets [32], then entries
+  const int ub = L.h + 128 + kPHdStage * 8;
   // phase C, per group: staged coefficients (T^2 int16), top-K keys, the
   // selected key, reduction slots
   L.grp_c = p_align(p_align(T * T * 2, 16) + CCW_MAX_TOPK * 8 + 8 + 16 * 8, 128);
@@ -173,55 +175,93 @@ __device__ void p_event(const WaveArgs& a, int64_t gidx, int wi, const Grp& g, i
   g.sync();
   int my_known = 0, my_const = 0, my_mask = 0, bad = 0;
   const bool words = s == 4 && ((it.o[0] | it.Gp[0]) & 3) == 0;
-  for (int u = g.lt; u < ncells; u += g.n) {
-    const int ux = u % Tj, uy = u / Tj;
-    int cf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (words) {
-      // one 32-bit word of 4 codes per block row (SWAR facies counts); hard
-      // data replace their bytes first
+  // facies counts of block u -> shared memory and this thread's sums
+  auto account = [&](int u, const int (&cf)[8]) {
+    int c = 0;
 #pragma unroll
-      for (int cy = 0; cy < 4; ++cy) {
-        const int qy = uy * 4 + cy;
-        const int gx0 = it.o[0] + ux * 4, gy = it.o[1] + qy;
-        uint32_t vw = *reinterpret_cast<const uint32_t*>(sg + gx0 + (int64_t)it.Gp[0] * gy);
-        if (it.overlay) {
-          const int hy = gy - it.off[1];
-          uint32_t hw = 0xFFFFFFFFu;
-          if (hy >= 0 && hy < it.G[1]) {
-            const uint8_t* orow = it.overlay + (int64_t)it.G[0] * hy;
+    for (int f = 0; f < 8; ++f) {
+      if (f >= t.F) break;
+      counts[f * ncells + u] = cf[f];
+      c += cf[f];
+    }
+    if (!c) return;
+    my_known += c;
+    ++my_mask;
+    if (t.score_mode == 0) my_const += t.sd * cf[(t.F - 1) & 7];
+  };
+  if (words) {
+    // one 32-bit word of 4 codes per block row (SWAR facies counts); the
+    // rows of kNb blocks are loaded before any is counted; hard data replace
+    // their bytes first
+    constexpr int kNb = 4;
+    for (int u0 = g.lt; u0 < ncells; u0 += kNb * g.n) {
+      uint32_t vw[kNb][4];
 #pragma unroll
-            for (int cx = 0; cx < 4; ++cx) {
-              const int hx = gx0 + cx - it.off[0];
-              const uint32_t h = (hx >= 0 && hx < it.G[0]) ? __ldg(orow + hx) : 0xFFu;
-              hw = (hw & ~(0xFFu << (8 * cx))) | (h << (8 * cx));
-            }
-          }
-          if (hw != 0xFFFFFFFFu) {
+      for (int b = 0; b < kNb; ++b) {
+        const int u = u0 + b * g.n;
+        if (u < ncells) {
+          const int ux = u % Tj, uy = u / Tj;
+          const uint8_t* r0 = sg + (it.o[0] + ux * 4) + (int64_t)it.Gp[0] * (it.o[1] + uy * 4);
 #pragma unroll
-            for (int cx = 0; cx < 4; ++cx) {
-              const uint32_t h = (hw >> (8 * cx)) & 0xFFu;
-              if (h == CCW_UNKNOWN) continue;
-              const int qx = ux * 4 + cx;
-              const int k = atomicAdd(&cnt[3], 1);
-              if (k < a.ev.hd_cap)
-                hdl[k] = make_int2(qx + t.tp[0] * qy, ((qx + T * qy) << 8) | (int)h);
-              if (h >= (uint32_t)t.F) bad |= kStatusBadCode;
-            }
-            const uint32_t keep = __vcmpeq4(hw, 0xFFFFFFFFu);
-            vw = (vw & keep) | (hw & ~keep);
-          }
+          for (int cy = 0; cy < 4; ++cy)
+            vw[b][cy] = *reinterpret_cast<const uint32_t*>(r0 + (int64_t)it.Gp[0] * cy);
         }
-        int seen = __popc(__vcmpeq4(vw, 0xFFFFFFFFu)) >> 3;
-#pragma unroll
-        for (int f = 0; f < 8; ++f) {
-          if (f >= t.F) break;
-          const int n = __popc(__vcmpeq4(vw, 0x01010101u * (uint32_t)f)) >> 3;
-          cf[f] += n;
-          seen += n;
-        }
-        if (seen != 4) bad |= kStatusBadCode;
       }
-    } else {
+#pragma unroll
+      for (int b = 0; b < kNb; ++b) {
+        const int u = u0 + b * g.n;
+        if (u >= ncells) break;
+        const int ux = u % Tj, uy = u / Tj;
+        int cf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int cy = 0; cy < 4; ++cy) {
+          const int qy = uy * 4 + cy;
+          const int gx0 = it.o[0] + ux * 4, gy = it.o[1] + qy;
+          uint32_t v = vw[b][cy];
+          if (it.overlay) {
+            const int hy = gy - it.off[1];
+            uint32_t hw = 0xFFFFFFFFu;
+            if (hy >= 0 && hy < it.G[1]) {
+              const uint8_t* orow = it.overlay + (int64_t)it.G[0] * hy;
+#pragma unroll
+              for (int cx = 0; cx < 4; ++cx) {
+                const int hx = gx0 + cx - it.off[0];
+                const uint32_t h = (hx >= 0 && hx < it.G[0]) ? __ldg(orow + hx) : 0xFFu;
+                hw = (hw & ~(0xFFu << (8 * cx))) | (h << (8 * cx));
+              }
+            }
+            if (hw != 0xFFFFFFFFu) {
+#pragma unroll
+              for (int cx = 0; cx < 4; ++cx) {
+                const uint32_t h = (hw >> (8 * cx)) & 0xFFu;
+                if (h == CCW_UNKNOWN) continue;
+                const int qx = ux * 4 + cx;
+                const int k = atomicAdd(&cnt[3], 1);
+                if (k < a.ev.hd_cap)
+                  hdl[k] = make_int2(qx + t.tp[0] * qy, ((qx + T * qy) << 8) | (int)h);
+                if (h >= (uint32_t)t.F) bad |= kStatusBadCode;
+              }
+              const uint32_t keep = __vcmpeq4(hw, 0xFFFFFFFFu);
+              v = (v & keep) | (hw & ~keep);
+            }
+          }
+          int seen = __popc(__vcmpeq4(v, 0xFFFFFFFFu)) >> 3;
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            if (f >= t.F) break;
+            const int n = __popc(__vcmpeq4(v, 0x01010101u * (uint32_t)f)) >> 3;
+            cf[f] += n;
+            seen += n;
+          }
+          if (seen != 4) bad |= kStatusBadCode;
+        }
+        account(u, cf);
+      }
+    }
+  } else {
+    for (int u = g.lt; u < ncells; u += g.n) {
+      const int ux = u % Tj, uy = u / Tj;
+      int cf[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int cy = 0; cy < s; ++cy) {
         const int qy = uy * s + cy;
         for (int cx = 0; cx < s; ++cx) {
@@ -247,18 +287,8 @@ __device__ void p_event(const WaveArgs& a, int64_t gidx, int wi, const Grp& g, i
           }
         }
       }
+      account(u, cf);
     }
-    int c = 0;
-#pragma unroll
-    for (int f = 0; f < 8; ++f) {
-      if (f >= t.F) break;
-      counts[f * ncells + u] = cf[f];
-      c += cf[f];
-    }
-    if (!c) continue;
-    my_known += c;
-    ++my_mask;
-    if (t.score_mode == 0) my_const += t.sd * cf[(t.F - 1) & 7];
   }
   my_known = __reduce_add_sync(0xffffffffu, my_known);
   my_const = __reduce_add_sync(0xffffffffu, my_const);
@@ -360,13 +390,29 @@ __device__ void p_finish(const WaveArgs& a, int64_t gidx, int wi, const Grp& g,
   const unsigned long long* all = a.part + (int64_t)wi * a.n_parts * K;
   g.sync();   // the group's previous item is done with the scratch
   const int M = a.n_parts * K;
+  // the CTAs' keys of this item: loaded once (all loads in flight together)
+  // when each thread holds at most kMine of them, else read per round
+  constexpr int kMine = 12;
+  const bool in_regs = M <= kMine * g.n;
+  uint64_t mine[kMine];
+#pragma unroll
+  for (int i = 0; i < kMine; ++i) {
+    const int j = g.lt + i * g.n;
+    mine[i] = (in_regs && j < M && (j % K) < Kp) ? all[j] : kNoKey;
+  }
   uint64_t prev = 0;
   for (int r = 0; r < Kp; ++r) {
     uint64_t m = kNoKey;
-    for (int j = g.lt; j < M; j += g.n) {
-      if ((j % K) >= Kp) continue;
-      const uint64_t v = all[j];
-      if ((r == 0 || v > prev) && v < m) m = v;
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < kMine; ++i)
+        if ((r == 0 || mine[i] > prev) && mine[i] < m) m = mine[i];
+    } else {
+      for (int j = g.lt; j < M; j += g.n) {
+        if ((j % K) >= Kp) continue;
+        const uint64_t v = all[j];
+        if ((r == 0 || v > prev) && v < m) m = v;
+      }
     }
     m = grp_min_u64(m, g, red);
     if (g.lt == 0) topk[r] = m;
@@ -542,21 +588,26 @@ __global__ void __launch_bounds__(kPThreads, 1) k_persist(const __grid_constant_
         }
         if (ok) {
           tc_fence_after();
+          // K steps (channel, template row, 16 taps) in order; the M-tiles'
+          // independent accumulators take turns, so consecutive MMAs never
+          // wait on each other's accumulation
           const uint32_t idesc = instr_desc(BF16, 128, nt);
           const int k16n = a.ks / 16;
           const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-          for (int j = 0; j < n_mt; ++j) {
-            const uint32_t d = tmem + (uint32_t)(j * nt);
-            for (int k = 0; k < a.ksteps; ++k) {
-              const int k16 = k % k16n;
-              const int rc = k / k16n;
-              const int row = rc % t.rows, ch = rc / t.rows;
-              const uint32_t q = (uint32_t)((128 * j + row * a.px8) / 8 + 2 * k16);
-              const uint64_t ad =
-                  smem_desc(a_base + (uint32_t)ch * a_bytes + q * 128u, 128u, 128u);
-              const uint64_t bd =
-                  smem_desc(b_base + (uint32_t)k * 32u * (uint32_t)nt, 128u, 256u);
-              mma_f16(d, ad, bd, idesc, k > 0 ? 1u : 0u);
+          const uint32_t b_step = 32u * (uint32_t)nt, row_bytes = (uint32_t)a.px8 * 16u;
+          uint32_t kidx = 0, b_addr = b_base;
+          for (int ch = 0; ch < nch; ++ch) {
+            uint32_t a_row = a_base + (uint32_t)ch * a_bytes;
+            for (int row = 0; row < t.rows; ++row, a_row += row_bytes) {
+              for (int k16 = 0; k16 < k16n; ++k16, ++kidx, b_addr += b_step) {
+                const uint64_t bd = smem_desc(b_addr, 128u, 256u);
+                const uint32_t acc = kidx > 0 ? 1u : 0u;
+                for (int j = 0; j < n_mt; ++j) {
+                  const uint64_t ad =
+                      smem_desc(a_row + (uint32_t)(16 * j + 2 * k16) * 128u, 128u, 128u);
+                  mma_f16(tmem + (uint32_t)(j * nt), ad, bd, idesc, acc);
+                }
+              }
             }
           }
           mma_commit(mma_done);
@@ -608,7 +659,14 @@ __global__ void __launch_bounds__(kPThreads, 1) k_persist(const __grid_constant_
           act |= meta[cc * ntc + i].w;
         }
         if (!act) continue;   // the same decision in every thread
-        const bool hd_tile = hd_sum >= 2 * ntc;
+        // hard-data mismatches in a separate pass per M-tile, from lists
+        // staged in shared memory (or, for very many, read from the records)
+        int* hoff = reinterpret_cast<int*>(U + L.h);
+        int2* hs = reinterpret_cast<int2*>(U + L.h + 128);
+        const bool staged = hd_sum > 0 &&
+                            stage_hard_data(a, meta, nti, nt, cc * ntc, ntc, hoff, hs, kPHdStage);
+        const bool hd_tile = staged || hd_sum >= 2 * ntc;
+        if (staged) __syncthreads();
 #pragma unroll 1
         for (int j = 0; j < n_mt; ++j) {
 #pragma unroll 1
@@ -621,7 +679,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_persist(const __grid_constant_
             dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
                                  __uint_as_float(v[6]), __uint_as_float(v[7]));
           }
-          if (hd_tile)
+          if (staged)
+            mismatch_tile_staged(t, meta + cc * ntc, ntc, hoff, hs, cand + j * 128, Mt, ntc + 2);
+          else if (hd_tile)
             mismatch_tile(a, meta, nti, nt, cc * ntc, ntc, cand + j * 128, Mt, ntc + 2);
           __syncthreads();
           uint64_t bound = kNoKey;

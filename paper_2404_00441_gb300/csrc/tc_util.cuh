@@ -148,6 +148,80 @@ __device__ __forceinline__ void mismatch_tile(const WaveArgs& a, const int4* met
   }
 }
 
+// The same count for the items of a chunk whose hard-data lists were first
+// staged in shared memory (item nl's list at hs + hoff[nl], meta[nl].z
+// entries): each lane keeps 4 candidates, and 4 hard data at a time put 16
+// TI loads in flight, none of them waiting on a global load of the list.
+__device__ __forceinline__ void mismatch_tile_staged(const TiDev& t, const int4* meta, int ntc,
+                                                     const int* hoff, const int2* hs,
+                                                     const int2* cand, uint16_t* Mt, int spm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int2 cr[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cr[i] = cand[lane + 32 * i];
+  for (int nl = warp; nl < ntc; nl += nw) {
+    const int4 q = meta[nl];
+    if (!q.w || q.z == 0) continue;
+    const int2* hd = hs + hoff[nl];
+    int mv[4] = {0, 0, 0, 0};
+    int k = 0;
+#pragma unroll 1
+    for (; k + 4 <= q.z; k += 4) {
+      int2 e[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) e[kk] = hd[k + kk];
+      uint8_t v[4][4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          v[kk][i] = cr[i].x >= 0 ? __ldg(t.ti + cr[i].y + e[kk].x) : (uint8_t)(e[kk].y & 0xFF);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mv[i] += v[kk][i] != (uint8_t)(e[kk].y & 0xFF);
+    }
+#pragma unroll 1
+    for (; k < q.z; ++k) {
+      const int2 e = hd[k];
+      const uint8_t code = (uint8_t)(e.y & 0xFF);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (cr[i].x >= 0) mv[i] += (__ldg(t.ti + cr[i].y + e.x) != code);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Mt[(lane + 32 * i) * spm + nl] = (uint16_t)min(mv[i], 0xFFFF);
+  }
+}
+
+// Stages the hard-data lists of the chunk's items (columns c0 .. c0+ntc-1 of
+// N-tile ntile) in shared memory: hoff[nl] = first entry of item nl in hs.
+// Returns false (nothing staged) when they hold more than cap entries.
+// Needs a barrier before hs is read.
+__device__ __forceinline__ bool stage_hard_data(const WaveArgs& a, const int4* meta, int ntile,
+                                                int nt, int c0, int ntc, int* hoff, int2* hs,
+                                                int cap) {
+  int total = 0;
+  for (int i = 0; i < ntc; ++i) total += meta[c0 + i].w ? meta[c0 + i].z : 0;
+  if (total > cap) return false;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((int)threadIdx.x < ntc) {
+    int off = 0;
+    for (int i = 0; i < (int)threadIdx.x; ++i) off += meta[c0 + i].w ? meta[c0 + i].z : 0;
+    hoff[threadIdx.x] = off;
+  }
+  for (int nl = warp; nl < ntc; nl += nw) {
+    const int4 q = meta[c0 + nl];
+    if (!q.w || q.z == 0) continue;
+    int off = 0;
+    for (int i = 0; i < nl; ++i) off += meta[c0 + i].w ? meta[c0 + i].z : 0;
+    const int2* src = reinterpret_cast<const int2*>(
+        a.ev.base + (int64_t)(ntile * nt + c0 + nl) * a.ev.stride + a.ev.hd_off);
+    for (int k = lane; k < q.z; k += 32) hs[off + k] = __ldg(src + k);
+  }
+  return true;
+}
+
 constexpr int kScanBatch = 4;
 
 template <int MODE, int KL>

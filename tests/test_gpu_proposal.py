@@ -149,6 +149,69 @@ def test_tables_hold_every_window(ccw, ti):
     ti.attach_proposal(None)
 
 
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().float().numpy()
+
+
+def test_tables_equal_the_fp64_encoder_oracle(ccw, ti):
+    """Each table row is the encoder (FP64 oracle, BF16-rounded weights) of
+    the TI window of its candidate under its mask type."""
+    from oracle import encoder_oracle as E
+    net = ccw.Net(F, TJ, seed=4)
+    ti.attach_proposal(net, 64, 0.0)
+    tables = ti.export(4).float().cpu().numpy()
+    params = E.unpack(bf16_round(net.get(0)).astype(np.float64), F, TJ)
+    rng = np.random.default_rng(2)
+    for mtype in (1, 4, 5, 6, 9):
+        cand = rng.integers(0, ti.n_cand, 96).astype(np.int32)
+        types = np.full(96, mtype, np.int32)
+        x = ti.proposal_inputs(1, cand=torch.from_numpy(cand).cuda(),
+                               types=torch.from_numpy(types).cuda()).cpu().numpy()
+        ref, _ = E.forward(params, x.astype(np.float64))
+        got = tables[mtype, cand]
+        cos = (got * ref).sum(1) / np.linalg.norm(got, axis=1)
+        assert np.all(cos >= 0.998), (mtype, cos.min())
+        assert np.abs(got - ref).max() <= 0.03, mtype
+    assert not tables[0].any() and not tables[3].any()   # unused mask types
+    ti.attach_proposal(None)
+
+
+def test_nearest_windows_equal_a_numpy_ranking(ccw, ti):
+    """The selector's n_prop proposals are the top of a numpy ranking of the
+    same tables by dot product with the event's embedding (score descending,
+    candidate ascending), up to FP32 rounding at the cut; its gap is the
+    relative spread of their scores."""
+    net = ccw.Net(F, TJ, seed=6)
+    ti.attach_proposal(net, 64, 0.0)
+    tables = ti.export(4).float().cpu().numpy().astype(np.float64)
+    _, _, counts = ccw.simulate_groups(ti, [dict(grid=(300, 260), n_real=3)], topk=1, seed=8,
+                                       want_log=True, want_counts=True)[0]
+    c = counts.reshape(-1, F, TJ * TJ).contiguous()
+    prop, gap, typ = ti.proposal_query(c)
+    prop, gap, typ = prop.cpu().numpy(), gap.cpu().numpy(), typ.cpu().numpy()
+    x, _ = ti.proposal_inputs(0, counts=c)
+    e = net.embed(x, bf16=1).cpu().numpy().astype(np.float64)
+    eps = 1e-5
+    checked = 0
+    for i in range(len(typ)):
+        if gap[i] < 0:
+            continue
+        s = tables[typ[i]] @ e[i]
+        order = np.lexsort((np.arange(len(s)), -s))
+        cut = s[order[63]]
+        p = prop[i]
+        assert len(set(p.tolist())) == 64
+        assert np.all(s[p] >= cut - eps), i
+        must = np.nonzero(s > cut + eps)[0]
+        assert set(must.tolist()) <= set(p.tolist()), i
+        assert np.all(np.diff(s[p]) <= eps), i
+        ref_gap = (s[p[0]] - s[p[63]]) / max(abs(s[p[0]]), 1e-6)
+        assert abs(gap[i] - ref_gap) <= 1e-4, i
+        checked += 1
+    assert checked >= 0.8 * np.sum(typ > 0)
+    ti.attach_proposal(None)
+
+
 def run(ccw, ti, n_real, learned, seed=5, base=0, precision=0):
     return ccw.simulate_groups(ti, [dict(grid=GRID, n_real=n_real, real_base=base)], topk=1,
                                seed=seed, want_log=True, want_counts=True, learned=learned,
