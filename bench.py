@@ -3,10 +3,15 @@
 
 A step is one whole simulation call (data events, their Haar approximation,
 the masked CCF over every candidate, top-K, Philox draw, Inverse-DWT paste,
-for every patch of the raster path) on the workload named by --workload
-(default c2: 2D 3-facies TI 1000x1000, one 2000x2000 realization, template
-64, overlap 16, level 2, 400 hard data, top-5). Inputs are synthetic and
-seeded (workloads/configs.py).
+for every patch of the raster path) on the workload named by --workload.
+The default (c5: 256 realizations 512x512 of the 250x250 binary ribbon TI,
+template 48, overlap 12, level 2) times the plain full-CCF batched form and
+then the learned+batched form (the encoder is trained on the GPU first,
+outside the timed region) on the same batch: `value` is the learned form,
+`plain` the full search, with the pattern statistics of both ensembles as
+the equal-accuracy evidence. Other workloads (--workload c2: one 2000x2000
+3-facies realization with 400 hard data, top-5; c3, c4, t2_*) time one form.
+Inputs are synthetic and seeded (workloads/configs.py).
 
 Prints one JSON line. `value` is device-timed (CUDA events on the launching
 stream, inputs resident, L2 flushed by a 256 MiB write between steps);
@@ -15,9 +20,9 @@ copied in from pinned memory and the realization copied back inside the
 timed region). `--impl reference` times the CPU oracle instead, on a bounded
 sample of patches per step.
 
-Multi-GPU (torchrun): realizations are independent, so each rank simulates
-its own realizations with no exchange (weak scaling); the time is the max
-over ranks.
+Multi-GPU (torchrun, or --gpus N alone, which starts the ranks): realizations
+are independent, so each rank simulates its own realizations with no exchange
+(weak scaling); the time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -57,6 +62,10 @@ def tensor_peak_tflops():
     except Exception:
         return 1900.0, "fallback (1.9 PFLOP/s dense bf16)"
 
+# workloads whose default run times the learned proposal beside the plain
+# full search (the metric's comparison)
+LEARNED_COMPARE = ("c5",)
+
 WORKLOAD_TEXT = {
     "c1": "2D binary ribbon TI 250x250; 1 realization 250x250; T40 OR10 J1; no hard data; K=1",
     "c2": "2D 3-facies channel/lens TI 1000x1000; 1 realization 2000x2000; T64 OR16 J2; "
@@ -83,7 +92,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--plain-only", action="store_true",
+                    help="on the learned-proposal workload, time the plain full-CCF form only")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -493,7 +504,9 @@ def ours_line(args, world, m):
     return line
 
 
-def run_ours(args, rank, world, local_rank):
+def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
+    """Measures one form of the simulation (learned proposal on or off) and
+    returns (JSON line or None off rank 0, the realizations when `keep`)."""
     import torch
     import torch.distributed as dist
 
@@ -521,8 +534,9 @@ def run_ours(args, rank, world, local_rank):
     bench_prec, bench_tile = configs.bench_tile(args.workload)
     precision = args.precision if args.precision is not None else bench_prec
     cells_per_step = sum(gr["n_real"] * cells_of(gr["grid"]) for gr in groups)
+    learned = args.learned if learned is None else learned
     learned_info = None
-    if args.learned:
+    if learned:
         learned_info = train_proposal(args, g, w, groups[0]["grid"])
     # CCF tiling: the autotuner times every accepted (precision, tile) pair on
     # this batch (outside the timed region); results do not depend on it
@@ -562,14 +576,14 @@ def run_ours(args, rank, world, local_rank):
             ccw.simulate(g, gr["grid"], n_real=gr["n_real"], topk=w["K"], seed=w["seed"],
                          hd_cells=hd_dev[0][0], hd_vals=hd_dev[0][1],
                          real_base=gr["real_base"], out=outs[0], precision=precision,
-                         learned=1 if args.learned else 0, ccf_tile=tile,
+                         learned=1 if learned else 0, ccf_tile=tile,
                          vt_ext=args.vt_ext, boundary_cut=int(args.boundary_cut))
             return outs
         res = ccw.simulate_groups(
             g, [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
                      hd_cells=h[0], hd_vals=h[1]) for gr, h in zip(groups, hd_dev)],
             topk=w["K"], seed=w["seed"], precision=precision,
-            learned=1 if args.learned else 0, ccf_tile=tile, vt_ext=args.vt_ext,
+            learned=1 if learned else 0, ccf_tile=tile, vt_ext=args.vt_ext,
             boundary_cut=int(args.boundary_cut))
         return [r[0] for r in res]
 
@@ -661,7 +675,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms, e2e_ms_max, kern_ms_max = max_over_ranks([total_ms, e2e_ms or 0.0, kern_ms], world,
                                                        "cuda")
     if rank != 0:
-        return
+        return None, (outs if keep else None)
     line = ours_line(args, world, dict(
         total_ms=total_ms, kern_ms=kern_ms, instr_ms=instr_ms, macs=macs, cand_evals=cand_evals,
         n_launch=n_launch, launches=launches, clocks=clk, precision=precision, tile=tile,
@@ -673,7 +687,7 @@ def run_ours(args, rank, world, local_rank):
         T=w["T"], Tj=w["T"] // (2 ** w["J"]), F=w["F"],
         wavefronts=max(wavefronts_of(gr["grid"], w["T"], w["O"]) for gr in groups),
         has_hd=any(gr["hd_host"] is not None for gr in groups)))
-    if not args.no_cpu_baseline and world == 1:
+    if cpu and not args.no_cpu_baseline and world == 1:
         w0 = dict(w, grid=groups[0]["grid"], hd=groups[0]["hd_host"])
         n, dt, ce = oracle_sample(w0, args.cpu_seconds)
         grid = groups[0]["grid"]
@@ -694,7 +708,58 @@ def run_ours(args, rank, world, local_rank):
                               f"one process per host core, {wall:.1f} s wall"}
             except Exception as e:   # the single-thread figure above stands
                 line["cpu_baseline"]["parallel"] = {"unavailable": f"{type(e).__name__}: {e}"}
-    print(json.dumps(line), flush=True)
+    return line, (outs if keep else None)
+
+
+def ensemble_statistics(outs, ti, F):
+    """Pattern-reproduction statistics of an ensemble of 2D realizations on
+    the GPU (Sec. 5.2-5.3): facies-1 proportion, E-W indicator variogram and
+    probability of connection of facies 1, 4 x 4 pattern histograms at full
+    and half resolution."""
+    import torch
+
+    from paper_2404_00441_gb300 import evaluate as ev
+    reals = torch.cat([o.reshape((-1,) + tuple(o.shape[-2:])) for o in outs])
+    lags = (1, 2, 4, 8, 16, 32)
+    plags = (8, 32, 64)
+    return dict(
+        n=int(reals.shape[0]),
+        prop=ev.proportions(reals, F).numpy()[:, 1],
+        vario=ev.variogram(reals, 1, 0, lags).numpy(),
+        conn=ev.connection_probability(reals, 1, plags, 0),
+        hist=[ev.pattern_histogram(reals, F, 4, d) for d in (1, 2)],
+        lags=lags, plags=plags)
+
+
+def compare_ensembles(a, b, ti_stats):
+    """Equal-accuracy evidence between two ensembles (means with 95 % half
+    widths, and the Jensen-Shannon divergence of their pattern histograms;
+    the same divergence of each against the TI)."""
+    import math
+
+    import numpy as np
+
+    from paper_2404_00441_gb300 import evaluate as ev
+
+    def ci(x):
+        x = np.asarray(x, np.float64)
+        return [float(np.nanmean(x, 0).round(6)) if x.ndim == 1 else
+                [round(float(v), 6) for v in np.nanmean(x, 0)],
+                float((1.96 * np.nanstd(x, 0, ddof=1) / math.sqrt(len(x))).max())]
+    out = {"realizations": [a["n"], b["n"]]}
+    for k in ("prop", "vario", "conn"):
+        out[k] = {"plain": ci(a[k]), "learned": ci(b[k])}
+    out["variogram_lags"] = list(a["lags"])
+    out["connection_lags"] = list(a["plags"])
+    out["js_learned_vs_plain"] = [round(ev.js_divergence(x, y), 5)
+                                  for x, y in zip(a["hist"], b["hist"])]
+    out["js_vs_ti"] = {"plain": [round(ev.js_divergence(x, y), 5)
+                                 for x, y in zip(a["hist"], ti_stats["hist"])],
+                       "learned": [round(ev.js_divergence(x, y), 5)
+                                   for x, y in zip(b["hist"], ti_stats["hist"])]}
+    out["note"] = ("means over the ensembles with 95 % half widths; JS divergence of 4x4 "
+                   "pattern histograms at down 1 and 2")
+    return out
 
 
 def rank_command(argv, n):
@@ -726,7 +791,31 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload in LEARNED_COMPARE and not args.plain_only and not args.learned:
+        # the metric's comparison: the plain full-CCF batched form, then the
+        # learned+batched form of the same batch (value = the latter)
+        plain, plain_outs = run_ours(args, rank, world, local_rank, learned=False, cpu=False,
+                                     keep=True)
+        line, outs = run_ours(args, rank, world, local_rank, learned=True, cpu=True, keep=True)
+        if rank == 0:
+            import torch
+            from workloads import configs
+            w = configs.workload(args.workload)
+            ti_t = torch.from_numpy(w["ti"]).cuda()[None]
+            line["plain"] = {k: plain[k] for k in ("value", "ms_per_step", "cand_evals_per_s",
+                                                   "e2e", "roofline", "gpu_launches", "config")
+                             if k in plain}
+            line["learned_vs_plain"] = line["value"] / plain["value"]
+            line["accuracy"] = compare_ensembles(
+                ensemble_statistics(plain_outs, w["ti"], w["F"]),
+                ensemble_statistics(outs, w["ti"], w["F"]),
+                ensemble_statistics([ti_t], w["ti"], w["F"]))
+            line["metric"] = "simulated cells/s (learned+batched; plain full-CCF in 'plain')"
+            print(json.dumps(line), flush=True)
+    else:
+        line, _ = run_ours(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -107,7 +107,12 @@ typedef struct {
                           stages (always so in 3D; K <= 8), bit 26: three
                           stages instead of two, bit 29: four (not with bit
                           26), bits 27-28 = v: stages of Tj / 2^v template
-                          rows (v <= 2). Bit 30 alone among bits 24-31
+                          rows (v <= 2). Bits 20-22 = L - 1 (any
+                          precision, not with the learned proposal or bit
+                          30): the realizations are split into L lanes
+                          whose wavefront chains run concurrently on
+                          separate streams of the call's graph (results
+                          unchanged). Bit 30 alone among bits 24-31
                           (2D, K <= 8, no vt_ext, boundary_cut or learned):
                           every wavefront of the call in one cooperative
                           kernel, nt in {16, 32, 64, 128, 256} items per
@@ -458,6 +463,21 @@ int ccw_eval_variogram(const uint8_t* real_dev, int32_t n_real, const int32_t di
 int ccw_eval_patterns(const uint8_t* real_dev, int32_t n_real, const int32_t dims[3],
                       int32_t n_facies, int32_t down, int32_t w, uint8_t* scratch_dev,
                       uint32_t* hist_dev, void* stream);
+/*
+ * ccw_eval_connectivity -- the probability of connection of Sec. 5.3 as two
+ *   exact counts per lag: pairs_dev uint64 [n_real][n_lags][2] = {cell pairs
+ *   (c, c + h e_axis) with both cells of `facies`, those of them in one
+ *   4-connected component of `facies`}, h = lags_dev[l] (int32, device,
+ *   >= 1); axis 0 = x (E-W), 1 = y (N-S); 2D only (dims[2] = 1, at most
+ *   2^31 - 1 cells). The probability is the second count over the first.
+ *   labels_dev: int32 scratch of n_real * (dims[0] * dims[1] + 1) entries
+ *   (component labels, then one flag per realization). The components come
+ *   from a union-find labelling with capped loops; a realization whose
+ *   labelling hit the cap (never expected) reports 2^64 - 1 counts.
+ */
+int ccw_eval_connectivity(const uint8_t* real_dev, int32_t n_real, const int32_t dims[3],
+                          int32_t facies, int32_t axis, const int32_t* lags_dev, int32_t n_lags,
+                          int32_t* labels_dev, uint64_t* pairs_dev, void* stream);
 const char* ccw_eval_last_error(void);
 
 /* ccw_last_error -- text of the last failure on the calling host thread. */

@@ -26,6 +26,9 @@ def _cache_path() -> str:
                         "autotune.json")
 
 
+LANES = (2, 3, 4, 6, 8)   # realization lanes tried on the best tiling
+
+
 def candidates(ti: "ccw.TI", precisions=(0, 1, 2)):
     """(precision, ccf_tile) pairs the library accepts for this TI."""
     out = []
@@ -71,9 +74,11 @@ def _time_call(fn, reps):
 
 def tune(ti: "ccw.TI", groups, topk=1, seed=0, score_mode=0, learned=0, precisions=(0, 1, 2),
          reps=2, use_cache=True, vt_ext=0, boundary_cut=0):
-    """Times every candidate tiling on simulate_groups(ti, groups, ...) and
-    returns (precision, ccf_tile, {"p<precision>/<tile>": ms}). Candidates the
-    library refuses (shared memory, exactness bounds) are skipped."""
+    """Times every candidate tiling on simulate_groups(ti, groups, ...), then
+    the fastest one with the realizations split into 2-8 concurrent lanes,
+    and returns (precision, ccf_tile, {"p<precision>/<tile>": ms}).
+    Candidates the library refuses (shared memory, exactness bounds) are
+    skipped."""
     key = _key(ti, groups, topk, score_mode, learned, precisions, vt_ext, boundary_cut)
     path = _cache_path()
     cache = {}
@@ -103,6 +108,27 @@ def tune(ti: "ccw.TI", groups, topk=1, seed=0, score_mode=0, learned=0, precisio
             best = (prec, tile, ms)
     if best is None:
         raise ccw.CCWError("no tiling accepted for this batch")
+    # second stage: the best tiling with the realizations split into lanes
+    # whose wavefront chains run concurrently (ccf_tile bits 20-22)
+    total_real = sum(int(g["n_real"]) for g in groups)
+    if not learned and not (best[1] >> 30) & 1:
+        for lanes in LANES:
+            if lanes > total_real:
+                break
+            prec, tile = best[0], best[1] | ((lanes - 1) << 20)
+
+            def call():
+                ccw.simulate_groups(ti, groups, topk=topk, seed=seed, score_mode=score_mode,
+                                    precision=prec, learned=learned, ccf_tile=tile,
+                                    vt_ext=vt_ext, boundary_cut=boundary_cut)
+            try:
+                call()
+            except ccw.CCWError:
+                continue
+            ms = _time_call(call, reps)
+            times[f"p{prec}/{tile:#x}"] = ms
+            if ms < best[2]:
+                best = (prec, tile, ms)
     if use_cache:
         cache[key] = {"precision": best[0], "ccf_tile": best[1], "times": times}
         try:

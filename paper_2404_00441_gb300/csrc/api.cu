@@ -175,6 +175,22 @@ struct SimPlan {
   unsigned long long* phase_ns = nullptr;   // persistent kernel: profiled phase times
   cudaEvent_t pev[2] = {nullptr, nullptr};  // persistent kernel: profiled launch
   EvDev evl;
+  // Realization lanes: the realizations are split into groups whose
+  // wavefront chains are captured on separate streams of the same graph, so
+  // that the kernels of different lanes run at the same time. Lane 0 uses
+  // the buffers above; every lane has its own schedule (offsets into
+  // `items`) and scratch.
+  struct Lane {
+    std::vector<int64_t> wave_off;   // [n_waves + 1]
+    int max_items = 0;
+    void* ev = nullptr;
+    void* part = nullptr;
+    void* bmat = nullptr;
+    cudaStream_t st = nullptr;       // capture stream (lanes >= 1)
+    cudaEvent_t done = nullptr;      // end of the lane's chain (lanes >= 1)
+  };
+  std::vector<Lane> lanes;
+  int64_t launches_per_call = 0;
   void* cp = nullptr;   // CcfPlan (defined with the kernels' host helpers)
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [profiling]
@@ -189,6 +205,13 @@ struct SimPlan {
         cudaEventDestroy(pr.second);
       }
     if (cap) cudaStreamDestroy(cap);
+    for (size_t l = 1; l < lanes.size(); ++l) {
+      cudaFree(lanes[l].ev);
+      cudaFree(lanes[l].part);
+      cudaFree(lanes[l].bmat);
+      if (lanes[l].st) cudaStreamDestroy(lanes[l].st);
+      if (lanes[l].done) cudaEventDestroy(lanes[l].done);
+    }
     for (auto& e : pev)
       if (e) cudaEventDestroy(e);
     cudaFree(wave_off_d);
@@ -428,8 +451,14 @@ void SimPlan::release_cp() { delete static_cast<CcfPlan*>(cp); }
 
 namespace {
 
+// ccf_tile bits 20-22: realization lanes - 1 (the graph path); the other
+// bits give the CCF tiling.
+constexpr int kTileLaneMask = 7 << 20;
+int tile_lanes(int hint) { return ((hint >> 20) & 7) + 1; }
+
 // Valid values of the `ccf_tile` hint (0 = the library's heuristic).
 bool valid_tile_hint(const ccw_ti* t, int precision, int hint) {
+  hint &= ~kTileLaneMask;
   if (hint == 0) return true;
   if (precision == 0)
     return t->ndim == 2 ? (hint == 1 || hint == 2 || hint == 4 || hint == 8)
@@ -1161,42 +1190,62 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
     pl->n_waves = std::max(pl->n_waves,
                            (g.np[0] - 1) + 2 * (g.np[1] - 1) + 4 * (g.np[2] - 1) + 1);
   }
+  // realization lanes (ccf_tile bits 20-22: lanes - 1); one lane for the
+  // learned proposal and the one-kernel form
+  int n_lanes = tile_lanes(p->ccf_tile);
+  int64_t total_real = 0;
+  for (int i = 0; i < n_groups; ++i) total_real += pl->groups[i].n_real;
+  if (p->learned || tile_is_persist(p->precision & 3, p->ccf_tile)) n_lanes = 1;
+  n_lanes = (int)std::max<int64_t>(1, std::min<int64_t>(n_lanes, total_real));
   // wavefront schedule: wave(p) = ix + 2 iy + 4 iz over the lattice index of
-  // every group; the items of one wave of all groups share the launches
-  std::vector<std::vector<int4>> waves(pl->n_waves);
+  // every group; the items of one wave of all groups (of one lane) share the
+  // launches; lane l takes slots [l n / L, (l + 1) n / L) of every group
+  std::vector<std::vector<std::vector<int4>>> waves(
+      n_lanes, std::vector<std::vector<int4>>(pl->n_waves));
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
-    for (int r = 0; r < g.n_real; ++r)
+    for (int r = 0; r < g.n_real; ++r) {
+      const int lane = (int)((int64_t)r * n_lanes / g.n_real);
       for (int64_t pp = 0; pp < g.n_patches; ++pp) {
         const int ix = (int)(pp % g.np[0]), iy = (int)((pp / g.np[0]) % g.np[1]),
                   iz = (int)(pp / ((int64_t)g.np[0] * g.np[1]));
-        waves[ix + 2 * iy + 4 * iz].push_back(make_int4(i, r, (int)pp, 0));
+        waves[lane][ix + 2 * iy + 4 * iz].push_back(make_int4(i, r, (int)pp, 0));
       }
+    }
   }
   std::vector<int4> items;
-  pl->wave_off.assign(pl->n_waves + 1, 0);
+  pl->lanes.resize(n_lanes);
   pl->max_items = 0;
-  for (int w = 0; w < pl->n_waves; ++w) {
-    pl->wave_off[w] = (int64_t)items.size();
-    items.insert(items.end(), waves[w].begin(), waves[w].end());
-    pl->max_items = std::max<int>(pl->max_items, (int)waves[w].size());
+  pl->launches_per_call = 0;
+  for (int l = 0; l < n_lanes; ++l) {
+    SimPlan::Lane& ln = pl->lanes[l];
+    ln.wave_off.assign(pl->n_waves + 1, 0);
+    for (int w = 0; w < pl->n_waves; ++w) {
+      ln.wave_off[w] = (int64_t)items.size();
+      items.insert(items.end(), waves[l][w].begin(), waves[l][w].end());
+      ln.max_items = std::max<int>(ln.max_items, (int)waves[l][w].size());
+      pl->launches_per_call += (p->learned ? 11 : 3) * ((waves[l][w].size() + 65534) / 65535);
+    }
+    ln.wave_off[pl->n_waves] = (int64_t)items.size();
+    pl->max_items = std::max(pl->max_items, ln.max_items);
   }
-  pl->wave_off[pl->n_waves] = (int64_t)items.size();
+  pl->wave_off = pl->lanes[0].wave_off;
   const int nch = p->score_mode == 0 ? t->F - 1 : 1;
   event_layout(nch, t->rows, t->TjP, hd_capacity(t, p->vt_ext), t->F, t->rows * t->Tj, pl->evl);
   CcfPlan* cp = new CcfPlan();
   pl->cp = cp;
   const int fmt = p->precision & 3;   // the format (the exactness flag was checked)
-  if (tile_is_persist(fmt, p->ccf_tile)) {
+  const int tiling = p->ccf_tile & ~kTileLaneMask;
+  if (tile_is_persist(fmt, tiling)) {
     cp->precision = fmt;
-    if (int rc = plan_persist(t, nch, pl->K, pl->max_items, p->ccf_tile, p->vt_ext,
+    if (int rc = plan_persist(t, nch, pl->K, pl->max_items, tiling, p->vt_ext,
                               p->boundary_cut, p->learned, *cp)) {
       delete pl;
       return rc;
     }
     cp->ev_bytes = (int64_t)pl->max_items * pl->evl.stride;
   } else {
-    plan_ccf(t, fmt, nch, pl->K, pl->max_items, pl->evl, *cp, p->ccf_tile);
+    plan_ccf(t, fmt, nch, pl->K, pl->max_items, pl->evl, *cp, tiling);
   }
   if (!cp->persist && cp->smem > 220 * 1024) {
     const int need = cp->smem;   // the plan owns cp
@@ -1236,6 +1285,20 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
     delete pl;
     return fail(CCW_ENOMEM, "simulation workspace: %s", cudaGetErrorString(e));
   }
+  pl->lanes[0].ev = pl->ev;
+  pl->lanes[0].part = pl->part;
+  pl->lanes[0].bmat = pl->bmat;
+  for (size_t l = 1; l < pl->lanes.size(); ++l) {
+    SimPlan::Lane& ln = pl->lanes[l];
+    if ((e = cudaMalloc(&ln.ev, (size_t)cp->ev_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&ln.part, (size_t)cp->part_bytes)) != cudaSuccess ||
+        (cp->bmat_bytes && (e = cudaMalloc(&ln.bmat, (size_t)cp->bmat_bytes)) != cudaSuccess) ||
+        (e = cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming)) != cudaSuccess) {
+      delete pl;
+      return fail(CCW_ENOMEM, "simulation lane workspace: %s", cudaGetErrorString(e));
+    }
+  }
   pl->evl.base = (unsigned char*)pl->ev;
   if ((cp->persist &&
        (e = cudaMemcpy(pl->wave_off_d, pl->wave_off.data(), sizeof(int64_t) * (pl->n_waves + 1),
@@ -1252,15 +1315,19 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
 
 // Launch phases A, B and C of every wave on `st` (while `st` is being
 // captured into the plan's graph).
-int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
+// Launch phases A, B and C of every wave of lane `lane` on `st` (while `st`
+// is being captured into the plan's graph); `pe` counts the profiled steps.
+int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, size_t& pe) {
+  const SimPlan::Lane& ln = pl->lanes[lane];
   WaveArgs a;
   fill_ti(t, pl->score_mode, a);
   a.ev = pl->evl;
+  a.ev.base = (unsigned char*)ln.ev;
   a.groups = pl->dgroups;
   a.S = t->T - t->O;
   a.call = pl->call;
   a.K = pl->K;
-  a.part = (unsigned long long*)pl->part;
+  a.part = (unsigned long long*)ln.part;
   a.vt_ext = pl->vt_ext;
   a.cut = pl->cut;
   if (pl->learned) {
@@ -1275,13 +1342,13 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, cudaStream_t st) {
     a.enc_act = (float*)pl->enc_act;
   }
   const CcfPlan& cp = *static_cast<const CcfPlan*>(pl->cp);
-  size_t pe = 0;
   for (int w = 0; w < pl->n_waves; ++w) {
-    for (int64_t i0 = pl->wave_off[w]; i0 < pl->wave_off[w + 1]; i0 += 65535) {
+    for (int64_t i0 = ln.wave_off[w]; i0 < ln.wave_off[w + 1]; i0 += 65535) {
       WaveArgs c = a;
       c.items = (const int4*)pl->items + i0;
-      c.n_items = (int)std::min<int64_t>(65535, pl->wave_off[w + 1] - i0);
-      apply_ccf(t, cp, pl->bmat, c);
+      c.n_items = (int)std::min<int64_t>(65535, ln.wave_off[w + 1] - i0);
+      if (c.n_items <= 0) continue;
+      apply_ccf(t, cp, ln.bmat, c);
       if (prof) {
         if (pe >= pl->prof_bounds.size()) {
           cudaEvent_t e0, e1;
@@ -1326,8 +1393,26 @@ int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-  int rc = launch_waves(t, pl, prof, pl->cap);
+  // lanes >= 1 fork from the capture stream and join it at the end
+  int rc = CCW_OK;
+  size_t pe = 0;
+  cudaEvent_t fork = nullptr;
+  if (pl->lanes.size() > 1) {
+    if ((e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(fork, pl->cap)) != cudaSuccess)
+      rc = cuda_fail(e, "capture fork");
+    for (size_t l = 1; l < pl->lanes.size() && !rc; ++l)
+      if ((e = cudaStreamWaitEvent(pl->lanes[l].st, fork, 0)) != cudaSuccess)
+        rc = cuda_fail(e, "capture fork");
+  }
+  for (size_t l = 0; l < pl->lanes.size() && !rc; ++l)
+    rc = launch_waves(t, pl, prof, (int)l, l == 0 ? pl->cap : pl->lanes[l].st, pe);
+  for (size_t l = 1; l < pl->lanes.size() && !rc; ++l)
+    if ((e = cudaEventRecord(pl->lanes[l].done, pl->lanes[l].st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(pl->cap, pl->lanes[l].done, 0)) != cudaSuccess)
+      rc = cuda_fail(e, "capture join");
   e = cudaStreamEndCapture(pl->cap, &graph);
+  if (fork) cudaEventDestroy(fork);
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
@@ -1499,11 +1584,7 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
       if (int rc = capture_waves(t, pl, prof)) return rc;
     if ((e = cudaGraphLaunch(pl->exec[gi], st)) != cudaSuccess)
       return cuda_fail(e, "graph launch");
-    int64_t wave_launches = 0;
-    for (int w = 0; w < pl->n_waves; ++w)
-      wave_launches += (pl->learned ? 11 : 3) *
-                       ((pl->wave_off[w + 1] - pl->wave_off[w] + 65534) / 65535);
-    g_launches += wave_launches;
+    g_launches += pl->launches_per_call;
   }
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];

@@ -117,6 +117,122 @@ int eval_fail(int code, const char* msg) {
 dim3 eval_grid(int64_t n, int n_real) {
   return dim3((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)n_real);
 }
+// ---------------------------------------------------------------------------
+// Probability of connection (Sec. 5.3): the 4-connected components of the
+// cells of facies f by union-find over cell labels. Every label points to a
+// smaller-or-equal index of its component (roots point to themselves), so
+// parent chains only descend and every find ends; a union links the larger
+// root under the smaller one with atomicMin and retries from the new parent
+// when another thread got there first. Loops carry an iteration cap as a
+// safety net; a realization whose labelling hit it reports counts of
+// 2^64 - 1.
+// ---------------------------------------------------------------------------
+constexpr int kUfCap = 1 << 24;
+
+__device__ __forceinline__ int uf_find(const int* L, int x) {
+  for (int i = 0; i < kUfCap; ++i) {
+    const int p = *(volatile const int*)(L + x);
+    if (p == x) return x;
+    x = p;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ bool uf_union(int* L, int a, int b) {
+  for (int it = 0; it < kUfCap; ++it) {
+    a = uf_find(L, a);
+    b = uf_find(L, b);
+    if (a < 0 || b < 0) return false;
+    if (a == b) return true;
+    if (a < b) {
+      const int tmp = a;
+      a = b;
+      b = tmp;
+    }
+    const int old = atomicMin(L + a, b);
+    if (old == a) return true;   // a was still a root: now under b
+    a = old;
+  }
+  return false;
+}
+
+__global__ void k_cc_init(const uint8_t* __restrict__ real, int64_t vol, int f, int* lab) {
+  const int64_t base = (int64_t)blockIdx.y * vol;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vol;
+       i += (int64_t)gridDim.x * blockDim.x)
+    lab[base + i] = real[base + i] == f ? (int)i : -1;
+}
+
+__global__ void k_cc_merge(const uint8_t* __restrict__ real, int nx, int ny, int f, int* lab,
+                           int* fail) {
+  const int64_t vol = (int64_t)nx * ny;
+  const uint8_t* rr = real + (int64_t)blockIdx.y * vol;
+  int* L = lab + (int64_t)blockIdx.y * vol;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vol;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (rr[i] != f) continue;
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    bool ok = true;
+    if (x > 0 && rr[i - 1] == f) ok &= uf_union(L, (int)i, (int)i - 1);
+    if (y > 0 && rr[i - nx] == f) ok &= uf_union(L, (int)i, (int)(i - nx));
+    if (!ok) atomicOr(fail + blockIdx.y, 1);
+  }
+}
+
+__global__ void k_cc_flatten(int64_t vol, int* lab, int* fail) {
+  int* L = lab + (int64_t)blockIdx.y * vol;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vol;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (L[i] < 0) continue;
+    const int r = uf_find(L, (int)i);
+    if (r < 0) atomicOr(fail + blockIdx.y, 1);
+    else L[i] = r;
+  }
+}
+
+// pairs[r][l] = {cell pairs (c, c + h e_axis) both of facies f, of them in
+// one component}; per-block counters in shared memory, then global.
+__global__ void k_cc_pairs(const int* __restrict__ lab, int nx, int ny, int axis,
+                           const int* __restrict__ lags, int n_lags,
+                           unsigned long long* pairs) {
+  extern __shared__ unsigned int cnt[];   // [n_lags][2]
+  for (int i = threadIdx.x; i < 2 * n_lags; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  const int64_t vol = (int64_t)nx * ny;
+  const int* L = lab + (int64_t)blockIdx.y * vol;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vol;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int li = L[i];
+    if (li < 0) continue;
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    for (int l = 0; l < n_lags; ++l) {
+      const int h = lags[l];
+      int64_t j;
+      if (axis == 0) {
+        if (x + h >= nx) continue;
+        j = i + h;
+      } else {
+        if (y + h >= ny) continue;
+        j = i + (int64_t)h * nx;
+      }
+      const int lj = L[j];
+      if (lj < 0) continue;
+      atomicAdd(&cnt[2 * l], 1u);
+      if (lj == li) atomicAdd(&cnt[2 * l + 1], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * n_lags; i += blockDim.x)
+    if (cnt[i]) atomicAdd(pairs + (int64_t)blockIdx.y * 2 * n_lags + i, (unsigned long long)cnt[i]);
+}
+
+__global__ void k_cc_mark_failed(const int* fail, int n_lags, unsigned long long* pairs) {
+  const int r = blockIdx.x;
+  if (!fail[r]) return;
+  for (int i = threadIdx.x; i < 2 * n_lags; i += blockDim.x)
+    pairs[(int64_t)r * 2 * n_lags + i] = ~0ull;
+}
+
 }  // namespace
 
 extern "C" {
@@ -179,6 +295,36 @@ int ccw_eval_patterns(const uint8_t* real_dev, int32_t n_real, const int32_t dim
   }
   k_eval_patterns<<<eval_grid((int64_t)mx * my, n_real), 256, 0, st>>>(src, mx, my, w, n_facies,
                                                                        hist_dev);
+  return cudaGetLastError() == cudaSuccess ? CCW_OK : eval_fail(CCW_ECUDA, "kernel launch");
+}
+
+int ccw_eval_connectivity(const uint8_t* real_dev, int32_t n_real, const int32_t dims[3],
+                          int32_t facies, int32_t axis, const int32_t* lags_dev, int32_t n_lags,
+                          int32_t* labels_dev, uint64_t* pairs_dev, void* stream) {
+  if (!real_dev || !dims || !labels_dev || !pairs_dev || (n_lags > 0 && !lags_dev))
+    return eval_fail(CCW_EINVAL, "NULL argument");
+  if (dims[2] != 1) return eval_fail(CCW_EINVAL, "the probability of connection is 2D");
+  if (n_real < 1 || n_real > 65535 || axis < 0 || axis > 1 || n_lags < 0 || n_lags > 4096)
+    return eval_fail(CCW_EINVAL, "bad n_real, axis or n_lags");
+  const int64_t vol = (int64_t)dims[0] * dims[1];
+  if (dims[0] <= 0 || dims[1] <= 0 || vol >= ((int64_t)1 << 31))
+    return eval_fail(CCW_EINVAL, "bad dims (at most 2^31 - 1 cells)");
+  if (n_lags == 0) return CCW_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // one give-up flag per realization, in the scratch after the labels
+  int* fail = labels_dev + (int64_t)n_real * vol;
+  if (cudaMemsetAsync(pairs_dev, 0, sizeof(uint64_t) * 2 * n_lags * n_real, st) != cudaSuccess ||
+      cudaMemsetAsync(fail, 0, sizeof(int) * n_real, st) != cudaSuccess)
+    return eval_fail(CCW_ECUDA, "memset");
+  const dim3 grid = eval_grid(vol, n_real);
+  k_cc_init<<<grid, 256, 0, st>>>(real_dev, vol, facies, labels_dev);
+  k_cc_merge<<<grid, 256, 0, st>>>(real_dev, dims[0], dims[1], facies, labels_dev, fail);
+  k_cc_flatten<<<grid, 256, 0, st>>>(vol, labels_dev, fail);
+  k_cc_pairs<<<grid, 256, sizeof(unsigned int) * 2 * n_lags, st>>>(
+      labels_dev, dims[0], dims[1], axis, lags_dev, n_lags,
+      reinterpret_cast<unsigned long long*>(pairs_dev));
+  k_cc_mark_failed<<<n_real, 256, 0, st>>>(fail, n_lags,
+                                          reinterpret_cast<unsigned long long*>(pairs_dev));
   return cudaGetLastError() == cudaSuccess ? CCW_OK : eval_fail(CCW_ECUDA, "kernel launch");
 }
 

@@ -176,18 +176,20 @@ __device__ void p_event(const WaveArgs& a, int64_t gidx, int wi, const Grp& g, i
   int my_known = 0, my_const = 0, my_mask = 0, bad = 0;
   const bool words = s == 4 && ((it.o[0] | it.Gp[0]) & 3) == 0;
   // facies counts of block u -> shared memory and this thread's sums
+  // (indices into cf stay compile-time constants: cf lives in registers)
   auto account = [&](int u, const int (&cf)[8]) {
-    int c = 0;
+    int c = 0, last = 0;
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
       if (f >= t.F) break;
       counts[f * ncells + u] = cf[f];
       c += cf[f];
+      last = cf[f];
     }
     if (!c) return;
     my_known += c;
     ++my_mask;
-    if (t.score_mode == 0) my_const += t.sd * cf[(t.F - 1) & 7];
+    if (t.score_mode == 0) my_const += t.sd * last;
   };
   if (words) {
     // one 32-bit word of 4 codes per block row (SWAR facies counts); the
@@ -283,7 +285,8 @@ __device__ void p_event(const WaveArgs& a, int64_t gidx, int wi, const Grp& g, i
           }
           if (v != CCW_UNKNOWN) {
             if (v >= t.F) bad |= kStatusBadCode;
-            else ++cf[v & 7];
+#pragma unroll
+            for (int f = 0; f < 8; ++f) cf[f] += (v == f);
           }
         }
       }

@@ -1,6 +1,7 @@
 """Pattern-reproduction statistics of realizations on the GPU (libccw's
-``ccw_eval_*`` kernels): facies proportions, indicator variograms and w x w
-pattern histograms at mode-downsampled resolutions, with the Jensen-Shannon
+``ccw_eval_*`` kernels): facies proportions, indicator variograms, the
+probability of connection and w x w pattern histograms at mode-downsampled
+resolutions, with the Jensen-Shannon
 divergence between two histograms (computed on the host from the counts).
 Used to compare ensembles (e.g. the learned proposal vs the full search) and
 an ensemble with its training image, as in the validation of Sec. 5.2-5.3.
@@ -22,6 +23,7 @@ def _lib():
         lib.ccw_eval_proportions.argtypes = [P, i32, P, i32, P, P]
         lib.ccw_eval_variogram.argtypes = [P, i32, P, i32, i32, P, i32, P, P]
         lib.ccw_eval_patterns.argtypes = [P, i32, P, i32, i32, i32, P, P, P]
+        lib.ccw_eval_connectivity.argtypes = [P, i32, P, i32, i32, P, i32, P, P, P]
         lib.ccw_eval_last_error.restype = C.c_char_p
         lib._eval_ready = True
     return lib
@@ -82,6 +84,32 @@ def pattern_histogram(reals: torch.Tensor, n_facies: int, w: int = 4, down: int 
                                  ccw._ptr(scratch) if scratch is not None else None,
                                  ccw._ptr(hist), ccw._stream(stream)))
     return hist.to(torch.int64)
+
+
+def connectivity_counts(reals: torch.Tensor, facies: int, lags, axis: int = 0,
+                        stream=None) -> torch.Tensor:
+    """``ccw_eval_connectivity``: int64 [n_real, len(lags), 2] = (cell pairs
+    (c, c + h e_axis) both of `facies`, those in one 4-connected component
+    of it) of 2D realizations; axis 0 = x (E-W), 1 = y (N-S)."""
+    lib = _lib()
+    n, ny, nx = reals.shape
+    lg = torch.tensor(list(lags), dtype=torch.int32, device=reals.device)
+    labels = torch.empty((n * (nx * ny + 1),), dtype=torch.int32, device=reals.device)
+    out = torch.empty((n, len(lags), 2), dtype=torch.int64, device=reals.device)
+    _check(lib.ccw_eval_connectivity(ccw._ptr(reals), n, _dims(reals), facies, axis,
+                                     ccw._ptr(lg), len(lags), ccw._ptr(labels), ccw._ptr(out),
+                                     ccw._stream(stream)))
+    return out
+
+
+def connection_probability(reals: torch.Tensor, facies: int, lags, axis: int = 0,
+                           stream=None) -> np.ndarray:
+    """Probability of connection (Sec. 5.3) float64 [n_real, len(lags)] of
+    `facies` along axis 0 = x (E-W) or 1 = y (N-S): connected pairs over
+    pairs, NaN where no pair exists."""
+    c = connectivity_counts(reals, facies, lags, axis, stream).cpu().numpy()
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(c[..., 0] > 0, c[..., 1] / np.maximum(c[..., 0], 1), np.nan)
 
 
 def js_divergence(h1: torch.Tensor, h2: torch.Tensor) -> float:

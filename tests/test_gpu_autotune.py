@@ -59,7 +59,7 @@ def test_all_tilings_agree_and_tuner_picks_one(ccw, ndim, tmp_path, monkeypatch)
     assert ran >= 3
     prec, tile, times = autotune.tune(g, groups, topk=K, seed=7,
                                       precisions=(0, 1, 2) if ndim == 2 else (0,))
-    assert (prec, tile) in cands and len(times) == ran
+    assert (prec, tile & ~(7 << 20)) in cands and len(times) >= ran
     # cached
     assert autotune.tune(g, groups, topk=K, seed=7,
                          precisions=(0, 1, 2) if ndim == 2 else (0,))[:2] == (prec, tile)

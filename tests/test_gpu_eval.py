@@ -60,3 +60,57 @@ def test_pattern_histograms_match_numpy(ev, down):
     assert ev.js_divergence(torch.from_numpy(h), torch.from_numpy(h)) == 0.0
     ref2 = stats.ensemble_histogram(list(reals[:1]), 2, k=down, w=4)
     assert abs(ev.js_divergence(torch.from_numpy(h), h2) - stats.js_divergence(ref, ref2)) < 1e-12
+
+
+def _pairs_by_flood_fill(real, f, lags, axis):
+    """Host counts from a 4-connected labelling (scipy.ndimage.label):
+    (pairs of facies f at lag h along the axis, pairs in one component)."""
+    from scipy import ndimage
+    lab, _ = ndimage.label(real == f)
+    out = []
+    for h in lags:
+        a, b = (lab[:, :-h], lab[:, h:]) if axis == 0 else (lab[:-h, :], lab[h:, :])
+        both = (a > 0) & (b > 0)
+        out.append((int(both.sum()), int((both & (a == b)).sum())))
+    return np.array(out, np.int64)
+
+
+@pytest.mark.parametrize("kind", ["ribbons", "random", "spiral"])
+def test_connection_probability_matches_flood_fill(ev, kind):
+    """The GPU probability of connection (union-find labelling, Sec. 5.3)
+    gives exactly the pair counts of a breadth-first labelling, on channel
+    layouts, percolation-like random fields and a long spiral (one component
+    whose union-find chains are long)."""
+    rng = np.random.default_rng(3)
+    if kind == "ribbons":
+        reals = np.stack([synth.ribbon_ti(180, 150, n_ribbons=8, seed=s, target=0.3, tol=0.2)
+                          for s in (1, 2, 3)])
+    elif kind == "random":
+        reals = (rng.random((4, 97, 131)) < 0.55).astype(np.uint8)
+    else:
+        n = 121
+        sp = np.zeros((n, n), np.uint8)
+        lo, hi = 0, n - 1
+        while lo <= hi:   # square spiral of width-1 corridors
+            sp[lo, lo:hi + 1] = 1
+            sp[lo:hi + 1, hi] = 1
+            if lo + 2 <= hi:
+                sp[hi, lo + 2:hi + 1] = 1
+                sp[lo + 2:hi + 1, lo + 2] = 1
+                sp[lo + 2, lo + 2:lo + 4] = 1
+            lo += 4
+            hi -= 4
+        reals = np.stack([sp, 1 - sp])
+    lags = (1, 2, 3, 8, 25, 64)
+    t = torch.from_numpy(np.ascontiguousarray(reals)).cuda()
+    for f in (0, 1):
+        for axis in (0, 1):
+            got = ev.connectivity_counts(t, f, lags, axis).cpu().numpy()
+            for i in range(len(reals)):
+                assert np.array_equal(got[i], _pairs_by_flood_fill(reals[i], f, lags, axis)), (
+                    f, axis, i)
+    # the probability equals the numpy definition (stats, axis 1 = x there)
+    p = ev.connection_probability(t, 1, lags, 0)
+    for i in range(len(reals)):
+        ref = stats.connection_probability(reals[i], 1, lags, axis=1)
+        assert np.allclose(p[i], ref, equal_nan=True, rtol=0, atol=0)

@@ -121,3 +121,32 @@ def test_mixed_grid_sizes_in_one_batch(ccw, precision):
                                    hd_vals=hds[gi][1], seed=4, r=groups[gi]["real_base"] + i)
             assert np.array_equal(log[i], rlog), f"group {gi} realization {i} log"
             assert np.array_equal(out[i], ref), f"group {gi} realization {i}"
+
+
+@pytest.mark.parametrize("precision,tile", [(0, 0), (2, 0x10020), (1, 0xa020020)])
+def test_realization_lanes_give_the_same_simulations(ccw, precision, tile):
+    """Realizations split into lanes whose wavefront chains run on separate
+    streams (ccf_tile bits 20-22) give exactly the one-lane simulations, in
+    one grid size and across two; sampled realizations equal the oracle's."""
+    ti = configs.ribbon_ti_250()
+    F, J, T, Ov, K = 2, 2, 48, 12, 3
+    g = ccw.TI(dev(ti), F, J, T, Ov)
+    grids = [(200, 160), (120, 100)]
+    groups = [dict(grid=grids[0], n_real=11, real_base=0), dict(grid=grids[1], n_real=5,
+                                                                 real_base=20)]
+    ref = None
+    for lanes in (1, 2, 3, 4, 8):
+        res = ccw.simulate_groups(g, groups, topk=K, seed=13, path_random=1, precision=precision,
+                                  ccf_tile=tile | ((lanes - 1) << 20), want_log=True)
+        got = [(o.cpu().numpy(), lg.cpu().numpy()) for o, lg in res]
+        if ref is None:
+            ref = got
+            continue
+        for (o0, l0), (o1, l1) in zip(ref, got):
+            assert np.array_equal(l0, l1), lanes
+            assert np.array_equal(o0, o1), lanes
+    o = O.OracleTI(ti, F, J)
+    for gi, i in ((0, 0), (0, 10), (1, 4)):
+        out, rlog = o.simulate(grids[gi], T, Ov, K=K, path_random=1, seed=13,
+                               r=groups[gi]["real_base"] + i)
+        assert np.array_equal(ref[gi][1][i], rlog) and np.array_equal(ref[gi][0][i], out)

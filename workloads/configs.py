@@ -68,7 +68,7 @@ BENCH_TILE = {
     "c4": (1, 0xa040040),
     "c4a": (1, 0xa040040),
     "c4b": (1, 0xa040040),
-    "c5": (2, 0x20020),
+    "c5": (2, 0x120020),
 }
 for _j in (1, 2, 3):
     for _h in (1000, 2000):
