@@ -80,6 +80,11 @@ WORKLOAD_TEXT = {
     "c5": "2D binary ribbon TI 250x250; 256 realizations 512x512; T48 OR12 J2; K=1",
 }
 for _j in (1, 2, 3):
+    for _g in (128, 256, 512, 768, 1024):
+        WORKLOAD_TEXT[f"sw_j{_j}_g{_g}"] = (
+            f"level sweep over grid sizes: 2D binary ribbon TI 250x250; 20 realizations "
+            f"{_g}x{_g}; T32 OR8 J{_j}; hard data at 1000 per 512^2; K=5")
+for _j in (1, 2, 3):
     for _h in (1000, 2000):
         WORKLOAD_TEXT[f"t2_j{_j}_h{_h}"] = (
             f"Table 2 level sweep: 2D binary ribbon TI 250x250; 20 realizations 512x512; T32 "

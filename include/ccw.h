@@ -138,6 +138,17 @@ typedef struct {
                           lower column, traced from the last row up); a
                           simulated cell takes the pattern only on the far
                           side of both cuts. Hard data are re-imposed. */
+  int32_t all_shift;   /* 0: candidates are the decimated origins (multiples
+                          of 2^J, Sec. 3.2); 1 (2D, precision 1 or 2 without
+                          streamed operands, bit 30, learned proposal or
+                          boundary cut): every fine origin c of the cropped TI
+                          with c + T <= n is a candidate, its approximation the
+                          2^(d J) block sums of its window; ranking index and
+                          patch-log index = c's raster index over the fine
+                          candidate grid, the pasted pattern = the TI crop at
+                          c, an empty data event draws over the fine grid.
+                          The library builds the TI's 2^(d J) phase planes on
+                          first use. */
 } ccw_params;
 
 /* Shape information of a prepared TI. */

@@ -32,7 +32,7 @@ class _Params(C.Structure):
                 ("n_real", C.c_int32), ("real_base", C.c_int32), ("path_random", C.c_int32),
                 ("score_mode", C.c_int32), ("precision", C.c_int32), ("learned", C.c_int32),
                 ("ccf_tile", C.c_int32), ("vt_ext", C.c_int32),
-                ("boundary_cut", C.c_int32)]
+                ("boundary_cut", C.c_int32), ("all_shift", C.c_int32)]
 
 
 class _Group(C.Structure):
@@ -246,7 +246,7 @@ class TI:
 
 def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None, real_base=0,
              path_random=0, score_mode=0, precision=0, want_log=False, out=None, log=None,
-             learned=0, ccf_tile=0, vt_ext=0, boundary_cut=0, stream=None):
+             learned=0, ccf_tile=0, vt_ext=0, boundary_cut=0, all_shift=0, stream=None):
     """``ccw_simulate``: returns (realizations uint8 [n_real, *grid[::-1]], log or None)."""
     lib = load()
     p = _Params()
@@ -262,6 +262,7 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
     p.ccf_tile = ccf_tile
     p.vt_ext = vt_ext
     p.boundary_cut = boundary_cut
+    p.all_shift = all_shift
     shape = (n_real,) + tuple(grid)[::-1]
     if out is None:
         out = torch.empty(shape, dtype=torch.uint8, device="cuda")
@@ -280,7 +281,7 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
 
 def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0, precision=0,
                     want_log=False, want_counts=False, learned=0, ccf_tile=0, vt_ext=0,
-                    boundary_cut=0, stream=None):
+                    boundary_cut=0, all_shift=0, stream=None):
     """``ccw_simulate_groups``: several grid sizes in one batch. ``groups`` is
     a list of dicts with keys grid, n_real, real_base and optionally hd_cells,
     hd_vals (CUDA tensors). Returns a list of (realizations, log or None)."""
@@ -297,6 +298,7 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
     p.ccf_tile = ccf_tile
     p.vt_ext = vt_ext
     p.boundary_cut = boundary_cut
+    p.all_shift = all_shift
     arr = (_Group * len(groups))()
     results = []
     keep = []

@@ -35,6 +35,9 @@ int persist_smem_bytes(int nch, int a_nq, int mt, int nt, int ksteps, int F, int
 int persist_grid(int smem, bool bf16);
 cudaError_t launch_persist(const WaveArgs& a, int smem, int grid, cudaStream_t st);
 // prepare.cu
+cudaError_t launch_phase_planes(const uint8_t* ti, int nx, int s, int F, int ph0, int ph1, int nc0,
+                                int nc1, float* planes, int px, int64_t plane_vol,
+                                cudaStream_t st);
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
                       int64_t nq, int nplanes, void* z8_f16, void* z8_bf16, cudaStream_t st);
 cudaError_t launch_crop_ti(const uint8_t* src, const int sdims[3], uint8_t* dst, const int n[3],
@@ -157,6 +160,9 @@ struct SimPlan {
   int K, score_mode, precision;
   int learned = 0, n_prop = 0, ccf_tile = 0;
   int vt_ext = 0, cut = 0;        // virtual-template extension, boundary cut
+  int all_shift = 0;              // all-shift candidates (phases of the TI)
+  PhaseDev* d_phases = nullptr;   // [n_phases] with this plan's M-groups and key lists
+  int n_phases = 0;
   int n_waves, max_items;
   std::vector<int64_t> wave_off;
   void* items = nullptr;
@@ -232,6 +238,7 @@ struct SimPlan {
     cudaFree(enc_act);
     cudaFree(call);
     cudaFree(dgroups);
+    cudaFree(d_phases);
     release_cp();
   }
   void release_cp();
@@ -264,6 +271,13 @@ struct ccw_ti {
   unsigned long long* d_learn_stats = nullptr;   // [3]
   int n_prop = 0;
   float gap_theta = 0.f;
+  // all-shift candidates (2D): level-J planes and 8-shift copies of every
+  // phase, built on first use
+  int n_phases = 0;
+  int fd[2] = {0, 0};                 // fine candidate grid
+  int64_t P_fine = 0;
+  std::vector<PhaseDev> h_phases;
+  std::vector<void*> phase_bufs;      // planes and 8-shift copies, freed with the TI
   std::mutex mu;
   SimPlan* plan = nullptr;
 };
@@ -996,6 +1010,7 @@ void ccw_ti_free(ccw_ti* t) {
   cudaFree(t->d_net);
   cudaFree(t->d_tables);
   cudaFree(t->d_learn_stats);
+  for (void* b : t->phase_bufs) cudaFree(b);
   delete t;
 }
 
@@ -1139,10 +1154,77 @@ int ccw_idwt_paste(const ccw_ti* t, int32_t B, const int32_t* pick_dev,
 // ---------------------------------------------------------------------------
 namespace {
 
+// The all-shift phases of a 2D TI (built once): for phase (ph0, ph1) in
+// [0, s)^2 the level-J planes of the blocks at (ph0 + s ux, ph1 + s uy), the
+// candidate grid of the fine origins of that phase with origin + T <= n, and
+// the planes' 8-shift copies for the tensor cores.
+int prepare_phases(ccw_ti* t, cudaStream_t st) {
+  if (t->n_phases) return CCW_OK;
+  if (t->ndim != 2) return fail(CCW_EINVAL, "all-shift candidates are 2D only");
+  const int s = t->s, T = t->T;
+  t->fd[0] = t->n[0] - T + 1;
+  t->fd[1] = t->n[1] - T + 1;
+  t->P_fine = (int64_t)t->fd[0] * t->fd[1];
+  if (t->P_fine >= (1 << 24)) return fail(CCW_EINVAL, "more than 2^24 - 1 all-shift candidates");
+  std::vector<PhaseDev> ph;
+  std::vector<void*> bufs;
+  cudaError_t e = cudaSuccess;
+  auto cleanup = [&]() {
+    for (void* b : bufs) cudaFree(b);
+  };
+  for (int ph1 = 0; ph1 < s; ++ph1)
+    for (int ph0 = 0; ph0 < s; ++ph0) {
+      const int nc0 = (t->n[0] - ph0) / s, nc1 = (t->n[1] - ph1) / s;
+      const int cd0 = nc0 - t->Tj + 1, cd1 = nc1 - t->Tj + 1;
+      if (cd0 <= 0 || cd1 <= 0) continue;   // no fine origin of this phase fits
+      PhaseDev d;
+      memset(&d, 0, sizeof(d));
+      d.ph0 = ph0;
+      d.ph1 = ph1;
+      d.cd0 = cd0;
+      d.cd1 = cd1;
+      d.px8 = (int)align_up(nc0, 8);
+      d.mtiles = (int)(((int64_t)d.px8 * cd1 + 127) / 128);
+      const int64_t roff_max = (int64_t)d.px8 * (t->Tj - 1);
+      d.z8_nq = std::max<int64_t>(
+          16LL * d.mtiles + 128 + (int64_t)(t->rows - 1) * d.px8 / 8 + 2 * (t->ks / 16) + 32,
+          (128LL * (d.mtiles + kTcMaxMt) + roff_max + t->ks + 256) / 8 + 8);
+      const int px = (int)align_up(nc0, 4);
+      const int64_t pv = (int64_t)px * nc1;
+      float* planes = nullptr;
+      void *zf = nullptr, *zb = nullptr;
+      const size_t zbytes = (size_t)t->F * d.z8_nq * 128;
+      if ((e = cudaMalloc(&planes, sizeof(float) * pv * t->F)) != cudaSuccess ||
+          (bufs.push_back(planes), (e = cudaMalloc(&zf, zbytes)) != cudaSuccess) ||
+          (bufs.push_back(zf), (e = cudaMalloc(&zb, zbytes)) != cudaSuccess)) {
+        cleanup();
+        return fail(CCW_ENOMEM, "all-shift planes: %s", cudaGetErrorString(e));
+      }
+      bufs.push_back(zb);
+      if ((e = cudaMemsetAsync(planes, 0, sizeof(float) * pv * t->F, st)) != cudaSuccess ||
+          (e = launch_phase_planes(t->d_ti, t->n[0], s, t->F, ph0, ph1, nc0, nc1, planes, px,
+                                   pv, st)) != cudaSuccess ||
+          (e = launch_z8(planes, px, pv, nc0, nc1, d.px8, d.z8_nq, t->F, zf, zb, st)) !=
+              cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "all-shift planes");
+      }
+      g_launches += 3;
+      d.z8_f16 = zf;
+      d.z8_bf16 = zb;
+      ph.push_back(d);
+    }
+  t->h_phases = ph;
+  t->phase_bufs = bufs;
+  t->n_phases = (int)ph.size();
+  return CCW_OK;
+}
+
 bool plan_matches(const SimPlan* pl, const ccw_params* p, const ccw_group* groups, int n_groups) {
   if (!pl || pl->n_groups != n_groups || pl->K != p->topk || pl->score_mode != p->score_mode ||
       pl->precision != p->precision || pl->learned != p->learned ||
-      pl->ccf_tile != p->ccf_tile || pl->vt_ext != p->vt_ext || pl->cut != p->boundary_cut)
+      pl->ccf_tile != p->ccf_tile || pl->vt_ext != p->vt_ext || pl->cut != p->boundary_cut ||
+      pl->all_shift != p->all_shift)
     return false;
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
@@ -1167,6 +1249,7 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   pl->ccf_tile = p->ccf_tile;
   pl->vt_ext = p->vt_ext;
   pl->cut = p->boundary_cut;
+  pl->all_shift = p->all_shift;
   pl->n_prop = p->learned ? t->n_prop : 0;
   pl->n_waves = 0;
   for (int i = 0; i < n_groups; ++i) {
@@ -1246,6 +1329,33 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
     cp->ev_bytes = (int64_t)pl->max_items * pl->evl.stride;
   } else {
     plan_ccf(t, fmt, nch, pl->K, pl->max_items, pl->evl, *cp, tiling);
+    if (p->all_shift) {
+      // every phase is searched by the CTAs of its grid layer, with the
+      // decimated plan's tiling; key lists [phase M-groups] per item
+      std::vector<PhaseDev> ph = t->h_phases;
+      const int mt = cp->tc.mt;
+      int parts = 0, mg_max = 0, a_nq_max = 0;
+      for (PhaseDev& d : ph) {
+        d.a_nq = 16 * (mt - 1) + (t->rows - 1) * d.px8 / 8 + 2 * (t->ks / 16 - 1) + 17;
+        d.n_mgroups = (d.mtiles + mt - 1) / mt;
+        d.part_base = parts;
+        parts += d.n_mgroups;
+        mg_max = std::max(mg_max, d.n_mgroups);
+        a_nq_max = std::max(a_nq_max, d.a_nq);
+      }
+      cp->tc.a_nq = a_nq_max;
+      cp->tc.n_mgroups = mg_max;
+      cp->n_parts = parts;
+      cp->smem = tc_smem_bytes(nch, a_nq_max, cp->tc.ksteps, cp->tc.nt, pl->K, cp->tc.tc_lane_epi);
+      cp->part_bytes = (int64_t)pl->max_items * parts * pl->K * 8;
+      pl->n_phases = (int)ph.size();
+      if (cudaMalloc((void**)&pl->d_phases, sizeof(PhaseDev) * ph.size()) != cudaSuccess ||
+          cudaMemcpy(pl->d_phases, ph.data(), sizeof(PhaseDev) * ph.size(),
+                     cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete pl;
+        return fail(CCW_ENOMEM, "all-shift phase table");
+      }
+    }
   }
   if (!cp->persist && cp->smem > 220 * 1024) {
     const int need = cp->smem;   // the plan owns cp
@@ -1330,6 +1440,13 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, s
   a.part = (unsigned long long*)ln.part;
   a.vt_ext = pl->vt_ext;
   a.cut = pl->cut;
+  if (pl->all_shift) {
+    a.allshift = 1;
+    a.phases = pl->d_phases;
+    a.n_phases = pl->n_phases;
+    a.fd0 = t->fd[0];
+    a.ti.P = t->P_fine;   // draws and K' range over the fine candidates
+  }
   if (pl->learned) {
     a.learned = 1;
     a.net = t->d_net;
@@ -1493,6 +1610,13 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   if (p->vt_ext < 0 || p->vt_ext > t->T)
     return fail(CCW_EINVAL, "vt_ext must be in [0, templ = %d]", t->T);
   if (p->boundary_cut != 0 && p->boundary_cut != 1) return fail(CCW_EINVAL, "bad boundary_cut");
+  if (p->all_shift != 0 && p->all_shift != 1) return fail(CCW_EINVAL, "bad all_shift");
+  if (p->all_shift &&
+      (d != 2 || (p->precision & 3) == 0 || p->learned || p->boundary_cut ||
+       ((p->ccf_tile >> 25) & 1) || tile_is_persist(p->precision & 3, p->ccf_tile)))
+    return fail(CCW_EINVAL,
+                "all_shift needs 2D, precision 1 or 2 with resident operands, and no learned "
+                "proposal, boundary cut or one-kernel form");
   if (p->boundary_cut && (d != 2 || t->T > kMaxCutTempl))
     return fail(CCW_EINVAL, "the boundary cut needs 2D and templ <= %d", kMaxCutTempl);
   if (int rc = check_score_bound(t, p->score_mode)) return rc;
@@ -1513,6 +1637,8 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
 
   std::lock_guard<std::mutex> lock(t->mu);
   cudaStream_t st = (cudaStream_t)stream;
+  if (p->all_shift)
+    if (int rc = prepare_phases(t, st)) return rc;
   SimPlan* pl = t->plan;
   if (!plan_matches(pl, p, groups, n_groups)) {
     cudaDeviceSynchronize();

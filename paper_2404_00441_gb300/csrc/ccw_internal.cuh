@@ -161,6 +161,20 @@ struct CallDev {
   unsigned long long* learn_stats;  // learned proposal counters [3] or NULL
 };
 
+// All-shift (polyphase) candidates: the TI's level-J planes of one phase
+// (block origins at phase + s u) and their 8-shift copies for the tensor
+// cores. A candidate's ranking index is its fine origin's raster index over
+// the fine candidate grid.
+struct PhaseDev {
+  const void* z8_f16;
+  const void* z8_bf16;
+  int64_t z8_nq;        // core matrices per plane of the 8-shift copies
+  int px8, mtiles, a_nq, n_mgroups;
+  int cd0, cd1;         // candidate grid of the phase (level-J origins)
+  int ph0, ph1;         // the phase (fine offset of block origins, < s)
+  int part_base;        // first partial key list of the phase per item
+};
+
 struct WaveArgs {
   TiDev ti;
   EvDev ev;
@@ -225,6 +239,11 @@ struct WaveArgs {
   uint32_t spin_limit;      // polls of a grid-barrier wait before it gives up
   int gw;                   // threads per item in the gather and paste phases
   unsigned long long* phase_ns;  // [3] summed phase durations (profiling) or NULL
+  // all-shift candidates (2D, tensor cores): CCF CTAs of phase blockIdx.z
+  int allshift;
+  const PhaseDev* phases;   // [n_phases] device array
+  int n_phases;
+  int fd0;                  // fine candidate grid width (n0 - T + 1)
 };
 
 }  // namespace ccw

@@ -355,6 +355,19 @@ __device__ void paste_blocks(const PasteGeom& p, const int16_t* staged, int nthr
   }
 }
 
+// CTA-cooperative paste of the TI crop at fine origin c (an all-shift
+// candidate; its level-J approximation and details reconstruct exactly
+// this crop). `ti` is the cropped fine TI with row pitch tp0 (2D).
+__device__ __forceinline__ void paste_crop2(const PasteGeom& p, const uint8_t* ti, int tp0,
+                                            int fd0, int c, int T, int nthreads, int lt) {
+  const int cx = c % fd0, cy = c / fd0;
+  for_window<2>(T, nthreads, lt, [&](int qx, int qy, int) {
+    const int gx = p.o[0] + qx, gy = p.o[1] + qy;
+    if (gx < 0 || gy < 0 || gx >= p.g[0] || gy >= p.g[1]) return;
+    p.grid[gx + (int64_t)p.g[0] * gy] = __ldg(ti + (cx + qx) + (int64_t)tp0 * (cy + qy));
+  });
+}
+
 // Re-impose the hard data of a pasted window (event-record list, int2 .y =
 // (window offset << 8) | code; virtual-template entries are skipped). Call
 // after a barrier that follows the paste.

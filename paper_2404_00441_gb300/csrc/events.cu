@@ -362,7 +362,10 @@ __global__ void __launch_bounds__(kThreads) k_events(const __grid_constant__ Wav
                                     : (tid < 3 ? 0 : -1));
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
-  paste_pixels<D>(g, pk, t.J, nth, tid);
+  if (D == 2 && a.allshift)
+    paste_crop2(g, t.ti, t.tp[0], a.fd0, pk, T, nth, tid);
+  else
+    paste_pixels<D>(g, pk, t.J, nth, tid);
   __syncthreads();
   paste_hard_data<D>(g, hdl, min(cnt[3], a.ev.hd_cap), T, nth, tid);
 }

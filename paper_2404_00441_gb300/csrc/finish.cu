@@ -248,7 +248,10 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     e[tid] = val;
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
-  if (D == 2 && a.cut && a.Oj > 0) {
+  if (D == 2 && a.allshift) {
+    // an all-shift candidate: the TI crop at its fine origin
+    paste_crop2(g, t.ti, t.tp[0], a.fd0, pk, t.T, nth, tid);
+  } else if (D == 2 && a.cut && a.Oj > 0) {
     // the pattern into shared memory, then the boundary-cut paste (the
     // launch guarantees staged_bytes > 0 and the cut buffers behind it)
     unsigned char* pat = reinterpret_cast<unsigned char*>(staged) + ((staged_bytes + 15) & ~15);

@@ -607,9 +607,102 @@ int64_t infer_act_floats(int C, int tj) {
   return 32LL * tj * tj + 32LL * s.h2 * s.h2 + s.flat + 64 + 1;
 }
 
+// One 3 x 3 convolution layer (pad 1) of one sample held in shared memory:
+// y[co][oy][ox] = round_bf16(relu(b[co] + sum_{ci,ky,kx} round_bf16(w) x)),
+// each output summed in the order of k_conv_fwd (bias first, then ci, ky, kx)
+// so that the result is the same bit for bit. A thread computes kCo output
+// channels of one pixel: every activation it loads serves kCo products.
+template <int kCo>
+__device__ __forceinline__ void conv_layer_smem(const float* __restrict__ x, int Ci, int H, int W,
+                                                const float* __restrict__ w,
+                                                const float* __restrict__ b, float* y, int Co,
+                                                int Ho, int Wo, int stride) {
+  const int npix = Ho * Wo, ngrp = Co / kCo;
+  for (int i = threadIdx.x; i < npix * ngrp; i += blockDim.x) {
+    const int pix = i % npix, co0 = (i / npix) * kCo;
+    const int oy = pix / Wo, ox = pix % Wo;
+    float acc[kCo];
+#pragma unroll
+    for (int c = 0; c < kCo; ++c) acc[c] = __ldg(b + co0 + c);
+    for (int ci = 0; ci < Ci; ++ci)
+      for (int ky = 0; ky < 3; ++ky) {
+        const int iy = oy * stride + ky - 1;
+        if (iy < 0 || iy >= H) continue;
+        for (int kx = 0; kx < 3; ++kx) {
+          const int ix = ox * stride + kx - 1;
+          if (ix < 0 || ix >= W) continue;
+          const float xv = x[(ci * H + iy) * W + ix];
+#pragma unroll
+          for (int c = 0; c < kCo; ++c)
+            acc[c] += round_bf16(__ldg(w + (((co0 + c) * Ci + ci) * 3 + ky) * 3 + kx), 1) * xv;
+        }
+      }
+#pragma unroll
+    for (int c = 0; c < kCo; ++c)
+      y[((co0 + c) * Ho + oy) * Wo + ox] = round_bf16(acc[c] < 0.f ? 0.f : acc[c], 1);
+  }
+}
+
+// The whole inference forward pass of one sample per CTA, activations in
+// shared memory; the same arithmetic as the layer-by-layer kernels
+// (k_conv_fwd x 3, k_linear_fwd, k_l2norm_fwd with bf16 = 1).
+__global__ void __launch_bounds__(256) k_encode_fused(const float* __restrict__ P, NetShape s,
+                                                      const float* __restrict__ x, int N,
+                                                      float* __restrict__ emb) {
+  extern __shared__ float sh[];
+  const int tj = s.tj, C = s.C;
+  float* xs = sh;                                   // [C][tj][tj]
+  float* a1 = xs + C * tj * tj;                     // [32][tj][tj]
+  float* a2 = a1 + 32 * tj * tj;                    // [32][h2][h2]
+  float* a3 = a2 + 32 * s.h2 * s.h2;                // [flat]
+  float* z = a3 + s.flat;                           // [64]
+  for (int n = blockIdx.x; n < N; n += gridDim.x) {
+    const float* xn = x + (int64_t)n * C * tj * tj;
+    for (int i = threadIdx.x; i < C * tj * tj; i += blockDim.x) xs[i] = __ldg(xn + i);
+    __syncthreads();
+    conv_layer_smem<4>(xs, C, tj, tj, P + s.o_w1, P + s.o_b1, a1, 32, tj, tj, 1);
+    __syncthreads();
+    conv_layer_smem<4>(a1, 32, tj, tj, P + s.o_w2, P + s.o_b2, a2, 32, s.h2, s.h2, 2);
+    __syncthreads();
+    conv_layer_smem<4>(a2, 32, s.h2, s.h2, P + s.o_w3, P + s.o_b3, a3, 32, s.h3, s.h3, 2);
+    __syncthreads();
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+      float acc = __ldg(P + s.o_bf + j);
+      for (int k = 0; k < s.flat; ++k)
+        acc += round_bf16(__ldg(P + s.o_wf + (int64_t)j * s.flat + k), 1) * a3[k];
+      z[j] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      float q = 0.f;
+      for (int k = lane; k < 64; k += 32) q += z[k] * z[k];
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      const float nr = sqrtf(fmaxf(q, 1e-24f));
+      for (int k = lane; k < 64; k += 32) emb[(int64_t)n * 64 + k] = z[k] / nr;
+    }
+    __syncthreads();   // the next sample reuses the buffers
+  }
+}
+
 cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
                       float* emb, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
+  {
+    // one CTA per sample with the activations in shared memory, when they fit
+    const NetShape s = net_shape(C, tj);
+    const int smem =
+        (int)sizeof(float) * (C * tj * tj + 32 * tj * tj + 32 * s.h2 * s.h2 + s.flat + 64);
+    if (smem <= 200 * 1024) {
+      if (smem > 48 * 1024 &&
+          cudaFuncSetAttribute(k_encode_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem) != cudaSuccess)
+        return cudaGetLastError();
+      const int grid = N < 65535 ? N : 65535;
+      k_encode_fused<<<grid, 256, smem, st>>>(P, s, x, N, emb);
+      return cudaGetLastError();
+    }
+  }
   const NetShape s = net_shape(C, tj);
   float* a1 = act;
   float* a2 = a1 + (int64_t)N * 32 * tj * tj;

@@ -195,6 +195,43 @@ __global__ void k_z8(const float* __restrict__ planes, int px, int64_t plane_vol
   }
 }
 
+// Level-J planes of one phase of the all-shift candidates (2D): block (ux,
+// uy) covers fine cells (ph0 + s ux + bx, ph1 + s uy + by), bx, by < s, of
+// the cropped TI; planes [F][nc1][px]: counts of facies 0..F-2, then the
+// code sums (the layout of the decimated planes).
+__global__ void k_phase_planes(const uint8_t* __restrict__ ti, int nx, int s, int F, int ph0,
+                               int ph1, int nc0, int nc1, float* __restrict__ planes, int px,
+                               int64_t plane_vol) {
+  const int64_t nb = (int64_t)nc0 * nc1;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int ux = (int)(b % nc0), uy = (int)(b / nc0);
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int code = 0;
+    for (int by = 0; by < s; ++by)
+      for (int bx = 0; bx < s; ++bx) {
+        const int v = ti[(ph0 + s * ux + bx) + (int64_t)nx * (ph1 + s * uy + by)];
+        code += v;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) cnt[f] += (v == f);
+      }
+    const int64_t o = ux + (int64_t)px * uy;
+#pragma unroll
+    for (int f = 0; f < 7; ++f)
+      if (f < F - 1) planes[f * plane_vol + o] = (float)cnt[f];
+    planes[(int64_t)(F - 1) * plane_vol + o] = (float)code;
+  }
+}
+
+cudaError_t launch_phase_planes(const uint8_t* ti, int nx, int s, int F, int ph0, int ph1, int nc0,
+                                int nc1, float* planes, int px, int64_t plane_vol,
+                                cudaStream_t st) {
+  const int64_t nb = (int64_t)nc0 * nc1;
+  const int blocks = (int)std::min<int64_t>((nb + 255) / 256, 152 * 8);
+  k_phase_planes<<<blocks, 256, 0, st>>>(ti, nx, s, F, ph0, ph1, nc0, nc1, planes, px, plane_vol);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_z8(const float* planes, int px, int64_t plane_vol, int nc0, int nc1, int px8,
                       int64_t nq, int nplanes, void* z8_f16, void* z8_bf16, cudaStream_t st) {
   const int64_t total = nq * 64 * nplanes;

@@ -93,10 +93,37 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quarter = warp & 3, parity = warp >> 2;
   const int mg = blockIdx.x, ntile = blockIdx.y;
+  // the candidate geometry: the TI's decimated level-J planes, or phase
+  // blockIdx.z of the all-shift candidates (block origins at phase + s u;
+  // ranking index = the fine origin's index over the fine candidate grid)
+  int mtiles = a.mtiles, px8 = a.px8, a_nq = a.a_nq, cd0 = t.cd[0], cd1 = t.cd[1];
+  int ph0 = 0, ph1 = 0, part_base = 0;
+  int64_t z8_nq = a.z8_nq;
+  const void* z8v = a.z8;
+  if (a.allshift) {
+    const PhaseDev& ph = a.phases[blockIdx.z];
+    if (mg >= ph.n_mgroups) return;   // the whole CTA, before any barrier
+    mtiles = ph.mtiles;
+    px8 = ph.px8;
+    a_nq = ph.a_nq;
+    cd0 = ph.cd0;
+    cd1 = ph.cd1;
+    ph0 = ph.ph0;
+    ph1 = ph.ph1;
+    part_base = ph.part_base;
+    z8_nq = ph.z8_nq;
+    z8v = a.precision == 2 ? ph.z8_bf16 : ph.z8_f16;
+  }
+  auto cand_index = [&](int cx, int cy) {
+    return a.allshift ? (t.s * cx + ph0) + a.fd0 * (t.s * cy + ph1) : cx + cd0 * cy;
+  };
+  auto cand_offset = [&](int cx, int cy) {
+    return (t.s * cx + ph0) + t.tp[0] * (t.s * cy + ph1);
+  };
   const int64_t L_start = (int64_t)mg * a.mt * 128;
-  const int n_mt = min(a.mt, a.mtiles - mg * a.mt);
+  const int n_mt = min(a.mt, mtiles - mg * a.mt);
   const int Kp = (int)((int64_t)K < t.P ? K : t.P);
-  const uint32_t a_bytes = (uint32_t)a.a_nq * 128u;
+  const uint32_t a_bytes = (uint32_t)a_nq * 128u;
   const uint32_t b_bytes = (uint32_t)a.ksteps * 32u * (uint32_t)nt;
 
   // ---- barriers and the (static) A region --------------------------------
@@ -105,10 +132,10 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
     fence_mbar_init();
     flag[0] = 0;
     mbar_arrive_expect_tx(&bar[kTcBarA], (uint32_t)nch * a_bytes);
-    const unsigned char* z8 = reinterpret_cast<const unsigned char*>(a.z8);
+    const unsigned char* z8 = reinterpret_cast<const unsigned char*>(z8v);
     for (int ch = 0; ch < nch; ++ch) {
       const unsigned char* src =
-          z8 + ((int64_t)(t.plane0 + ch) * a.z8_nq + L_start / 8) * 128;
+          z8 + ((int64_t)(t.plane0 + ch) * z8_nq + L_start / 8) * 128;
       bulk_g2s(As + (int64_t)ch * a_bytes, src, a_bytes, &bar[kTcBarA]);
     }
   }
@@ -132,7 +159,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
     meta[i] = m;
   }
   unsigned long long* work = (MODE == kModeSim) ? a.call->work : a.work;
-  if (work && mg == 0 && MODE != kModeMap) {
+  if (work && mg == 0 && blockIdx.z == 0 && MODE != kModeMap) {
     // profiling: candidate evaluations and algorithmic multiply-adds (data
     // cells of the template times channels) of every item, counted once
     for (int i = tid; i < nt; i += kTcThreads) {
@@ -159,20 +186,25 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       flag[0] = 1;
     } else {
       tc_fence_after();
+      // K steps (channel, template row, 16 taps) in order, the M-tiles'
+      // independent accumulators taking turns so that consecutive MMAs do
+      // not wait on each other's accumulation; addresses advance by constants
       const uint32_t idesc = instr_desc(BF16, 128, nt);
       const int k16n = a.ks / 16;
       const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-      for (int j = 0; j < n_mt; ++j) {
-        const uint32_t d = tmem + (uint32_t)(j * nt);
-        for (int k = 0; k < a.ksteps; ++k) {
-          const int k16 = k % k16n;
-          const int rc = k / k16n;          // ch * rows + row
-          const int row = rc % t.rows, ch = rc / t.rows;
-          const uint32_t q = (uint32_t)((128 * j + row * a.px8) / 8 + 2 * k16);
-          const uint64_t ad = smem_desc(a_base + (uint32_t)ch * a_bytes + q * 128u, 128u, 128u);
-          const uint64_t bd = smem_desc(b_base + (uint32_t)k * 32u * (uint32_t)nt, 128u, 256u);
-          mma_f16(d, ad, bd, idesc, k > 0 ? 1u : 0u);
-        }
+      const uint32_t b_step = 32u * (uint32_t)nt, row_bytes = (uint32_t)px8 * 16u;
+      uint32_t kidx = 0, b_addr = b_base;
+      for (int ch = 0; ch < nch; ++ch) {
+        uint32_t a_row = a_base + (uint32_t)ch * a_bytes;
+        for (int row = 0; row < t.rows; ++row, a_row += row_bytes)
+          for (int k16 = 0; k16 < k16n; ++k16, ++kidx, b_addr += b_step) {
+            const uint64_t bd = smem_desc(b_addr, 128u, 256u);
+            for (int j = 0; j < n_mt; ++j) {
+              const uint64_t ad =
+                  smem_desc(a_row + (uint32_t)(16 * j + 2 * k16) * 128u, 128u, 128u);
+              mma_f16(tmem + (uint32_t)(j * nt), ad, bd, idesc, kidx > 0 ? 1u : 0u);
+            }
+          }
       }
       mma_commit(&bar[kTcBarMma]);
     }
@@ -199,10 +231,9 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
     const int sp = nt + 4;
     for (int i = tid; i < n_mt * 128; i += kTcThreads) {
       const int64_t Lpos = L_start + i;
-      const int cx = (int)(Lpos % a.px8), cy = (int)(Lpos / a.px8);
-      const bool valid = cx < t.cd[0] && cy < t.cd[1];
-      cand[i] = make_int2(valid ? cx + t.cd[0] * cy : -1,
-                          t.s * cx + t.tp[0] * (t.s * cy));
+      const int cx = (int)(Lpos % px8), cy = (int)(Lpos / px8);
+      const bool valid = cx < cd0 && cy < cd1;
+      cand[i] = make_int2(valid ? cand_index(cx, cy) : -1, cand_offset(cx, cy));
     }
     const int n = tid % nt, nseg = kTcThreads / nt, seg = tid / nt;
     const int seg_len = 128 / nseg;
@@ -244,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
     for (int nn = warp; nn < nt; nn += 8) {
       if (!meta[nn].w) continue;
       const int item2 = ntile * nt + nn;
-      unsigned long long* part = a.part + ((int64_t)item2 * a.n_parts + mg) * K;
+      unsigned long long* part = a.part + ((int64_t)item2 * a.n_parts + part_base + mg) * K;
       int head = 0;
       const bool has = lane < nseg;
       for (int r = 0; r < Kp; ++r) {
@@ -268,10 +299,10 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
 #pragma unroll
     for (int j = 0; j < kTcMaxMt; ++j) {
       const int64_t Lpos = L_start + 128 * j + m;
-      const int cx = (int)(Lpos % a.px8), cy = (int)(Lpos / a.px8);
-      const bool valid = j < n_mt && cx < t.cd[0] && cy < t.cd[1];
-      cidx[j] = valid ? cx + t.cd[0] * cy : -1;
-      tb[j] = t.ti + (int64_t)t.s * cx + (int64_t)t.tp[0] * ((int64_t)t.s * cy);
+      const int cx = (int)(Lpos % px8), cy = (int)(Lpos / px8);
+      const bool valid = j < n_mt && cx < cd0 && cy < cd1;
+      cidx[j] = valid ? cand_index(cx, cy) : -1;
+      tb[j] = t.ti + cand_offset(cx, cy);
     }
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
@@ -336,7 +367,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       if (!meta[n].w) continue;
       const int item = ntile * nt + n;
       const int p = n & 1;   // the warps of parity p handled item n
-      unsigned long long* part = a.part + ((int64_t)item * a.n_parts + mg) * K;
+      unsigned long long* part = a.part + ((int64_t)item * a.n_parts + part_base + mg) * K;
       uint64_t prev = 0;
       for (int r = 0; r < Kp; ++r) {
         uint64_t best = kNoKey;
@@ -373,7 +404,7 @@ static cudaError_t launch_t(const WaveArgs& a, int smem, bool pdl, cudaStream_t 
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  dim3 grid(a.n_mgroups, (a.n_items + a.nt - 1) / a.nt);
+  dim3 grid(a.n_mgroups, (a.n_items + a.nt - 1) / a.nt, a.allshift ? a.n_phases : 1);
   return launch_pdl(fn, grid, dim3(kTcThreads), smem, st, pdl, a);
 }
 

@@ -15,6 +15,9 @@ stand-in with ``workloads.synth``:
   hard data per grid size from a second field (seed 6), K = 5.
 * ``c5`` -- c1's TI; 256 realizations of 512x512, template 48, overlap 12,
   level 2 (the learned-proposal geometry), K = 1.
+* ``sw_j<J>_g<G>`` -- the level sweep over grid sizes G x G (G = 128, 256,
+  512, 768, 1024), template 32, overlap 8, level J = 1..3, 20 realizations,
+  hard data at the Table 2 density, on c1's TI.
 * ``t2_j<J>_h<n>`` -- the DWT-level sweep of Table 2: c1's TI; 20
   realizations of 512x512, template 32, overlap 8, level J = 1..3, n = 1000
   or 2000 hard data from a second ribbon field (512x512, seed 9), K = 5.
@@ -73,6 +76,10 @@ BENCH_TILE = {
 for _j in (1, 2, 3):
     for _h in (1000, 2000):
         BENCH_TILE[f"t2_j{_j}_h{_h}"] = (2, 0)
+SWEEP_GRIDS = (128, 256, 512, 768, 1024)
+for _j in (1, 2, 3):
+    for _g in SWEEP_GRIDS:
+        BENCH_TILE[f"sw_j{_j}_g{_g}"] = (2, 0)
 
 
 def bench_tile(name: str):
@@ -118,6 +125,18 @@ def workload(name: str) -> dict:
         cells, vals = synth.sample_hard_data(hd_field_512(), n_hd, seed=10 + n_hd)
         return dict(name=name, ti=ribbon_ti_250(), F=2, J=J, T=32, O=8, K=5,
                     grid=(512, 512), n_real=20, hd=(cells, vals), seed=6)
+    if name.startswith("sw_"):
+        # the level sweep over grid sizes (Sec. 5.6): grids G x G, G in 128,
+        # 256, 512, 768, 1024, template 32, overlap 8, level J = 1..3, 20
+        # conditional realizations, hard data at the Table 2 density (1000
+        # per 512^2), on the 250 x 250 binary channel TI
+        _, j, gs = name.split("_")
+        J, G = int(j[1:]), int(gs[1:])
+        n_hd = max(1, round(1000 * G * G / (512 * 512)))
+        field = synth.ribbon_ti(G, G, n_ribbons=max(2, (24 * G) // 512), seed=9)
+        cells, vals = synth.sample_hard_data(field, n_hd, seed=20 + G)
+        return dict(name=name, ti=ribbon_ti_250(), F=2, J=J, T=32, O=8, K=5,
+                    grid=(G, G), n_real=20, hd=(cells, vals), seed=6)
     if name == "c5":
         return dict(name="c5", ti=ribbon_ti_250(), F=2, J=2, T=48, O=12, K=1,
                     grid=(512, 512), n_real=256, hd=None, seed=5)
