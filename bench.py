@@ -131,10 +131,12 @@ def parse_args():
     return ap.parse_args()
 
 
-def profiled_traffic(kernel: str, workload: str, tile: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.txt), if it was taken on this workload and tiling with
-    the current kernel source; None otherwise."""
+def profiled_traffic(kernel: str, workload: str, tile: int, items_per_launch: float):
+    """DRAM bytes of an average launch of `kernel` in the timed call, from the
+    committed ncu summary (profiles/traffic.txt: bytes per launch over a few
+    mid-call launches and the data events those launches processed), scaled
+    to the timed call's mean data events per launch; None unless the capture
+    was taken on this workload and tiling with the current kernel source."""
     import hashlib
     src = {"k_ccf_tc": "tc.cu", "k_ccf_tcs": "tcs.cu", "k_ccf_simt": "ccf_simt.cu"}[kernel]
     path = os.path.join(ROOT, "paper_2404_00441_gb300", "csrc", src)
@@ -144,10 +146,10 @@ def profiled_traffic(kernel: str, workload: str, tile: int):
         with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) >= 5 and not line.startswith("#") and parts[0] == kernel and \
+                if len(parts) >= 6 and not line.startswith("#") and parts[0] == kernel and \
                         parts[1] == workload and int(parts[2], 0) == tile and parts[3] == sha:
-                    return int(parts[4])
-    except (OSError, ValueError):
+                    return int(float(parts[4]) * items_per_launch / float(parts[5]))
+    except (OSError, ValueError, ZeroDivisionError):
         pass
     return None
 
@@ -424,6 +426,14 @@ def train_proposal(args, ti, w, grid):
             "prep_s": time.time() - t0}
 
 
+def encoder_macs(C, tj):
+    """Multiply-adds of one encoder pass (3 x 3 convolutions C -> 32, 32 -> 32
+    stride 2, 32 -> 32 stride 2, linear -> 64) on a C x tj x tj input."""
+    h2 = (tj - 1) // 2 + 1
+    h3 = (h2 - 1) // 2 + 1
+    return 32 * C * 9 * tj * tj + 32 * 32 * 9 * (h2 * h2 + h3 * h3) + 64 * 32 * h3 * h3
+
+
 def ours_line(args, world, m):
     """The benchmark's JSON line from the measurements `m` (see run_ours)."""
     cells = m["cells_per_step"] * world * args.steps
@@ -461,10 +471,14 @@ def ours_line(args, world, m):
                    "parallelism": f"realizations sharded over {world} GPU(s), no exchange"},
         "roofline": {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(kernel, args.workload, tile),
-                     "traffic_note": "cold-cache DRAM bytes per launch from profiles/traffic.txt "
-                                     "(null unless taken on this workload, tiling and kernel "
-                                     "source)",
+                     "traffic": profiled_traffic(
+                         kernel, args.workload, tile,
+                         m["items_per_step"] * args.steps / max(m["n_launch"], 1)),
+                     "traffic_note": "cold-cache DRAM bytes (read + write) per launch: ncu's "
+                                     "bytes per data event over a few mid-call launches "
+                                     "(profiles/traffic.txt) times the call's mean data events "
+                                     "per launch; null unless taken on this workload, tiling "
+                                     "and kernel source",
                      "launches": m["n_launch"],
                      "kernel_ms_per_step": kern_ms / args.steps,
                      "instrumented_ms_per_step": m["instr_ms"] / args.steps,
@@ -477,6 +491,37 @@ def ours_line(args, world, m):
     }
     if m.get("learned") is not None:
         line["config"]["learned"] = m["learned"]
+    if m.get("prop_ms") and any(m["prop_ms"]):
+        # the learned form: its dominant kernel may be the encoder or the
+        # nearest-window selection rather than the CCF (FP32 lanes, per data
+        # event: the encoder's multiply-adds; 64 per window of the table)
+        items = m["items_per_step"] * world
+        enc_ms, sel_ms = (v / args.steps for v in m["prop_ms"])
+        enc_flop = 2.0 * encoder_macs(m["F"], m["Tj"]) * items
+        sel_flop = 2.0 * 64 * m["n_cand"] * items
+        parts = {"k_encode_fused": (enc_ms, enc_flop), "k_nnsel_multi": (sel_ms, sel_flop),
+                 kernel: (kern_ms / args.steps, 2.0 * m["macs"] / args.steps)}
+        line["learned_kernels"] = {
+            k: {"ms_per_step": v[0], "flop_per_step": v[1],
+                "tflops": v[1] / (v[0] / 1e3) / 1e12 if v[0] > 0 else 0.0}
+            for k, v in parts.items()}
+        top = max(parts, key=lambda k: parts[k][0])
+        if top != kernel:
+            ms, fl = parts[top]
+            ach = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+            line["roofline"] = {
+                "bound": "alu", "kernel": top + (" (encoder of the data events, FP32 lanes)"
+                                                 if top == "k_encode_fused" else
+                                                 " (nearest TI windows by embedding, FP32 "
+                                                 "lanes, with the exact re-rank)"),
+                "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel_ms_per_step": ms,
+                "timing": "CUDA events around the proposal kernels inside the captured graph, "
+                          "second pass of the same K steps",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "work": "encoder: 2 x its multiply-adds per data event; selection: 2 x 64 "
+                        "flop per (data event, TI window)"}
     if getattr(args, "vt_ext", 0):
         line["config"]["vt_ext"] = args.vt_ext
     if getattr(args, "boundary_cut", False):
@@ -632,11 +677,14 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
     ccw.profile_enable(True)
     run()   # captures the instrumented graph (not timed)
     torch.cuda.synchronize()
-    ccw.profile_read()
+    ccw.profile_read()           # drop the capture call's counters
+    ccw.profile_read_phases()
+    ccw.profile_read_proposal()
     instr_ms = timed_steps()
     ccw.profile_enable(False)
     n_launch, kern_ms, cand_evals, macs = ccw.profile_read()
     phase_ms = ccw.profile_read_phases()
+    prop_ms = ccw.profile_read_proposal()
     clk = clocks.stop()
 
     # end to end through the public API with host buffers: the hard data come
@@ -686,7 +734,8 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
         n_launch=n_launch, launches=launches, clocks=clk, precision=precision, tile=tile,
         ndim=ndim, total_real=total_real, cells_per_step=cells_per_step,
         e2e_ms=e2e_ms_max if e2e_ms else None, h2d=h2d, d2h=d2h, learned=learned_info,
-        autotune=tune_info, phase_ms=phase_ms,
+        autotune=tune_info, phase_ms=phase_ms, prop_ms=prop_ms if learned else None,
+        n_cand=g.n_cand,
         items_per_step=sum(gr["n_real"] * n_patches_of(gr["grid"], w["T"], w["O"])
                            for gr in groups),
         T=w["T"], Tj=w["T"] // (2 ** w["J"]), F=w["F"],

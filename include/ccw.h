@@ -534,6 +534,11 @@ int ccw_profile_read(int64_t* launches, double* total_ms, double* cand_evals, do
  * learned proposal's kernels), ms[1] CCF, ms[2] finish (top-K merge, pick,
  * inverse-DWT paste); read and reset. */
 int ccw_profile_read_phases(double ms[3]);
+/* ccw_profile_read_proposal -- the learned proposal's share of the profiled
+ * simulations (stream-ordered events in the captured graph): ms[0] the
+ * encoder (inputs and embedding of the data events), ms[1] the nearest-window
+ * selection and the exact re-rank; read and reset. */
+int ccw_profile_read_proposal(double ms[2]);
 int64_t ccw_launch_count(void);
 
 #ifdef __cplusplus

@@ -80,6 +80,7 @@ def load():
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.ccw_launch_count.restype = i64
     lib.ccw_profile_read_phases.argtypes = [C.POINTER(C.c_double)]
+    lib.ccw_profile_read_proposal.argtypes = [C.POINTER(C.c_double)]
     f32 = C.c_float
     lib.ccw_net_create.argtypes = [i32, i32, u64, C.POINTER(P)]
     lib.ccw_net_free.argtypes = [P]
@@ -389,6 +390,14 @@ def profile_read_phases():
     last read."""
     v = (C.c_double * 3)()
     _check(load().ccw_profile_read_phases(v))
+    return tuple(float(x) for x in v)
+
+
+def profile_read_proposal():
+    """(encoder ms, nearest-window selection + re-rank ms) of the profiled
+    learned simulations since the last read."""
+    v = (C.c_double * 2)()
+    _check(load().ccw_profile_read_proposal(v))
     return tuple(float(x) for x in v)
 
 

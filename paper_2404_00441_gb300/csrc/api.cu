@@ -110,6 +110,7 @@ struct Profiler {
   int64_t launches = 0;
   double total_ms = 0.0;
   double phase_ms[3] = {0.0, 0.0, 0.0};   // simulations: events, CCF, finish
+  double prop_ms[2] = {0.0, 0.0};          // learned proposal: encoder, selection + re-rank
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // direct launches
   unsigned long long* d_work = nullptr;
 } g_prof;
@@ -202,6 +203,7 @@ struct SimPlan {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [profiling]
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;   // around each CCF launch
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_bounds;   // before events, after finish
+  std::vector<cudaEvent_t> prof_prop;   // learned: [3] per step: before encoder, before selection, after
   ~SimPlan() {
     for (auto& e : exec)
       if (e) cudaGraphExecDestroy(e);
@@ -210,6 +212,7 @@ struct SimPlan {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
       }
+    for (auto ev : prof_prop) cudaEventDestroy(ev);
     if (cap) cudaStreamDestroy(cap);
     for (size_t l = 1; l < lanes.size(); ++l) {
       cudaFree(lanes[l].ev);
@@ -770,6 +773,16 @@ int ccw_profile_read_phases(double ms[3]) {
   for (int i = 0; i < 3; ++i) {
     ms[i] = g_prof.phase_ms[i];
     g_prof.phase_ms[i] = 0.0;
+  }
+  return CCW_OK;
+}
+
+int ccw_profile_read_proposal(double ms[2]) {
+  if (!ms) return fail(CCW_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  for (int i = 0; i < 2; ++i) {
+    ms[i] = g_prof.prop_ms[i];
+    g_prof.prop_ms[i] = 0.0;
   }
   return CCW_OK;
 }
@@ -1480,10 +1493,23 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, s
       if (pl->learned) {
         // learned proposal: embed, nearest windows, exact re-rank; the CCF
         // kernel then skips the items the proposal settled
-        if ((e = launch_encode_items(c, c.enc_x, c.enc_act, true, st)) != cudaSuccess ||
-            (e = launch_nnsel(c, true, st)) != cudaSuccess ||
+        cudaEvent_t* pev = nullptr;
+        if (prof) {
+          while (pl->prof_prop.size() < 3 * (pe + 1)) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            pl->prof_prop.push_back(ev);
+          }
+          pev = &pl->prof_prop[3 * pe];
+          cudaEventRecordWithFlags(pev[0], st, cudaEventRecordExternal);
+        }
+        if ((e = launch_encode_items(c, c.enc_x, c.enc_act, !prof, st)) != cudaSuccess)
+          return cuda_fail(e, "proposal kernel launch");
+        if (prof) cudaEventRecordWithFlags(pev[1], st, cudaEventRecordExternal);
+        if ((e = launch_nnsel(c, !prof, st)) != cudaSuccess ||
             (e = launch_rerank(c, true, st)) != cudaSuccess)
           return cuda_fail(e, "proposal kernel launch");
+        if (prof) cudaEventRecordWithFlags(pev[2], st, cudaEventRecordExternal);
       }
       if (prof) {
         if (pe >= pl->prof_events.size()) {
@@ -1750,6 +1776,15 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
       if (cudaEventElapsedTime(&ev, bd.first, pr.first) == cudaSuccess) g_prof.phase_ms[0] += ev;
       if (cudaEventElapsedTime(&fin, pr.second, bd.second) == cudaSuccess)
         g_prof.phase_ms[2] += fin;
+      if (pl->learned && pl->prof_prop.size() >= 3 * (i + 1)) {
+        float enc = 0.f, sel = 0.f;
+        if (cudaEventElapsedTime(&enc, pl->prof_prop[3 * i], pl->prof_prop[3 * i + 1]) ==
+            cudaSuccess)
+          g_prof.prop_ms[0] += enc;
+        if (cudaEventElapsedTime(&sel, pl->prof_prop[3 * i + 1], pl->prof_prop[3 * i + 2]) ==
+            cudaSuccess)
+          g_prof.prop_ms[1] += sel;
+      }
     }
   }
   if (status & kStatusBadCode)

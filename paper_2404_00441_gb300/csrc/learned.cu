@@ -607,44 +607,83 @@ int64_t infer_act_floats(int C, int tj) {
   return 32LL * tj * tj + 32LL * s.h2 * s.h2 + s.flat + 64 + 1;
 }
 
-// One 3 x 3 convolution layer (pad 1) of one sample held in shared memory:
+// BF16 value of a 16-bit pattern (the weights are BF16-rounded when staged)
+__device__ __forceinline__ float bf16_at(const uint16_t* w, int i) {
+  return __uint_as_float((uint32_t)w[i] << 16);
+}
+
+// One 3 x 3 convolution layer (pad 1) of one sample in shared memory:
 // y[co][oy][ox] = round_bf16(relu(b[co] + sum_{ci,ky,kx} round_bf16(w) x)),
 // each output summed in the order of k_conv_fwd (bias first, then ci, ky, kx)
-// so that the result is the same bit for bit. A thread computes kCo output
-// channels of one pixel: every activation it loads serves kCo products.
-template <int kCo>
+// so that the result is the same bit for bit. The weights are staged
+// channel-minor, wt[((ci * 3 + ky) * 3 + kx) * 32 + co] (BF16), so that one
+// 8-byte load serves the 4 output channels a thread computes.
 __device__ __forceinline__ void conv_layer_smem(const float* __restrict__ x, int Ci, int H, int W,
-                                                const float* __restrict__ w,
-                                                const float* __restrict__ b, float* y, int Co,
-                                                int Ho, int Wo, int stride) {
-  const int npix = Ho * Wo, ngrp = Co / kCo;
-  for (int i = threadIdx.x; i < npix * ngrp; i += blockDim.x) {
-    const int pix = i % npix, co0 = (i / npix) * kCo;
+                                                const uint16_t* __restrict__ wt,
+                                                const float* __restrict__ b, float* y, int Ho,
+                                                int Wo, int stride) {
+  const int npix = Ho * Wo;
+  for (int i = threadIdx.x; i < npix * 8; i += blockDim.x) {
+    const int pix = i % npix, co0 = (i / npix) * 4;
     const int oy = pix / Wo, ox = pix % Wo;
-    float acc[kCo];
+    float acc[4];
 #pragma unroll
-    for (int c = 0; c < kCo; ++c) acc[c] = __ldg(b + co0 + c);
+    for (int c = 0; c < 4; ++c) acc[c] = __ldg(b + co0 + c);
     for (int ci = 0; ci < Ci; ++ci)
       for (int ky = 0; ky < 3; ++ky) {
         const int iy = oy * stride + ky - 1;
         if (iy < 0 || iy >= H) continue;
+#pragma unroll
         for (int kx = 0; kx < 3; ++kx) {
           const int ix = ox * stride + kx - 1;
           if (ix < 0 || ix >= W) continue;
           const float xv = x[(ci * H + iy) * W + ix];
-#pragma unroll
-          for (int c = 0; c < kCo; ++c)
-            acc[c] += round_bf16(__ldg(w + (((co0 + c) * Ci + ci) * 3 + ky) * 3 + kx), 1) * xv;
+          const uint2 w4 = *reinterpret_cast<const uint2*>(wt + ((ci * 3 + ky) * 3 + kx) * 32 + co0);
+          acc[0] += __uint_as_float(w4.x << 16) * xv;
+          acc[1] += __uint_as_float(w4.x & 0xFFFF0000u) * xv;
+          acc[2] += __uint_as_float(w4.y << 16) * xv;
+          acc[3] += __uint_as_float(w4.y & 0xFFFF0000u) * xv;
         }
       }
 #pragma unroll
-    for (int c = 0; c < kCo; ++c)
+    for (int c = 0; c < 4; ++c)
       y[((co0 + c) * Ho + oy) * Wo + ox] = round_bf16(acc[c] < 0.f ? 0.f : acc[c], 1);
   }
 }
 
-// The whole inference forward pass of one sample per CTA, activations in
-// shared memory; the same arithmetic as the layer-by-layer kernels
+// Stages conv weights w[co][ci][3][3] (FP32 masters) as BF16 in the
+// channel-minor layout of conv_layer_smem.
+// Reads w[0 .. n) in its own (contiguous) order, 8 loads in flight per
+// thread, and stores element i at dst[perm(i)] as BF16.
+template <typename Perm>
+__device__ __forceinline__ void stage_bf16(const float* __restrict__ w, int n, uint16_t* dst,
+                                           Perm perm) {
+  for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+    float v[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = i0 + b * blockDim.x;
+      v[b] = i < n ? __ldg(w + i) : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = i0 + b * blockDim.x;
+      if (i < n) dst[perm(i)] = __bfloat16_as_ushort(__float2bfloat16_rn(v[b]));
+    }
+  }
+}
+
+// Stages conv weights w[co][ci][3][3] (FP32 masters) as BF16 in the
+// channel-minor layout of conv_layer_smem.
+__device__ __forceinline__ void stage_conv_weights(const float* __restrict__ w, int Ci,
+                                                   uint16_t* wt) {
+  const int per = Ci * 9;   // r = (ci * 3 + ky) * 3 + kx
+  stage_bf16(w, 32 * per, wt, [per](int i) { return (i % per) * 32 + i / per; });
+}
+
+// The whole inference forward pass of the encoder, samples taken in turn by
+// each CTA, activations and BF16 weights in shared memory (the weights staged
+// once per CTA); the same arithmetic as the layer-by-layer kernels
 // (k_conv_fwd x 3, k_linear_fwd, k_l2norm_fwd with bf16 = 1).
 __global__ void __launch_bounds__(256) k_encode_fused(const float* __restrict__ P, NetShape s,
                                                       const float* __restrict__ x, int N,
@@ -656,20 +695,32 @@ __global__ void __launch_bounds__(256) k_encode_fused(const float* __restrict__ 
   float* a2 = a1 + 32 * tj * tj;                    // [32][h2][h2]
   float* a3 = a2 + 32 * s.h2 * s.h2;                // [flat]
   float* z = a3 + s.flat;                           // [64]
+  // the BF16 weights start 16-byte aligned (8-byte loads of 4 channels)
+  const int act_floats = (C * tj * tj + 32 * tj * tj + 32 * s.h2 * s.h2 + s.flat + 64 + 3) & ~3;
+  uint16_t* w1 = reinterpret_cast<uint16_t*>(sh + act_floats);   // [C*9][32]
+  uint16_t* w2 = w1 + 32 * C * 9;                   // [32*9][32]
+  uint16_t* w3 = w2 + 32 * 32 * 9;                  // [32*9][32]
+  uint16_t* wf = w3 + 32 * 32 * 9;                  // [flat][64]
+  stage_conv_weights(P + s.o_w1, C, w1);
+  stage_conv_weights(P + s.o_w2, 32, w2);
+  stage_conv_weights(P + s.o_w3, 32, w3);
+  {
+    const int flat = s.flat;   // wf[k][j] from the master's [j][k]
+    stage_bf16(P + s.o_wf, 64 * flat, wf, [flat](int i) { return (i % flat) * 64 + i / flat; });
+  }
   for (int n = blockIdx.x; n < N; n += gridDim.x) {
     const float* xn = x + (int64_t)n * C * tj * tj;
     for (int i = threadIdx.x; i < C * tj * tj; i += blockDim.x) xs[i] = __ldg(xn + i);
     __syncthreads();
-    conv_layer_smem<4>(xs, C, tj, tj, P + s.o_w1, P + s.o_b1, a1, 32, tj, tj, 1);
+    conv_layer_smem(xs, C, tj, tj, w1, P + s.o_b1, a1, tj, tj, 1);
     __syncthreads();
-    conv_layer_smem<4>(a1, 32, tj, tj, P + s.o_w2, P + s.o_b2, a2, 32, s.h2, s.h2, 2);
+    conv_layer_smem(a1, 32, tj, tj, w2, P + s.o_b2, a2, s.h2, s.h2, 2);
     __syncthreads();
-    conv_layer_smem<4>(a2, 32, s.h2, s.h2, P + s.o_w3, P + s.o_b3, a3, 32, s.h3, s.h3, 2);
+    conv_layer_smem(a2, 32, s.h2, s.h2, w3, P + s.o_b3, a3, s.h3, s.h3, 2);
     __syncthreads();
     for (int j = threadIdx.x; j < 64; j += blockDim.x) {
       float acc = __ldg(P + s.o_bf + j);
-      for (int k = 0; k < s.flat; ++k)
-        acc += round_bf16(__ldg(P + s.o_wf + (int64_t)j * s.flat + k), 1) * a3[k];
+      for (int k = 0; k < s.flat; ++k) acc += bf16_at(wf, k * 64 + j) * a3[k];
       z[j] = acc;
     }
     __syncthreads();
@@ -685,20 +736,36 @@ __global__ void __launch_bounds__(256) k_encode_fused(const float* __restrict__ 
   }
 }
 
+// Shared-memory bytes of k_encode_fused: activations, then BF16 weights.
+int encode_fused_smem(const NetShape& s) {
+  const int act = (int)sizeof(float) *
+                  ((s.C * s.tj * s.tj + 32 * s.tj * s.tj + 32 * s.h2 * s.h2 + s.flat + 64 + 3) &
+                   ~3);
+  const int w = 2 * (32 * s.C * 9 + 2 * 32 * 32 * 9 + 64 * s.flat);
+  return act + ((w + 15) & ~15);
+}
+
 cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
                       float* emb, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   {
     // one CTA per sample with the activations in shared memory, when they fit
     const NetShape s = net_shape(C, tj);
-    const int smem =
-        (int)sizeof(float) * (C * tj * tj + 32 * tj * tj + 32 * s.h2 * s.h2 + s.flat + 64);
-    if (smem <= 200 * 1024) {
+    const int smem = encode_fused_smem(s);
+    if (smem <= 110 * 1024) {
       if (smem > 48 * 1024 &&
           cudaFuncSetAttribute(k_encode_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                smem) != cudaSuccess)
         return cudaGetLastError();
-      const int grid = N < 65535 ? N : 65535;
+      // two CTAs per SM take the samples in turn (weights staged once each)
+      static int sms = 0;
+      if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+      }
+      const int grid = N < 2 * sms ? N : 2 * sms;
       k_encode_fused<<<grid, 256, smem, st>>>(P, s, x, N, emb);
       return cudaGetLastError();
     }

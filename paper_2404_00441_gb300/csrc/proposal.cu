@@ -262,6 +262,211 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ Wa
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same selection for kNnG data events per CTA: each table row is loaded
+// once into registers and dotted with every event of its mask type (the
+// events of a wavefront mostly share one), the scores kept in shared memory;
+// then one warp per event finds the threshold with the same two-level
+// histogram (so the same events fall back to the full search) and ranks the
+// survivors with a bitonic sort of (score descending, index ascending) keys.
+// For tables of at most kScoreCache windows.
+// ---------------------------------------------------------------------------
+constexpr int kNnG = 4;
+
+// The row's 64 BF16 values (8 x 16-byte words) dotted with e in the order of
+// nn_score (even and odd terms summed apart): the same score bit for bit.
+__device__ __forceinline__ float nn_score_regs(const uint4 (&r)[8], const float* e) {
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t w[4] = {r[q].x, r[q].y, r[q].z, r[q].w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const float lo = __uint_as_float(w[h] << 16), hi = __uint_as_float(w[h] & 0xFFFF0000u);
+      s0 = fmaf(lo, e[8 * q + 2 * h], s0);
+      s1 = fmaf(hi, e[8 * q + 2 * h + 1], s1);
+    }
+  }
+  return s0 + s1;
+}
+
+// Ascending order of these keys = score descending, then index ascending.
+__device__ __forceinline__ uint64_t nn_rank_key(float sc, int idx) {
+  uint32_t u = __float_as_uint(sc);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // ascending with the score
+  return ((uint64_t)(~u) << 32) | (uint32_t)idx;
+}
+
+struct NnMultiSmem {
+  float e[kNnG][64];
+  int hist[kNnG][kBins];
+  uint64_t keys[kNnG][kCollect];
+  int type[kNnG], ok[kNnG], cnt[kNnG];
+};
+
+__device__ __forceinline__ float nn_key_score(uint64_t k) {
+  const uint32_t ord = ~(uint32_t)(k >> 32);
+  return __uint_as_float((ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord);
+}
+
+__global__ void __launch_bounds__(kNnThreads) k_nnsel_multi(const __grid_constant__ WaveArgs a) {
+  extern __shared__ unsigned char nn_smem[];
+  NnMultiSmem& S = *reinterpret_cast<NnMultiSmem*>(nn_smem);
+  float* cache = reinterpret_cast<float*>(nn_smem + sizeof(NnMultiSmem));   // [kNnG][P]
+  const TiDev& t = a.ti;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i0 = blockIdx.x * kNnG;
+  const int P = (int)t.P;
+  pdl_trigger();
+  pdl_wait();
+  unsigned long long* stats = a.call ? a.call->learn_stats : nullptr;
+  if (tid < kNnG) {
+    const int item = i0 + tid;
+    int type = -1, ok = 0;
+    if (item < a.n_items) {
+      const int* meta = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+      type = meta[kEvMaskType];
+      const bool known = meta[kEvKnown] > 0;
+      ok = known && usable_type(type);
+      if (!ok) a.prop_gap[item] = -1.f;   // no proposals: full search
+      if (stats && known) atomicAdd(&stats[0], 1ull);
+      if (stats && ok) atomicAdd(&stats[1], 1ull);
+    }
+    S.type[tid] = ok ? type : -1;
+    S.ok[tid] = ok;
+  }
+  for (int i = tid; i < kNnG * 64; i += kNnThreads) {
+    const int g = i / 64, item = i0 + g;
+    S.e[g][i % 64] = item < a.n_items ? a.emb[(int64_t)item * 64 + i % 64] : 0.f;
+  }
+  __syncthreads();
+  // scores: every row of a type present in the group, loaded once
+  for (int g = 0; g < kNnG; ++g) {
+    const int type = S.type[g];
+    if (type < 0) continue;
+    bool first = true;
+    for (int h = 0; h < g; ++h) first &= S.type[h] != type;
+    if (!first) continue;   // already scored with an earlier event of this type
+    const uint4* tab = reinterpret_cast<const uint4*>(a.tables + (int64_t)type * t.P * 64);
+    for (int c = tid; c < P; c += kNnThreads) {
+      uint4 r[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) r[q] = __ldg(tab + (int64_t)c * 8 + q);
+#pragma unroll
+      for (int h = 0; h < kNnG; ++h)
+        if (S.type[h] == type) cache[h * P + c] = nn_score_regs(r, S.e[h]);
+    }
+  }
+  __syncthreads();
+  if (warp >= kNnG || !S.ok[warp]) return;
+  // selection: one warp per event
+  const int g = warp, item = i0 + g;
+  const float* sc = cache + g * P;
+  int* hist = S.hist[g];
+  uint64_t* keys = S.keys[g];
+  const int np = (int)min((int64_t)a.n_prop, t.P);
+  float lo = -1.5f, hi = 1.5f;
+  int above_prev = 0;
+  float thr = lo;
+  for (int level = 0; level < 2; ++level) {
+    for (int b = lane; b < kBins; b += 32) hist[b] = 0;
+    __syncwarp();
+    const float scale = kBins / (hi - lo);
+    for (int cb = 0; cb < P; cb += 32) {
+      const int c = cb + lane;
+      int b = -1;
+      if (c < P) {
+        const float v = sc[c];
+        if (v >= lo && v < hi) b = min(kBins - 1, max(0, (int)((v - lo) * scale)));
+      }
+      const unsigned same = __match_any_sync(0xffffffffu, b);
+      if (b >= 0 && lane == __ffs(same) - 1) atomicAdd(&hist[b], __popc(same));
+    }
+    __syncwarp();
+    // the highest bin b >= 1 whose count with everything above reaches np
+    // (else bin 0): lane L holds bins 32L .. 32L + 31
+    int part = 0;
+    for (int k = 0; k < 32; ++k) part += hist[32 * lane + k];
+    int above_lanes = 0;   // bins of the lanes above this one
+    for (int L = 31; L > 0; --L) {
+      const int v = __shfl_sync(0xffffffffu, part, L);
+      if (L > lane) above_lanes += v;
+    }
+    int run = above_prev + above_lanes, fb = -1, fabove = 0;
+    for (int k = 31; k >= 0; --k) {
+      const int b = 32 * lane + k;
+      if (b > 0 && run + hist[b] >= np && fb < 0) {
+        fb = b;
+        fabove = run;
+      }
+      run += hist[b];
+      if (b == 0 && fb < 0) {
+        fb = -2;   // reached bin 0 without a hit: bin 0 with `run - hist[0]` above
+        fabove = run - hist[0];
+      }
+    }
+    const unsigned hits = __ballot_sync(0xffffffffu, fb >= 0);
+    int bsel, above;
+    if (hits) {
+      const int src = 31 - __clz(hits);
+      bsel = __shfl_sync(0xffffffffu, fb, src);
+      above = __shfl_sync(0xffffffffu, fabove, src);
+    } else {
+      bsel = 0;
+      above = __shfl_sync(0xffffffffu, fabove, 0);
+    }
+    const int inbin = hist[bsel];
+    thr = lo + bsel / scale;
+    if (above + inbin <= kCollect || level == 1) break;
+    const float nlo = thr, nhi = lo + (bsel + 1) / scale;
+    above_prev = above;
+    __syncwarp();
+    lo = nlo;
+    hi = nhi;
+  }
+  // survivors: keys (score descending, index ascending)
+  int total = 0;
+  for (int cb = 0; cb < P; cb += 32) {
+    const int c = cb + lane;
+    const bool keep = c < P && sc[c] >= thr;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int k = total + __popc(bal & ((1u << lane) - 1u));
+      if (k < kCollect) keys[k] = nn_rank_key(sc[c] + 0.f, c);
+    }
+    total += __popc(bal);
+  }
+  const int ncoll = min(total, kCollect);
+  if (total > kCollect || ncoll < np) {
+    if (lane == 0) a.prop_gap[item] = -1.f;   // threshold not usable: full search
+    return;
+  }
+  for (int k = ncoll + lane; k < kCollect; k += 32) keys[k] = kNoKey;
+  __syncwarp();
+  // bitonic sort of kCollect keys, ascending
+  for (int k = 2; k <= kCollect; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < kCollect; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint64_t x = keys[i], y = keys[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            keys[i] = y;
+            keys[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  for (int r = lane; r < np; r += 32)
+    a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
+  if (lane == 0) {
+    const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
+    a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+  }
+}
+
 // Event records from explicit block counts (the query entry point): known
 // cells, mask type and counts, as the event kernel writes them.
 __global__ void k_records_from_counts(const __grid_constant__ WaveArgs a, const uint8_t* counts,
@@ -426,6 +631,18 @@ cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tab
 }
 
 cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st) {
+  if (a.ti.P <= kScoreCache) {
+    const int smem = (int)(sizeof(NnMultiSmem) + sizeof(float) * kNnG * a.ti.P);
+    static int configured = 0;
+    if (smem > configured) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_nnsel_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
+    return launch_pdl(k_nnsel_multi, dim3((a.n_items + kNnG - 1) / kNnG), dim3(kNnThreads),
+                      smem, st, pdl, a);
+  }
   return launch_pdl(k_nnsel, dim3(a.n_items), dim3(kNnThreads), 0, st, pdl, a);
 }
 
