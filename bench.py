@@ -138,6 +138,8 @@ def profiled_traffic(kernel: str, workload: str, tile: int, items_per_launch: fl
     to the timed call's mean data events per launch; None unless the capture
     was taken on this workload and tiling with the current kernel source."""
     import hashlib
+    if items_per_launch <= 0:
+        return None
     src = {"k_ccf_tc": "tc.cu", "k_ccf_tcs": "tcs.cu", "k_ccf_simt": "ccf_simt.cu"}[kernel]
     path = os.path.join(ROOT, "paper_2404_00441_gb300", "csrc", src)
     try:
@@ -473,7 +475,7 @@ def ours_line(args, world, m):
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(
                          kernel, args.workload, tile,
-                         m["items_per_step"] * args.steps / max(m["n_launch"], 1)),
+                         m.get("items_per_step", 0) * args.steps / max(m["n_launch"], 1)),
                      "traffic_note": "cold-cache DRAM bytes (read + write) per launch: ncu's "
                                      "bytes per data event over a few mid-call launches "
                                      "(profiles/traffic.txt) times the call's mean data events "

@@ -367,6 +367,15 @@ int ccw_ti_status(const ccw_ti* ti, void* stream, int32_t* status_out);
  * ------------------------------------------------------------------------ */
 typedef struct ccw_net ccw_net;
 
+/* ccw_set_nn_path -- which kernel scores and selects the nearest TI windows
+ * of the learned proposal (the proposals are the same up to FP32 rounding of
+ * the scores): 0 (default) the tcgen05 kernel for tables of at most 3584
+ * windows, else the FP32-lane kernel with several data events per CTA (at
+ * most 6144 windows), else one CTA per data event; 1 never the tensor cores;
+ * 2 always one CTA per data event. Process-wide; CCW_EINVAL for other
+ * values. */
+int ccw_set_nn_path(int32_t path);
+
 /* ccw_net_create -- new encoder for in_ch channels of tj x tj, He-normal
  * weights from `seed` (deterministic), zero biases. */
 int ccw_net_create(int32_t in_ch, int32_t tj, uint64_t seed, ccw_net** out);
@@ -377,7 +386,12 @@ int64_t ccw_net_param_count(const ccw_net* net);
 int ccw_net_get(const ccw_net* net, int32_t what, float* host);
 int ccw_net_set(ccw_net* net, const float* host);
 /* ccw_net_embed -- unit embeddings float [n][64] of inputs float [n][C][tj][tj]
- * (device pointers). */
+ * (device pointers). bf16 = 0: the training forward pass in FP32; 1: the
+ * same with BF16 weights and activations; 2: the inference pass that the
+ * learned proposal runs (tcgen05 tensor cores where the shape fits: C <= 8
+ * and the layer planes in shared memory; inputs taken as BF16, which the
+ * proposal's block-count inputs are exactly); 3: the fused FP32-lane
+ * inference kernel (BF16 weights and activations, as 1). */
 int ccw_net_embed(ccw_net* net, const float* x_dev, int32_t n, int32_t bf16, float* emb_dev,
                   void* stream);
 /* ccw_net_train_step -- one InfoNCE step: anchors [B][C][tj][tj], candidates

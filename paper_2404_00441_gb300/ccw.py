@@ -81,6 +81,7 @@ def load():
     lib.ccw_launch_count.restype = i64
     lib.ccw_profile_read_phases.argtypes = [C.POINTER(C.c_double)]
     lib.ccw_profile_read_proposal.argtypes = [C.POINTER(C.c_double)]
+    lib.ccw_set_nn_path.argtypes = [C.c_int32]
     f32 = C.c_float
     lib.ccw_net_create.argtypes = [i32, i32, u64, C.POINTER(P)]
     lib.ccw_net_free.argtypes = [P]
@@ -399,6 +400,12 @@ def profile_read_proposal():
     v = (C.c_double * 2)()
     _check(load().ccw_profile_read_proposal(v))
     return tuple(float(x) for x in v)
+
+
+def set_nn_path(path: int):
+    """``ccw_set_nn_path``: 0 auto (tensor cores for small tables), 1 never the
+    tensor cores, 2 one CTA per data event."""
+    _check(load().ccw_set_nn_path(int(path)))
 
 
 def philox_host(ctr, key):

@@ -61,9 +61,15 @@ cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3],
 cudaError_t launch_round_weights(float* p, int C, int tj, cudaStream_t st);
 cudaError_t launch_encode_items(const WaveArgs& a, float* x, float* act, bool pdl,
                                 cudaStream_t st);
+int64_t enc_tc_image_bytes(int C, int tj);
+cudaError_t enc_tc_build_image(const float* P, int C, int tj, void* img, cudaStream_t st);
+cudaError_t launch_tables_mma(const __nv_bfloat16* tables, int64_t P, __nv_bfloat16* out,
+                              cudaStream_t st);
+int64_t tables_mma_elems(int64_t P);
 cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tables, float* x,
                                  float* act, float* emb, int chunk, cudaStream_t st);
 cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st);
+int encode_items_launches(int F, int Tj, bool img);
 cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st);
 cudaError_t launch_records_from_counts(const WaveArgs& a, const uint8_t* counts,
                                       int32_t* type_out, cudaStream_t st);
@@ -271,6 +277,8 @@ struct ccw_ti {
   // learned proposal (2D): encoder parameters, window tables per mask type
   float* d_net = nullptr;
   __nv_bfloat16* d_tables = nullptr;   // [16][P][64]
+  __nv_bfloat16* d_tables_mma = nullptr;   // the same in 128-window MMA blocks (small P)
+  void* d_enc_img = nullptr;               // the encoder's tensor-core weight image
   unsigned long long* d_learn_stats = nullptr;   // [3]
   int n_prop = 0;
   float gap_theta = 0.f;
@@ -1022,6 +1030,8 @@ void ccw_ti_free(ccw_ti* t) {
   cudaFree(t->d_status);
   cudaFree(t->d_net);
   cudaFree(t->d_tables);
+  cudaFree(t->d_tables_mma);
+  cudaFree(t->d_enc_img);
   cudaFree(t->d_learn_stats);
   for (void* b : t->phase_bufs) cudaFree(b);
   delete t;
@@ -1320,7 +1330,9 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
       ln.wave_off[w] = (int64_t)items.size();
       items.insert(items.end(), waves[l][w].begin(), waves[l][w].end());
       ln.max_items = std::max<int>(ln.max_items, (int)waves[l][w].size());
-      pl->launches_per_call += (p->learned ? 11 : 3) * ((waves[l][w].size() + 65534) / 65535);
+      pl->launches_per_call +=
+          (p->learned ? 5 + encode_items_launches(t->F, t->Tj, t->d_enc_img != nullptr) : 3) *
+          ((waves[l][w].size() + 65534) / 65535);
     }
     ln.wave_off[pl->n_waves] = (int64_t)items.size();
     pl->max_items = std::max(pl->max_items, ln.max_items);
@@ -1464,6 +1476,8 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, s
     a.learned = 1;
     a.net = t->d_net;
     a.tables = t->d_tables;
+    a.tables_mma = t->d_tables_mma;
+    a.enc_img = t->d_enc_img;
     a.n_prop = pl->n_prop;
     a.emb = (float*)pl->emb;
     a.prop = (int*)pl->prop;
@@ -1829,8 +1843,12 @@ extern "C" int ccw_ti_attach_proposal(ccw_ti* t, const ccw_net* net, int32_t n_p
   t->plan = nullptr;
   cudaFree(t->d_net);
   cudaFree(t->d_tables);
+  cudaFree(t->d_tables_mma);
+  cudaFree(t->d_enc_img);
   t->d_net = nullptr;
   t->d_tables = nullptr;
+  t->d_tables_mma = nullptr;
+  t->d_enc_img = nullptr;
   t->n_prop = 0;
   if (!net) return CCW_OK;
   if (t->ndim != 2) return fail(CCW_EINVAL, "the learned proposal is 2D only");
@@ -1864,9 +1882,17 @@ extern "C" int ccw_ti_attach_proposal(ccw_ti* t, const ccw_net* net, int32_t n_p
           cudaSuccess)
     return cuda_fail(e, "attach proposal");
   ++g_launches;   // weight rounding
+  const int64_t img_bytes = enc_tc_image_bytes(C, tj);
+  if (img_bytes > 0) {
+    if ((e = cudaMalloc(&t->d_enc_img, (size_t)img_bytes)) != cudaSuccess ||
+        (e = enc_tc_build_image(t->d_net, C, tj, t->d_enc_img, st)) != cudaSuccess)
+      return cuda_fail(e, "encoder weight image");
+    ++g_launches;
+  }
   WaveArgs a;
   fill_ti(t, 0, a);
   a.net = t->d_net;
+  a.enc_img = t->d_enc_img;
   // scratch of the table passes, freed at the end
   const int chunk = (int)std::min<int64_t>(t->P, 16384);
   float *x = nullptr, *act = nullptr, *emb = nullptr;
@@ -1881,7 +1907,17 @@ extern "C" int ccw_ti_attach_proposal(ccw_ti* t, const ccw_net* net, int32_t n_p
   for (int type = 1; type < 16 && e == cudaSuccess; ++type) {
     if (!usable_mask_type(type)) continue;
     e = launch_encode_tables(a, type, t->d_tables, x, act, emb, chunk, st);
-    g_launches += 7 * ((t->P + chunk - 1) / chunk);
+    // per chunk: window inputs, the encoder (1 launch, or 5 layer by layer), BF16 copy
+    const int enc = encode_items_launches(C, tj, t->d_enc_img != nullptr);
+    g_launches += (2 + (enc == 1 ? 1 : enc - 1)) * ((t->P + chunk - 1) / chunk);
+  }
+  // the tensor-core selector's copy of small tables
+  const int64_t mma_elems = tables_mma_elems(t->P);
+  if (e == cudaSuccess && mma_elems > 0) {
+    if ((e = cudaMalloc((void**)&t->d_tables_mma, sizeof(__nv_bfloat16) * mma_elems)) ==
+        cudaSuccess)
+      e = launch_tables_mma(t->d_tables, t->P, t->d_tables_mma, st);
+    ++g_launches;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(x);
@@ -1931,6 +1967,8 @@ extern "C" int ccw_proposal_query(const ccw_ti* tc, const uint8_t* counts_dev, i
     a.n_items = std::min(chunk, n - i0);
     a.net = t->d_net;
     a.tables = t->d_tables;
+    a.tables_mma = t->d_tables_mma;
+    a.enc_img = t->d_enc_img;
     a.n_prop = t->n_prop;
     a.emb = (float*)emb;
     a.prop = prop_dev + (int64_t)i0 * t->n_prop;
@@ -1940,7 +1978,7 @@ extern "C" int ccw_proposal_query(const ccw_ti* tc, const uint8_t* counts_dev, i
         (e = launch_encode_items(a, (float*)x, (float*)act, false, st)) != cudaSuccess ||
         (e = launch_nnsel(a, false, st)) != cudaSuccess)
       rc = cuda_fail(e, "proposal query kernels");
-    g_launches += 8;
+    g_launches += 2 + encode_items_launches(t->F, t->Tj, t->d_enc_img != nullptr);
   }
   cudaFreeAsync(act, st);
   cudaFreeAsync(x, st);

@@ -221,7 +221,9 @@ struct WaveArgs {
   // learned proposal (simulation mode)
   int learned;
   const float* net;         // encoder parameters (FP32)
+  const void* enc_img;      // their tensor-core weight image, or NULL
   const __nv_bfloat16* tables;  // [16 mask types][P][64] unit embeddings of TI windows
+  const __nv_bfloat16* tables_mma;  // the same in 128-window MMA blocks, or NULL
   float* emb;               // [n_items][64] item embeddings
   float* enc_x;             // [n_items][F][Tj^2] encoder inputs
   float* enc_act;           // encoder activations of the step's items

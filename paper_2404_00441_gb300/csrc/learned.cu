@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "ccw_internal.cuh"
+#include "net_shape.cuh"
 
 namespace ccw {
 
@@ -308,30 +309,10 @@ __global__ void k_adamw(float* __restrict__ p, const float* __restrict__ g, floa
 // ---------------------------------------------------------------------------
 namespace ccw {
 
-struct NetShape {
-  int C, tj, h2, h3, flat;
-  int64_t o_w1, o_b1, o_w2, o_b2, o_w3, o_b3, o_wf, o_bf, n;
-};
-
-inline NetShape net_shape(int C, int tj) {
-  NetShape s;
-  s.C = C;
-  s.tj = tj;
-  s.h2 = (tj - 1) / 2 + 1;
-  s.h3 = (s.h2 - 1) / 2 + 1;
-  s.flat = 32 * s.h3 * s.h3;
-  int64_t o = 0;
-  s.o_w1 = o; o += 32LL * C * 9;
-  s.o_b1 = o; o += 32;
-  s.o_w2 = o; o += 32LL * 32 * 9;
-  s.o_b2 = o; o += 32;
-  s.o_w3 = o; o += 32LL * 32 * 9;
-  s.o_b3 = o; o += 32;
-  s.o_wf = o; o += 64LL * s.flat;
-  s.o_bf = o; o += 64;
-  s.n = o;
-  return s;
-}
+int64_t infer_act_floats(int C, int tj);
+// Inference pass (defined below): see net_infer.
+cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
+                      float* emb, cudaStream_t st, int* status, int path, const void* wimg);
 
 static int grid_for(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
@@ -522,6 +503,20 @@ int ccw_net_embed(ccw_net* n, const float* x_dev, int32_t N, int32_t bf16, float
     return net_fail(CCW_EINVAL, "bad argument");
   if (N == 0) return CCW_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  if (bf16 == 2 || bf16 == 3) {
+    // the inference pass of the proposal (2: tensor cores where the shape
+    // fits; 3: the FP32-lane kernels), with scratch for the per-layer path
+    float* act = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&act,
+                                    sizeof(float) * (size_t)infer_act_floats(n->s.C, n->s.tj) * N,
+                                    st);
+    if (e != cudaSuccess) return net_fail(CCW_ENOMEM, "inference scratch");
+    e = net_infer(n->p, n->s.C, n->s.tj, x_dev, N, act, emb_dev, st, nullptr, bf16 == 3 ? 1 : 0,
+                  nullptr);
+    cudaFreeAsync(act, st);
+    if (e != cudaSuccess) return net_fail(CCW_ECUDA, "inference kernel");
+    return CCW_OK;
+  }
   for (int i0 = 0; i0 < N; i0 += 4096) {
     const int c = std::min(4096, N - i0);
     if (int rc = ensure_acts(n, c)) return rc;
@@ -736,6 +731,10 @@ __global__ void __launch_bounds__(256) k_encode_fused(const float* __restrict__ 
   }
 }
 
+int encode_fused_smem(const NetShape& s);
+// Does the fused FP32-lane inference kernel take shape (C, tj)?
+bool net_infer_fused_fits(int C, int tj) { return encode_fused_smem(net_shape(C, tj)) <= 110 * 1024; }
+
 // Shared-memory bytes of k_encode_fused: activations, then BF16 weights.
 int encode_fused_smem(const NetShape& s) {
   const int act = (int)sizeof(float) *
@@ -745,9 +744,19 @@ int encode_fused_smem(const NetShape& s) {
   return act + ((w + 15) & ~15);
 }
 
+cudaError_t net_infer_tc(const float* P, const void* wimg, int C, int tj, const float* x, int N,
+                         float* emb, int* status, cudaStream_t st);
+
+// path 0: the tensor-core kernel where the shape fits (encoder_tc.cu; wimg
+// its weight image or NULL), else the fused FP32-lane kernel, else one launch
+// per layer (needs `act`); path 1: never the tensor cores.
 cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
-                      float* emb, cudaStream_t st) {
+                      float* emb, cudaStream_t st, int* status, int path, const void* wimg) {
   if (N <= 0) return cudaSuccess;
+  if (path == 0) {
+    const cudaError_t e = net_infer_tc(P, wimg, C, tj, x, N, emb, status, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   {
     // one CTA per sample with the activations in shared memory, when they fit
     const NetShape s = net_shape(C, tj);
@@ -770,6 +779,7 @@ cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, floa
       return cudaGetLastError();
     }
   }
+  if (!act) return cudaErrorInvalidValue;
   const NetShape s = net_shape(C, tj);
   float* a1 = act;
   float* a2 = a1 + (int64_t)N * 32 * tj * tj;

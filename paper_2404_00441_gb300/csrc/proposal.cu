@@ -7,12 +7,14 @@
 #include <algorithm>
 
 #include "device_util.cuh"
+#include "tc_util.cuh"
 
 namespace ccw {
 
 // learned.cu
 cudaError_t net_infer(const float* P, int C, int tj, const float* x, int N, float* act,
-                      float* emb, cudaStream_t st);
+                      float* emb, cudaStream_t st, int* status = nullptr, int path = 0,
+                      const void* wimg = nullptr);
 
 // Is level-J cell (ux, uy) inside the overlap strips of mask type `type`?
 __device__ __forceinline__ bool in_mask(int type, int ux, int uy, int Tj, int Oj) {
@@ -103,7 +105,8 @@ __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Nearest neighbours: scores s_c = table[type][c] . e over every candidate,
+// Nearest neighbours: scores s_c = table[type][c] . bf16(e) over every
+// candidate (BF16 table rows and query, FP32 sums),
 // the n_prop best by (score desc, index asc), and the relative gap
 // (s_1 - s_nprop) / max(|s_1|, eps). A two-level histogram over [-1, 1]
 // finds a threshold that keeps at least n_prop and at most kCollect
@@ -113,6 +116,7 @@ constexpr int kNnThreads = 256;
 constexpr int kBins = 1024;
 constexpr int kCollect = 512;
 constexpr int kScoreCache = 6144;   // candidates whose scores stay in shared memory
+constexpr int kSortSmall = 128;     // survivors sorted in registers (4 per lane)
 
 __device__ __forceinline__ float nn_score(const __nv_bfloat16* row, const float* e) {
   float s0 = 0.f, s1 = 0.f;
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel(const __grid_constant__ Wa
     atomicAdd(&stats[0], 1ull);
     atomicAdd(&stats[1], 1ull);
   }
-  if (tid < 64) e[tid] = a.emb[(int64_t)item * 64 + tid];
+  if (tid < 64) e[tid] = bf(a.emb[(int64_t)item * 64 + tid]);   // the BF16 query
   for (int b = tid; b < kBins; b += kNnThreads) hist[b] = 0;
   __syncthreads();
   const __nv_bfloat16* tab = a.tables + (int64_t)type * t.P * 64;
@@ -309,6 +313,185 @@ __device__ __forceinline__ float nn_key_score(uint64_t k) {
   return __uint_as_float((ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord);
 }
 
+// Selection of one data event by one warp from its scores sc[0 .. P): a
+// two-level histogram over [-1.5, 1.5) finds a threshold that keeps at least
+// n_prop and at most kCollect windows; the survivors' keys (score
+// descending, index ascending) are sorted (bitonic, the smallest power of two
+// >= their count and >= 64) and the first n_prop written with the gap.
+// hist: kBins ints, keys: kCollect words of this warp's shared memory.
+// Level-0 histogram bin of score v (-1 outside [-1.5, 1.5)).
+__device__ __forceinline__ int nn_bin0(float v) {
+  const float lo = -1.5f, hi = 1.5f, scale = kBins / (hi - lo);
+  return (v >= lo && v < hi) ? min(kBins - 1, max(0, (int)((v - lo) * scale))) : -1;
+}
+
+__device__ __forceinline__ void nn_select_warp(const WaveArgs& a, int item, const float* sc, int P,
+                                            int* hist, uint64_t* keys, int lane,
+                                            bool hist_ready = false) {
+  const TiDev& t = a.ti;
+  const int np = (int)min((int64_t)a.n_prop, t.P);
+  float lo = -1.5f, hi = 1.5f;
+  int above_prev = 0;
+  float thr = lo;
+  for (int level = 0; level < 2; ++level) {
+    const float scale = kBins / (hi - lo);
+    // hist_ready: the caller built the level-0 histogram (nn_bin0)
+    if (level > 0 || !hist_ready) {
+      for (int b = lane; b < kBins; b += 32) hist[b] = 0;
+      __syncwarp();
+      for (int cb = 0; cb < P; cb += 32) {
+        const int c = cb + lane;
+        int b = -1;
+        if (c < P) {
+          const float v = sc[c];
+          if (v >= lo && v < hi) b = min(kBins - 1, max(0, (int)((v - lo) * scale)));
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(same) - 1) atomicAdd(&hist[b], __popc(same));
+      }
+    }
+    __syncwarp();
+    // the highest bin b >= 1 whose count with everything above reaches np
+    // (else bin 0): lane L holds bins 32L .. 32L + 31
+    int part = 0;
+    for (int k = 0; k < 32; ++k) part += hist[32 * lane + k];
+    int suffix = part;   // bins of this lane and the lanes above it
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_down_sync(0xffffffffu, suffix, o);
+      if (lane + o < 32) suffix += v;
+    }
+    const int above_lanes = suffix - part;   // bins of the lanes above this one
+    int run = above_prev + above_lanes, fb = -1, fabove = 0;
+    for (int k = 31; k >= 0; --k) {
+      const int b = 32 * lane + k;
+      if (b > 0 && run + hist[b] >= np && fb < 0) {
+        fb = b;
+        fabove = run;
+      }
+      run += hist[b];
+      if (b == 0 && fb < 0) {
+        fb = -2;   // reached bin 0 without a hit: bin 0 with `run - hist[0]` above
+        fabove = run - hist[0];
+      }
+    }
+    const unsigned hits = __ballot_sync(0xffffffffu, fb >= 0);
+    int bsel, above;
+    if (hits) {
+      const int src = 31 - __clz(hits);
+      bsel = __shfl_sync(0xffffffffu, fb, src);
+      above = __shfl_sync(0xffffffffu, fabove, src);
+    } else {
+      bsel = 0;
+      above = __shfl_sync(0xffffffffu, fabove, 0);
+    }
+    const int inbin = hist[bsel];
+    thr = lo + bsel / scale;
+    // refine past kSortSmall survivors: the proposals and the fallback
+    // decisions are those of refining past kCollect (the finer threshold
+    // keeps a subset that still holds the n_prop best), the sort is cheaper
+    if (above + inbin <= kSortSmall || level == 1) break;
+    const float nlo = thr, nhi = lo + (bsel + 1) / scale;
+    above_prev = above;
+    __syncwarp();
+    lo = nlo;
+    hi = nhi;
+  }
+  // survivors: keys (score descending, index ascending)
+  int total = 0;
+  for (int cb = 0; cb < P; cb += 32) {
+    const int c = cb + lane;
+    const bool keep = c < P && sc[c] >= thr;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int k = total + __popc(bal & ((1u << lane) - 1u));
+      if (k < kCollect) keys[k] = nn_rank_key(sc[c] + 0.f, c);
+    }
+    total += __popc(bal);
+  }
+  const int ncoll = min(total, kCollect);
+  if (total > kCollect || ncoll < np) {
+    if (lane == 0) a.prop_gap[item] = -1.f;   // threshold not usable: full search
+    return;
+  }
+  __syncwarp();
+  if (ncoll <= kSortSmall) {
+    // bitonic sort of kSortSmall keys in registers: element e = 4 lane + r
+    uint64_t x[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = 4 * lane + r;
+      x[r] = e < ncoll ? keys[e] : kNoKey;
+    }
+#pragma unroll
+    for (int k = 2; k <= kSortSmall; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j >= 4) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int e = 4 * lane + r;
+            const uint64_t y = __shfl_xor_sync(0xffffffffu, x[r], j >> 2);
+            const bool up = (e & k) == 0, lower = (e & j) == 0;
+            x[r] = (lower == up) ? (x[r] < y ? x[r] : y) : (x[r] > y ? x[r] : y);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if ((r & j) == 0) {
+              const int e = 4 * lane + r;
+              const bool up = (e & k) == 0;
+              const uint64_t u = x[r], v = x[r ^ j];
+              if ((u > v) == up) {
+                x[r] = v;
+                x[r ^ j] = u;
+              }
+            }
+        }
+      }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = 4 * lane + r;
+      if (e < np) a.prop[(int64_t)item * a.n_prop + e] = (int)(x[r] & 0xFFFFFFFFu);
+    }
+    const uint64_t k1 = __shfl_sync(0xffffffffu, x[0], 0);
+    const int rn = (np - 1) & 3;
+    const uint64_t xn = rn == 0 ? x[0] : rn == 1 ? x[1] : rn == 2 ? x[2] : x[3];
+    const uint64_t kn = __shfl_sync(0xffffffffu, xn, (np - 1) >> 2);
+    if (lane == 0) {
+      const float s1 = nn_key_score(k1), sn = nn_key_score(kn);
+      a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+    }
+    return;
+  }
+  int L = 64;
+  while (L < ncoll) L <<= 1;
+  for (int k = ncoll + lane; k < L; k += 32) keys[k] = kNoKey;
+  __syncwarp();
+  // bitonic sort of L keys, ascending
+  for (int k = 2; k <= L; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < L; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint64_t x = keys[i], y = keys[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            keys[i] = y;
+            keys[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  for (int r = lane; r < np; r += 32)
+    a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
+  if (lane == 0) {
+    const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
+    a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+  }
+}
+
 __global__ void __launch_bounds__(kNnThreads) k_nnsel_multi(const __grid_constant__ WaveArgs a) {
   extern __shared__ unsigned char nn_smem[];
   NnMultiSmem& S = *reinterpret_cast<NnMultiSmem*>(nn_smem);
@@ -337,7 +520,7 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel_multi(const __grid_constan
   }
   for (int i = tid; i < kNnG * 64; i += kNnThreads) {
     const int g = i / 64, item = i0 + g;
-    S.e[g][i % 64] = item < a.n_items ? a.emb[(int64_t)item * 64 + i % 64] : 0.f;
+    S.e[g][i % 64] = item < a.n_items ? bf(a.emb[(int64_t)item * 64 + i % 64]) : 0.f;
   }
   __syncthreads();
   // scores: every row of a type present in the group, loaded once
@@ -360,111 +543,225 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel_multi(const __grid_constan
   __syncthreads();
   if (warp >= kNnG || !S.ok[warp]) return;
   // selection: one warp per event
-  const int g = warp, item = i0 + g;
-  const float* sc = cache + g * P;
-  int* hist = S.hist[g];
-  uint64_t* keys = S.keys[g];
-  const int np = (int)min((int64_t)a.n_prop, t.P);
-  float lo = -1.5f, hi = 1.5f;
-  int above_prev = 0;
-  float thr = lo;
-  for (int level = 0; level < 2; ++level) {
-    for (int b = lane; b < kBins; b += 32) hist[b] = 0;
-    __syncwarp();
-    const float scale = kBins / (hi - lo);
-    for (int cb = 0; cb < P; cb += 32) {
-      const int c = cb + lane;
-      int b = -1;
-      if (c < P) {
-        const float v = sc[c];
-        if (v >= lo && v < hi) b = min(kBins - 1, max(0, (int)((v - lo) * scale)));
-      }
-      const unsigned same = __match_any_sync(0xffffffffu, b);
-      if (b >= 0 && lane == __ffs(same) - 1) atomicAdd(&hist[b], __popc(same));
-    }
-    __syncwarp();
-    // the highest bin b >= 1 whose count with everything above reaches np
-    // (else bin 0): lane L holds bins 32L .. 32L + 31
-    int part = 0;
-    for (int k = 0; k < 32; ++k) part += hist[32 * lane + k];
-    int above_lanes = 0;   // bins of the lanes above this one
-    for (int L = 31; L > 0; --L) {
-      const int v = __shfl_sync(0xffffffffu, part, L);
-      if (L > lane) above_lanes += v;
-    }
-    int run = above_prev + above_lanes, fb = -1, fabove = 0;
-    for (int k = 31; k >= 0; --k) {
-      const int b = 32 * lane + k;
-      if (b > 0 && run + hist[b] >= np && fb < 0) {
-        fb = b;
-        fabove = run;
-      }
-      run += hist[b];
-      if (b == 0 && fb < 0) {
-        fb = -2;   // reached bin 0 without a hit: bin 0 with `run - hist[0]` above
-        fabove = run - hist[0];
-      }
-    }
-    const unsigned hits = __ballot_sync(0xffffffffu, fb >= 0);
-    int bsel, above;
-    if (hits) {
-      const int src = 31 - __clz(hits);
-      bsel = __shfl_sync(0xffffffffu, fb, src);
-      above = __shfl_sync(0xffffffffu, fabove, src);
-    } else {
-      bsel = 0;
-      above = __shfl_sync(0xffffffffu, fabove, 0);
-    }
-    const int inbin = hist[bsel];
-    thr = lo + bsel / scale;
-    if (above + inbin <= kCollect || level == 1) break;
-    const float nlo = thr, nhi = lo + (bsel + 1) / scale;
-    above_prev = above;
-    __syncwarp();
-    lo = nlo;
-    hi = nhi;
+  nn_select_warp(a, i0 + warp, cache + warp * P, P, S.hist[warp], S.keys[warp], lane);
+}
+
+// ---------------------------------------------------------------------------
+// The same selection with the scores from the tcgen05 tensor cores: the
+// tables are kept a second time in the MMA's K-major core-matrix layout, one
+// 16 KB block per 128 windows ([16 row groups][8 K chunks][8 rows][16 bytes],
+// zero rows past P); a CTA takes kNnTcG data events (MMA N = 16, columns
+// kNnTcG..15 zero), and for each mask type among them streams that type's
+// blocks through two shared-memory stages (bulk copies) into one MMA chain
+// (M = 128 windows, K = 64), the scores of every block in their own tensor
+// memory columns. The scores then move to shared memory, and one warp per
+// event selects as k_nnsel_multi does. For tables of at most kNnTcMaxP windows.
+// ---------------------------------------------------------------------------
+constexpr int kNnTcG = 8;
+constexpr int kNnTcMaxP = 24 * 128;
+constexpr int kNnTcBlock = 128 * 64;   // BF16 values per 128-window block
+constexpr int kNnTcMaxStages = 6;
+
+struct NnTcSmem {
+  uint64_t bar_load[kNnTcMaxStages], bar_mma[kNnTcMaxStages], bar_done;
+  uint32_t tslot;
+  int flag;
+  int type[kNnTcG], ok[kNnTcG];
+  int hist[kNnTcG][kBins];
+  uint64_t keys[kNnTcG][kCollect];
+};
+
+// Offset (bytes) of element (row, k) of a K-major operand block with 8-row
+// groups of all 8 K chunks: [rows / 8][8 chunks][8 rows][16 bytes].
+__host__ __device__ __forceinline__ int nn_tc_off(int row, int k) {
+  return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// k_nnsel_tc's shared memory for P windows: the fixed part, then as many
+// 16 KB stages (2 .. kNnTcMaxStages) as fit beside the scores.
+__host__ __device__ inline int nn_tc_head() { return ((int)sizeof(NnTcSmem) + 127) & ~127; }
+__host__ __device__ inline int nn_tc_stages(int64_t P) {
+  const int64_t room = 227 * 1024 - nn_tc_head() - 2048 - (int64_t)sizeof(float) * kNnTcG * P;
+  const int64_t n = room / 16384;
+  return (int)(n < 2 ? 2 : n > kNnTcMaxStages ? kNnTcMaxStages : n);
+}
+__host__ __device__ inline int nn_tc_smem(int64_t P) {
+  return nn_tc_head() + 2048 + nn_tc_stages(P) * 16384 + (int)(sizeof(float) * kNnTcG * P);
+}
+
+__global__ void k_tables_mma(const __nv_bfloat16* __restrict__ tables, int64_t P, int nblk,
+                             __nv_bfloat16* __restrict__ out) {
+  const int64_t n = (int64_t)16 * nblk * kNnTcBlock;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // i enumerates the source order (type, window, k) over the padded rows
+    const int k = (int)(i % 64);
+    const int64_t r = (i / 64) % ((int64_t)nblk * 128), type = i / 64 / ((int64_t)nblk * 128);
+    const __nv_bfloat16 v = r < P ? tables[(type * P + r) * 64 + k] : __float2bfloat16_rn(0.f);
+    const int64_t blk = type * nblk + r / 128;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(out) +
+                                      blk * (int64_t)kNnTcBlock * 2 +
+                                      nn_tc_off((int)(r % 128), k)) = v;
   }
-  // survivors: keys (score descending, index ascending)
-  int total = 0;
-  for (int cb = 0; cb < P; cb += 32) {
-    const int c = cb + lane;
-    const bool keep = c < P && sc[c] >= thr;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      const int k = total + __popc(bal & ((1u << lane) - 1u));
-      if (k < kCollect) keys[k] = nn_rank_key(sc[c] + 0.f, c);
+}
+
+__global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constant__ WaveArgs a) {
+  extern __shared__ __align__(128) unsigned char nn_smem[];
+  NnTcSmem& S = *reinterpret_cast<NnTcSmem*>(nn_smem);
+  const TiDev& t = a.ti;
+  const int P = (int)t.P;
+  const int NS = nn_tc_stages(P);
+  unsigned char* eb = nn_smem + nn_tc_head();                          // B: 16 rows
+  unsigned char* stage = eb + 2048;                                    // NS x 16 KB
+  float* cache = reinterpret_cast<float*>(stage + NS * 16384);        // [kNnTcG][P]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i0 = blockIdx.x * kNnTcG;
+  const int nblk = (P + 127) / 128;
+  pdl_trigger();
+  pdl_wait();
+  unsigned long long* stats = a.call ? a.call->learn_stats : nullptr;
+  if (tid < kNnTcG) {
+    const int item = i0 + tid;
+    int type = -1, ok = 0;
+    if (item < a.n_items) {
+      const int* meta = reinterpret_cast<const int*>(a.ev.base + (int64_t)item * a.ev.stride);
+      type = meta[kEvMaskType];
+      const bool known = meta[kEvKnown] > 0;
+      ok = known && usable_type(type);
+      if (!ok) a.prop_gap[item] = -1.f;   // no proposals: full search
+      if (stats && known) atomicAdd(&stats[0], 1ull);
+      if (stats && ok) atomicAdd(&stats[1], 1ull);
     }
-    total += __popc(bal);
+    S.type[tid] = ok ? type : -1;
+    S.ok[tid] = ok;
   }
-  const int ncoll = min(total, kCollect);
-  if (total > kCollect || ncoll < np) {
-    if (lane == 0) a.prop_gap[item] = -1.f;   // threshold not usable: full search
-    return;
+  // B operand: the BF16 query of event h in row h (rows kNnTcG..15 zero)
+  for (int i = tid; i < kNnTcG * kBins; i += kNnThreads) (&S.hist[0][0])[i] = 0;
+  for (int i = tid; i < 16 * 64; i += kNnThreads) {
+    const int h = i / 64, k = i % 64, item = i0 + h;
+    const float v = (h < kNnTcG && item < a.n_items) ? a.emb[(int64_t)item * 64 + k] : 0.f;
+    *reinterpret_cast<__nv_bfloat16*>(eb + nn_tc_off(h, k)) = __float2bfloat16_rn(v);
   }
-  for (int k = ncoll + lane; k < kCollect; k += 32) keys[k] = kNoKey;
-  __syncwarp();
-  // bitonic sort of kCollect keys, ascending
-  for (int k = 2; k <= kCollect; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < kCollect; i += 32) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint64_t x = keys[i], y = keys[l];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            keys[i] = y;
-            keys[l] = x;
+  uint32_t ncols = 32;
+  while ((int)ncols < nblk * 16) ncols <<= 1;
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&S.bar_load[k], 1);
+      mbar_init(&S.bar_mma[k], 1);
+    }
+    mbar_init(&S.bar_done, 1);
+    S.flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&S.tslot, ncols);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tslot;
+  const uint32_t idesc = instr_desc(true, 128, 16);
+  const uint32_t eb_addr = smem_u32(eb), st_addr = smem_u32(stage);
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+  // blocks are numbered over all passes (b = passes * nblk + j): block b
+  // uses stage b % NS, the (b / NS)-th use of that stage's barriers
+  int issued = 0, waited = 0;   // thread 0: blocks whose copy was issued / landed
+  uint32_t passes = 0;
+  for (int g = 0; g < kNnTcG; ++g) {
+    const int type = S.type[g];
+    if (type < 0) continue;
+    bool first = true;
+    for (int h = 0; h < g; ++h) first &= S.type[h] != type;
+    if (!first) continue;   // scored with an earlier event of this type
+    if (tid == 0) {
+      const __nv_bfloat16* tab = a.tables_mma + (int64_t)type * nblk * kNnTcBlock;
+      const int b0 = (int)passes * nblk;
+      // CTAs start at different blocks of the table so that they do not all
+      // read the same L2 lines at the same time
+      const int start = (int)((blockIdx.x * 5u) % (unsigned)nblk);
+      auto blk = [&](int b) { return (start + b - b0) % nblk; };
+      auto issue = [&](int b) {
+        const int sidx = b % NS;
+        mbar_arrive_expect_tx(&S.bar_load[sidx], 16384u);
+        bulk_g2s(stage + sidx * 16384, tab + (int64_t)blk(b) * kNnTcBlock, 16384u,
+                 &S.bar_load[sidx]);
+        issued = b + 1;
+      };
+      for (int b = b0; b < b0 + NS && b < b0 + nblk; ++b) issue(b);
+      bool ok = true;
+      for (int b = b0; b < b0 + nblk; ++b) {
+        const int sidx = b % NS;
+        if (!mbar_wait_bounded(&S.bar_load[sidx], (uint32_t)(b / NS) & 1u)) {
+          ok = false;
+          break;
+        }
+        waited = b + 1;
+        tc_fence_after();
+#pragma unroll
+        for (int k16 = 0; k16 < 4; ++k16)
+          mma_f16(tmem + (uint32_t)(blk(b) * 16),
+                  smem_desc(st_addr + (uint32_t)(sidx * 16384 + k16 * 256), 128u, 1024u),
+                  smem_desc(eb_addr + (uint32_t)(k16 * 256), 128u, 1024u), idesc,
+                  k16 > 0 ? 1u : 0u);
+        mma_commit(&S.bar_mma[sidx]);
+        // refill the stage of the previous block once its MMAs are done
+        // (the tensor pipe meanwhile works on this block)
+        const int pb = b - 1;
+        if (pb >= b0 && pb + NS < b0 + nblk) {
+          if (!mbar_wait_bounded(&S.bar_mma[pb % NS], (uint32_t)(pb / NS) & 1u)) {
+            ok = false;
+            break;
           }
+          issue(pb + NS);
         }
       }
-      __syncwarp();
+      if (!ok) S.flag = 1;
+      mma_commit(&S.bar_done);
+      // thread 0 alone waits (the others wait at the barrier, not polling
+      // beside it in its warp)
+      if (!mbar_wait_bounded(&S.bar_done, passes & 1u)) S.flag = 1;
     }
-  for (int r = lane; r < np; r += 32)
-    a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
-  if (lane == 0) {
-    const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
-    a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+    __syncthreads();
+    if (S.flag) break;
+    mbar_try_wait(&S.bar_done, passes & 1u);   // every thread observes the phase
+    ++passes;
+    tc_fence_after();
+    for (int j = half; j < nblk; j += 2) {
+      uint32_t v[16];
+      tmem_ld16(lane_base + (uint32_t)(j * 16), v);
+      const int c = 128 * j + quarter * 32 + lane;
+      if (c < P) {
+        // scores to shared memory, and the level-0 histogram of each event
+#pragma unroll
+        for (int h = 0; h < kNnTcG; ++h)
+          if (S.type[h] == type) {
+            const float sc = __uint_as_float(v[h]);
+            cache[h * P + c] = sc;
+            const int b = nn_bin0(sc);
+            if (b >= 0) atomicAdd(&S.hist[h][b], 1);
+          }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
   }
+  const bool failed = S.flag != 0;
+  if (failed && tid == 0) {
+    // a copy or commit never arrived: let what is in flight land (bounded)
+    if (a.status) atomicOr(a.status, kStatusTimeout);
+    mbar_wait_bounded(&S.bar_done, passes & 1u);
+    for (int b = waited; b < issued; ++b)
+      mbar_wait_bounded(&S.bar_load[b % NS], (uint32_t)(b / NS) & 1u);
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+  if (failed || warp >= kNnTcG || !S.ok[warp]) {
+    if (failed && warp < kNnTcG && lane == 0 && i0 + warp < a.n_items)
+      a.prop_gap[i0 + warp] = -1.f;   // no proposals: full search
+    return;
+  }
+  nn_select_warp(a, i0 + warp, cache + warp * P, P, S.hist[warp], S.keys[warp], lane, true);
 }
 
 // Event records from explicit block counts (the query entry point): known
@@ -560,7 +857,20 @@ __global__ void __launch_bounds__(256) k_rerank(const __grid_constant__ WaveArgs
       for (int row = part; row < t.rows; row += 4) {
         const float* wr = W + (ch * t.rows + row) * t.TjP;
         const float* pr = plane + (cx) + (int64_t)t.px * (cy + row);
-        for (int ux = 0; ux < t.Tj; ++ux) acc = fmaf(wr[ux], __ldg(pr + ux), acc);
+        // integer-valued products: the sum is exact in any order, so four
+        // partial sums keep four loads in flight
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int ux = 0;
+        for (; ux + 4 <= t.Tj; ux += 4) {
+          const float p0 = __ldg(pr + ux), p1 = __ldg(pr + ux + 1);
+          const float p2 = __ldg(pr + ux + 2), p3 = __ldg(pr + ux + 3);
+          s0 = fmaf(wr[ux], p0, s0);
+          s1 = fmaf(wr[ux + 1], p1, s1);
+          s2 = fmaf(wr[ux + 2], p2, s2);
+          s3 = fmaf(wr[ux + 3], p3, s3);
+        }
+        for (; ux < t.Tj; ++ux) s0 = fmaf(wr[ux], __ldg(pr + ux), s0);
+        acc += (s0 + s1) + (s2 + s3);
       }
     }
   }
@@ -606,11 +916,29 @@ __global__ void __launch_bounds__(256) k_rerank(const __grid_constant__ WaveArgs
 }
 
 // ---------------------------------------------------------------------------
+int64_t enc_tc_image_bytes(int C, int tj);
+bool net_infer_fused_fits(int C, int tj);
+cudaError_t net_infer_tc_records(const float* P, const void* wimg, int C, int tj,
+                                 const unsigned char* rec, int64_t stride, int counts_off,
+                                 float inv, int N, float* emb, int* status, cudaStream_t st);
+
+// Kernel launches of one launch_encode_items.
+int encode_items_launches(int F, int Tj, bool img) {
+  if (img && enc_tc_image_bytes(F, Tj) > 0) return 1;
+  return 1 + (net_infer_fused_fits(F, Tj) ? 1 : 5);
+}
+
 cudaError_t launch_encode_items(const WaveArgs& a, float* x, float* act, bool pdl,
                                 cudaStream_t st) {
+  if (a.enc_img && enc_tc_image_bytes(a.ti.F, a.ti.Tj) > 0)
+    // the tensor-core pass reads the block counts from the event records
+    return net_infer_tc_records(a.net, a.enc_img, a.ti.F, a.ti.Tj, a.ev.base, a.ev.stride,
+                                a.ev.counts_off, 1.f / (float)a.ti.sd, a.n_items, a.emb,
+                                a.status, st);
   cudaError_t e = launch_pdl(k_event_inputs, dim3(a.n_items), dim3(128), 0, st, pdl, a, x);
   if (e != cudaSuccess) return e;
-  return net_infer(a.net, a.ti.F, a.ti.Tj, x, a.n_items, act, a.emb, st);
+  return net_infer(a.net, a.ti.F, a.ti.Tj, x, a.n_items, act, a.emb, st, a.status, 0,
+                   a.enc_img);
 }
 
 // Table of mask type `type`: embeddings of every candidate window, in
@@ -622,7 +950,9 @@ cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tab
     k_window_inputs<<<n, 128, 0, st>>>(a, type, c0, x);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = net_infer(a.net, a.ti.F, a.ti.Tj, x, n, act, emb, st)) != cudaSuccess) return e;
+    if ((e = net_infer(a.net, a.ti.F, a.ti.Tj, x, n, act, emb, st, a.status, 0, a.enc_img)) !=
+        cudaSuccess)
+      return e;
     k_to_bf16<<<256, 256, 0, st>>>(emb, tables + ((int64_t)type * a.ti.P + c0) * 64,
                                    (int64_t)n * 64);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -630,8 +960,35 @@ cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tab
   return cudaSuccess;
 }
 
+cudaError_t launch_tables_mma(const __nv_bfloat16* tables, int64_t P, __nv_bfloat16* out,
+                              cudaStream_t st) {
+  const int nblk = (int)((P + 127) / 128);
+  k_tables_mma<<<1024, 256, 0, st>>>(tables, P, nblk, out);
+  return cudaGetLastError();
+}
+
+int64_t tables_mma_elems(int64_t P) {
+  return P <= kNnTcMaxP ? (int64_t)16 * ((P + 127) / 128) * kNnTcBlock : 0;
+}
+
+static int g_nn_path = 0;   // ccw_set_nn_path
+
 cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st) {
-  if (a.ti.P <= kScoreCache) {
+  if (g_nn_path == 0 && a.tables_mma && a.ti.P <= kNnTcMaxP) {
+    // one CTA per SM when the scores take more than half of the tensor memory
+    int smem = nn_tc_smem(a.ti.P);
+    if ((a.ti.P + 127) / 128 * 16 > 256 && smem < 120 * 1024) smem = 120 * 1024;
+    static int configured = 0;
+    if (smem > configured) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_nnsel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
+    return launch_pdl(k_nnsel_tc, dim3((a.n_items + kNnTcG - 1) / kNnTcG), dim3(kNnThreads),
+                      smem, st, pdl, a);
+  }
+  if (g_nn_path <= 1 && a.ti.P <= kScoreCache) {
     const int smem = (int)(sizeof(NnMultiSmem) + sizeof(float) * kNnG * a.ti.P);
     static int configured = 0;
     if (smem > configured) {
@@ -671,3 +1028,9 @@ cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st) {
 }
 
 }  // namespace ccw
+
+extern "C" int ccw_set_nn_path(int32_t path) {
+  if (path < 0 || path > 2) return CCW_EINVAL;
+  ccw::g_nn_path = path;
+  return CCW_OK;
+}

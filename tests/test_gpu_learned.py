@@ -57,3 +57,36 @@ def test_training_reduces_the_loss(ccw):
         l = net.train_step(a[i0:i0 + 64], c[i0:i0 + 64], tau=0.1, lr=2e-3, bf16=1)
         losses.append(float(l.item()))
     assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:5])
+
+
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().float().numpy()
+
+
+@pytest.mark.parametrize("C,tj,N", [(2, 12, 7 * 9 + 3), (3, 16, 3 * 5 + 2), (2, 9, 8 * 3 + 1),
+                                    (1, 7, 1), (2, 20, 6)])
+def test_inference_pass_matches_the_encoder(ccw, C, tj, N):
+    """The proposal's inference pass (the tcgen05 implicit-GEMM kernel where
+    the shape fits, several sample groups and a ragged last group) embeds like
+    the FP64 encoder oracle with BF16 weights and non-zero biases, and like
+    the fused FP32-lane kernel up to the BF16 rounding of the activations."""
+    net = ccw.Net(C, tj, seed=11)
+    rng = np.random.default_rng(C * 100 + tj)
+    d = E.unpack(net.get(0), C, tj)
+    for name in ("b1", "b2", "b3", "bf"):
+        d[name] = rng.normal(0.0, 0.05, d[name].shape)
+    flat = E.pack(d, C, tj).astype(np.float32)
+    net.set(flat)
+    ref_p = {k: (_bf16(v).astype(np.float64) if k[0] == "w" else v.astype(np.float32)
+                 .astype(np.float64)) for k, v in E.unpack(flat, C, tj).items()}
+    # inputs as the proposal makes them: block counts / 2^(d J), exact in BF16
+    x = (rng.integers(0, 17, (N, C, tj, tj)) / 16.0).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    tc = net.embed(xt, bf16=2).cpu().numpy().astype(np.float64)
+    simt = net.embed(xt, bf16=3).cpu().numpy().astype(np.float64)
+    ref, _ = E.forward(ref_p, x.astype(np.float64))
+    for got in (tc, simt):
+        assert np.all(np.abs(np.linalg.norm(got, axis=1) - 1.0) < 1e-5)
+        assert np.all((got * ref).sum(1) >= 0.998)
+        assert np.abs(got - ref).max() <= 0.03
+    assert np.abs(tc - simt).max() <= 0.02

@@ -176,11 +176,19 @@ def test_tables_equal_the_fp64_encoder_oracle(ccw, ti):
     ti.attach_proposal(None)
 
 
-def test_nearest_windows_equal_a_numpy_ranking(ccw, ti):
+@pytest.fixture(params=[0, 1, 2])
+def nn_path(request, ccw):
+    ccw.set_nn_path(request.param)
+    yield request.param
+    ccw.set_nn_path(0)
+
+
+def test_nearest_windows_equal_a_numpy_ranking(ccw, ti, nn_path):
     """The selector's n_prop proposals are the top of a numpy ranking of the
-    same tables by dot product with the event's embedding (score descending,
-    candidate ascending), up to FP32 rounding at the cut; its gap is the
-    relative spread of their scores."""
+    same tables by dot product with the event's BF16 embedding (score
+    descending, candidate ascending), up to FP32 rounding at the cut; its gap
+    is the relative spread of their scores. Each selector kernel: tensor
+    cores, FP32 lanes with several events per CTA, one CTA per event."""
     net = ccw.Net(F, TJ, seed=6)
     ti.attach_proposal(net, 64, 0.0)
     tables = ti.export(4).float().cpu().numpy().astype(np.float64)
@@ -190,7 +198,8 @@ def test_nearest_windows_equal_a_numpy_ranking(ccw, ti):
     prop, gap, typ = ti.proposal_query(c)
     prop, gap, typ = prop.cpu().numpy(), gap.cpu().numpy(), typ.cpu().numpy()
     x, _ = ti.proposal_inputs(0, counts=c)
-    e = net.embed(x, bf16=1).cpu().numpy().astype(np.float64)
+    # the query's own inference pass, rounded to BF16 as the selectors take it
+    e = bf16_round(net.embed(x, bf16=2).cpu().numpy()).astype(np.float64)
     eps = 1e-5
     checked = 0
     for i in range(len(typ)):
