@@ -119,6 +119,9 @@ def parse_args():
     ap.add_argument("--vt-ext", type=int, default=0,
                     help="non-causal conditioning: hard data up to this many cells beyond the "
                          "template's forward edges join the mismatch count (0 = off)")
+    ap.add_argument("--all-shift", action="store_true",
+                    help="all-shift (polyphase) candidates: every fine offset of the TI, "
+                         "not only block-aligned ones (2D, tensor cores)")
     ap.add_argument("--boundary-cut", action="store_true",
                     help="paste through the minimum-error boundary cuts (2D)")
     ap.add_argument("--learned", action="store_true",
@@ -535,6 +538,8 @@ def ours_line(args, world, m):
         line["config"]["vt_ext"] = args.vt_ext
     if getattr(args, "boundary_cut", False):
         line["config"]["boundary_cut"] = 1
+    if getattr(args, "all_shift", False):
+        line["config"]["all_shift"] = 1
     if m.get("autotune") is not None:
         line["config"]["autotune"] = m["autotune"]
     if m.get("e2e_ms"):
@@ -640,14 +645,15 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
                          hd_cells=hd_dev[0][0], hd_vals=hd_dev[0][1],
                          real_base=gr["real_base"], out=outs[0], precision=precision,
                          learned=1 if learned else 0, ccf_tile=tile,
-                         vt_ext=args.vt_ext, boundary_cut=int(args.boundary_cut))
+                         vt_ext=args.vt_ext, boundary_cut=int(args.boundary_cut),
+                         all_shift=int(getattr(args, "all_shift", False)))
             return outs
         res = ccw.simulate_groups(
             g, [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
                      hd_cells=h[0], hd_vals=h[1]) for gr, h in zip(groups, hd_dev)],
             topk=w["K"], seed=w["seed"], precision=precision,
             learned=1 if learned else 0, ccf_tile=tile, vt_ext=args.vt_ext,
-            boundary_cut=int(args.boundary_cut))
+            boundary_cut=int(args.boundary_cut), all_shift=int(getattr(args, "all_shift", False)))
         return [r[0] for r in res]
 
     for _ in range(max(args.warmup, 0)):

@@ -70,6 +70,8 @@ cudaError_t launch_encode_tables(const WaveArgs& a, int type, __nv_bfloat16* tab
                                  float* act, float* emb, int chunk, cudaStream_t st);
 cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st);
 int encode_items_launches(int F, int Tj, bool img);
+bool nnsel_fuses_rerank(const WaveArgs& a);
+bool nnsel_fuses_rerank_shape(int64_t P, int nch, int rows, int Tj, int n_prop);
 cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st);
 cudaError_t launch_records_from_counts(const WaveArgs& a, const uint8_t* counts,
                                       int32_t* type_out, cudaStream_t st);
@@ -1308,18 +1310,24 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   // launches; lane l takes slots [l n / L, (l + 1) n / L) of every group
   std::vector<std::vector<std::vector<int4>>> waves(
       n_lanes, std::vector<std::vector<int4>>(pl->n_waves));
+  // Within a wave the items run patch-major: consecutive items are the same
+  // patch of successive realizations, so they share the overlap mask type
+  // (the learned proposal's selector scores one table per CTA).
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
-    for (int r = 0; r < g.n_real; ++r) {
-      const int lane = (int)((int64_t)r * n_lanes / g.n_real);
-      for (int64_t pp = 0; pp < g.n_patches; ++pp) {
-        const int ix = (int)(pp % g.np[0]), iy = (int)((pp / g.np[0]) % g.np[1]),
-                  iz = (int)(pp / ((int64_t)g.np[0] * g.np[1]));
+    for (int64_t pp = 0; pp < g.n_patches; ++pp) {
+      const int ix = (int)(pp % g.np[0]), iy = (int)((pp / g.np[0]) % g.np[1]),
+                iz = (int)(pp / ((int64_t)g.np[0] * g.np[1]));
+      for (int r = 0; r < g.n_real; ++r) {
+        const int lane = (int)((int64_t)r * n_lanes / g.n_real);
         waves[lane][ix + 2 * iy + 4 * iz].push_back(make_int4(i, r, (int)pp, 0));
       }
     }
   }
   std::vector<int4> items;
+  const bool learned_fused =
+      p->learned && nnsel_fuses_rerank_shape(t->P, p->score_mode == 0 ? t->F - 1 : 1, t->rows,
+                                             t->Tj, t->n_prop);
   pl->lanes.resize(n_lanes);
   pl->max_items = 0;
   pl->launches_per_call = 0;
@@ -1330,8 +1338,12 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
       ln.wave_off[w] = (int64_t)items.size();
       items.insert(items.end(), waves[l][w].begin(), waves[l][w].end());
       ln.max_items = std::max<int>(ln.max_items, (int)waves[l][w].size());
+      // learned: events, the encoder, the selector, the re-rank unless the
+      // selector does it, the CCF of the fallbacks, finish
       pl->launches_per_call +=
-          (p->learned ? 5 + encode_items_launches(t->F, t->Tj, t->d_enc_img != nullptr) : 3) *
+          (p->learned ? 4 + encode_items_launches(t->F, t->Tj, t->d_enc_img != nullptr) +
+                            (learned_fused ? 0 : 1)
+                      : 3) *
           ((waves[l][w].size() + 65534) / 65535);
     }
     ln.wave_off[pl->n_waves] = (int64_t)items.size();
@@ -1521,7 +1533,7 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, s
           return cuda_fail(e, "proposal kernel launch");
         if (prof) cudaEventRecordWithFlags(pev[1], st, cudaEventRecordExternal);
         if ((e = launch_nnsel(c, !prof, st)) != cudaSuccess ||
-            (e = launch_rerank(c, true, st)) != cudaSuccess)
+            (!nnsel_fuses_rerank(c) && (e = launch_rerank(c, true, st)) != cudaSuccess))
           return cuda_fail(e, "proposal kernel launch");
         if (prof) cudaEventRecordWithFlags(pev[2], st, cudaEventRecordExternal);
       }

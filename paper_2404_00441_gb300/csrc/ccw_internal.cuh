@@ -230,6 +230,7 @@ struct WaveArgs {
   int* prop;                // [n_items][n_prop] proposals
   float* prop_gap;          // [n_items] relative embedding gap of the proposals
   int n_prop;
+  int fuse_rerank;          // the selector re-ranks its own proposals (no k_rerank)
   int Oj;                   // overlap in level-J blocks
   // paste and conditioning variants (simulation mode)
   int vt_ext;               // cells the virtual template extends the window forward

@@ -319,15 +319,69 @@ __device__ __forceinline__ float nn_key_score(uint64_t k) {
 // descending, index ascending) are sorted (bitonic, the smallest power of two
 // >= their count and >= 64) and the first n_prop written with the gap.
 // hist: kBins ints, keys: kCollect words of this warp's shared memory.
+// The n_prop best of ncoll <= kSortSmall survivor keys (keys[0 .. ncoll)):
+// bitonic sort in registers (element e = 4 lane + r), proposals written, gap
+// written by lane 0 and returned to every lane. One warp.
+__device__ __forceinline__ float nn_sort_small_warp(const WaveArgs& a, int item,
+                                                    const uint64_t* keys, int ncoll, int np,
+                                                    int lane) {
+  // bitonic sort of kSortSmall keys in registers: element e = 4 lane + r
+  uint64_t x[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = 4 * lane + r;
+    x[r] = e < ncoll ? keys[e] : kNoKey;
+  }
+#pragma unroll
+  for (int k = 2; k <= kSortSmall; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int e = 4 * lane + r;
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, x[r], j >> 2);
+          const bool up = (e & k) == 0, lower = (e & j) == 0;
+          x[r] = (lower == up) ? (x[r] < y ? x[r] : y) : (x[r] > y ? x[r] : y);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if ((r & j) == 0) {
+            const int e = 4 * lane + r;
+            const bool up = (e & k) == 0;
+            const uint64_t u = x[r], v = x[r ^ j];
+            if ((u > v) == up) {
+              x[r] = v;
+              x[r ^ j] = u;
+            }
+          }
+      }
+    }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = 4 * lane + r;
+    if (e < np) a.prop[(int64_t)item * a.n_prop + e] = (int)(x[r] & 0xFFFFFFFFu);
+  }
+  const uint64_t k1 = __shfl_sync(0xffffffffu, x[0], 0);
+  const int rn = (np - 1) & 3;
+  const uint64_t xn = rn == 0 ? x[0] : rn == 1 ? x[1] : rn == 2 ? x[2] : x[3];
+  const uint64_t kn = __shfl_sync(0xffffffffu, xn, (np - 1) >> 2);
+  const float s1 = nn_key_score(k1), sn = nn_key_score(kn);
+  const float gap = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+  if (lane == 0) a.prop_gap[item] = gap;
+  return gap;
+}
+
 // Level-0 histogram bin of score v (-1 outside [-1.5, 1.5)).
 __device__ __forceinline__ int nn_bin0(float v) {
   const float lo = -1.5f, hi = 1.5f, scale = kBins / (hi - lo);
   return (v >= lo && v < hi) ? min(kBins - 1, max(0, (int)((v - lo) * scale))) : -1;
 }
 
-__device__ __forceinline__ void nn_select_warp(const WaveArgs& a, int item, const float* sc, int P,
-                                            int* hist, uint64_t* keys, int lane,
-                                            bool hist_ready = false) {
+__device__ __forceinline__ float nn_select_warp(const WaveArgs& a, int item, const float* sc, int P,
+                                             int* hist, uint64_t* keys, int lane,
+                                             bool hist_ready = false) {
   const TiDev& t = a.ti;
   const int np = (int)min((int64_t)a.n_prop, t.P);
   float lo = -1.5f, hi = 1.5f;
@@ -412,58 +466,10 @@ __device__ __forceinline__ void nn_select_warp(const WaveArgs& a, int item, cons
   const int ncoll = min(total, kCollect);
   if (total > kCollect || ncoll < np) {
     if (lane == 0) a.prop_gap[item] = -1.f;   // threshold not usable: full search
-    return;
+    return -1.f;
   }
   __syncwarp();
-  if (ncoll <= kSortSmall) {
-    // bitonic sort of kSortSmall keys in registers: element e = 4 lane + r
-    uint64_t x[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = 4 * lane + r;
-      x[r] = e < ncoll ? keys[e] : kNoKey;
-    }
-#pragma unroll
-    for (int k = 2; k <= kSortSmall; k <<= 1)
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        if (j >= 4) {
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int e = 4 * lane + r;
-            const uint64_t y = __shfl_xor_sync(0xffffffffu, x[r], j >> 2);
-            const bool up = (e & k) == 0, lower = (e & j) == 0;
-            x[r] = (lower == up) ? (x[r] < y ? x[r] : y) : (x[r] > y ? x[r] : y);
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-            if ((r & j) == 0) {
-              const int e = 4 * lane + r;
-              const bool up = (e & k) == 0;
-              const uint64_t u = x[r], v = x[r ^ j];
-              if ((u > v) == up) {
-                x[r] = v;
-                x[r ^ j] = u;
-              }
-            }
-        }
-      }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = 4 * lane + r;
-      if (e < np) a.prop[(int64_t)item * a.n_prop + e] = (int)(x[r] & 0xFFFFFFFFu);
-    }
-    const uint64_t k1 = __shfl_sync(0xffffffffu, x[0], 0);
-    const int rn = (np - 1) & 3;
-    const uint64_t xn = rn == 0 ? x[0] : rn == 1 ? x[1] : rn == 2 ? x[2] : x[3];
-    const uint64_t kn = __shfl_sync(0xffffffffu, xn, (np - 1) >> 2);
-    if (lane == 0) {
-      const float s1 = nn_key_score(k1), sn = nn_key_score(kn);
-      a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
-    }
-    return;
-  }
+  if (ncoll <= kSortSmall) return nn_sort_small_warp(a, item, keys, ncoll, np, lane);
   int L = 64;
   while (L < ncoll) L <<= 1;
   for (int k = ncoll + lane; k < L; k += 32) keys[k] = kNoKey;
@@ -486,9 +492,110 @@ __device__ __forceinline__ void nn_select_warp(const WaveArgs& a, int item, cons
     }
   for (int r = lane; r < np; r += 32)
     a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
+  const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
+  const float gap = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+  if (lane == 0) a.prop_gap[item] = gap;
+  return gap;
+}
+
+// The exact re-rank of k_rerank done by the selecting warp right after its
+// selection (simulation mode): Eq. CCW on the event's level-J weights for the
+// n_prop proposals (two per lane), the hard-data mismatches, the K best keys
+// in the item's first partial list, and the item marked resolved. wsm holds
+// at least nch * rows * Tj floats, ksm at least K words (this warp's).
+__device__ __forceinline__ void nn_rerank_warp(const WaveArgs& a, int item, float gap, float* wsm,
+                                               uint64_t* ksm, int lane) {
+  const TiDev& t = a.ti;
+  unsigned char* rec = a.ev.base + (int64_t)item * a.ev.stride;
+  int* meta = reinterpret_cast<int*>(rec);
+  if (meta[kEvKnown] == 0 || gap < 0.f || gap < a.call->gap_theta) return;
+  const int np = (int)min((int64_t)a.n_prop, t.P);
+  const int K = a.K;
+  const int Kp = (int)min((int64_t)K, (int64_t)np);
+  const float* W = reinterpret_cast<const float*>(rec + a.ev.w_off);
+  const int2* hdl = reinterpret_cast<const int2*>(rec + a.ev.hd_off);
+  const int nhd = meta[kEvNHd], cons = meta[kEvConst];
+  const int nw = t.nch * t.rows * t.Tj;
+  for (int i = lane; i < nw; i += 32) {
+    const int ux = i % t.Tj, r = i / t.Tj;
+    wsm[i] = W[r * t.TjP + ux];
+  }
+  __syncwarp();
+  // both proposals of the lane row by row, eight loads in flight
+  int cq[2], cxq[2], cyq[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int pi = lane + 32 * q;
+    cq[q] = pi < np ? a.prop[(int64_t)item * a.n_prop + pi] : 0;
+    cxq[q] = cq[q] % t.cd[0];
+    cyq[q] = cq[q] / t.cd[0];
+  }
+  float acc[2] = {0.f, 0.f};
+  for (int ch = 0; ch < t.nch; ++ch) {
+    const float* plane = t.planes + (int64_t)(t.plane0 + ch) * t.plane_vol;
+    for (int row = 0; row < t.rows; ++row) {
+      const float* wr = wsm + (ch * t.rows + row) * t.Tj;
+      const float* p0 = plane + cxq[0] + (int64_t)t.px * (cyq[0] + row);
+      const float* p1 = plane + cxq[1] + (int64_t)t.px * (cyq[1] + row);
+      // integer-valued products: the sums are exact in any order
+      float s0 = 0.f, s1 = 0.f, u0 = 0.f, u1 = 0.f;
+      int ux = 0;
+      for (; ux + 4 <= t.Tj; ux += 4) {
+        const float a0 = __ldg(p0 + ux), a1 = __ldg(p0 + ux + 1);
+        const float a2 = __ldg(p0 + ux + 2), a3 = __ldg(p0 + ux + 3);
+        const float b0 = __ldg(p1 + ux), b1 = __ldg(p1 + ux + 1);
+        const float b2 = __ldg(p1 + ux + 2), b3 = __ldg(p1 + ux + 3);
+        const float w0 = wr[ux], w1 = wr[ux + 1], w2 = wr[ux + 2], w3 = wr[ux + 3];
+        s0 = fmaf(w0, a0, s0);
+        s1 = fmaf(w1, a1, s1);
+        s0 = fmaf(w2, a2, s0);
+        s1 = fmaf(w3, a3, s1);
+        u0 = fmaf(w0, b0, u0);
+        u1 = fmaf(w1, b1, u1);
+        u0 = fmaf(w2, b2, u0);
+        u1 = fmaf(w3, b3, u1);
+      }
+      for (; ux < t.Tj; ++ux) {
+        s0 = fmaf(wr[ux], __ldg(p0 + ux), s0);
+        u0 = fmaf(wr[ux], __ldg(p1 + ux), u0);
+      }
+      acc[0] += s0 + s1;
+      acc[1] += u0 + u1;
+    }
+  }
+  uint64_t key[2] = {kNoKey, kNoKey};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (lane + 32 * q >= np) continue;
+    const uint8_t* tb =
+        t.ti + (int64_t)t.s * cxq[q] + (int64_t)t.tp[0] * ((int64_t)t.s * cyq[q]);
+    int mis = 0;
+    for (int k = 0; k < nhd; ++k) {
+      const int2 e = hdl[k];
+      mis += (__ldg(tb + e.x) != (uint8_t)(e.y & 0xFF));
+    }
+    key[q] = make_key(mis, __float2int_rn(acc[q]) + cons, cq[q]);
+  }
+  // the Kp smallest keys, in order
+  uint64_t prev = 0;
+  for (int r = 0; r < Kp; ++r) {
+    uint64_t m = kNoKey;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if ((r == 0 || key[q] > prev) && key[q] < m) m = key[q];
+    m = warp_min_u64(m);
+    prev = m;
+    if (lane == 0) ksm[r] = m;
+  }
+  __syncwarp();
+  unsigned long long* dst = a.part + (int64_t)item * a.n_parts * K;
+  for (int i = lane; i < a.n_parts * K; i += 32) {
+    const int p = i / K, r = i % K;
+    dst[i] = (p == 0 && r < Kp) ? ksm[r] : kNoKey;
+  }
   if (lane == 0) {
-    const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
-    a.prop_gap[item] = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+    meta[kEvResolved] = 1;
+    if (a.call->learn_stats) atomicAdd(&a.call->learn_stats[2], 1ull);
   }
 }
 
@@ -543,7 +650,10 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel_multi(const __grid_constan
   __syncthreads();
   if (warp >= kNnG || !S.ok[warp]) return;
   // selection: one warp per event
-  nn_select_warp(a, i0 + warp, cache + warp * P, P, S.hist[warp], S.keys[warp], lane);
+  const float gap =
+      nn_select_warp(a, i0 + warp, cache + warp * P, P, S.hist[warp], S.keys[warp], lane);
+  if (a.fuse_rerank)
+    nn_rerank_warp(a, i0 + warp, gap, reinterpret_cast<float*>(S.hist[warp]), S.keys[warp], lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -562,12 +672,21 @@ constexpr int kNnTcMaxP = 24 * 128;
 constexpr int kNnTcBlock = 128 * 64;   // BF16 values per 128-window block
 constexpr int kNnTcMaxStages = 6;
 
+// Histograms of the tensor-core selector: bin b at b + b / 32, so that lane L
+// reading its 32 bins 32 L .. 32 L + 31 touches 32 different banks.
+constexpr int kBinsPad = kBins + kBins / 32;
+__device__ __forceinline__ int hpad(int b) { return b + (b >> 5); }
+
 struct NnTcSmem {
   uint64_t bar_load[kNnTcMaxStages], bar_mma[kNnTcMaxStages], bar_done;
   uint32_t tslot;
   int flag;
   int type[kNnTcG], ok[kNnTcG];
-  int hist[kNnTcG][kBins];
+  // per event: threshold, level-1 range, count above it, survivors, state
+  float thr[kNnTcG], lo1[kNnTcG], hi1[kNnTcG];
+  int above0[kNnTcG], need1[kNnTcG], cnt[kNnTcG], state[kNnTcG];
+  float gap[kNnTcG];
+  int hist[kNnTcG][kBinsPad];
   uint64_t keys[kNnTcG][kCollect];
 };
 
@@ -587,6 +706,181 @@ __host__ __device__ inline int nn_tc_stages(int64_t P) {
 }
 __host__ __device__ inline int nn_tc_smem(int64_t P) {
   return nn_tc_head() + 2048 + nn_tc_stages(P) * 16384 + (int)(sizeof(float) * kNnTcG * P);
+}
+
+// The threshold bin of a padded histogram (one warp, lane L taking bins
+// 32 L .. 32 L + 31): the highest bin b >= 1 whose count together with
+// everything above it (above_prev lies above the histogram's range) reaches
+// np, else bin 0; `above` is the count above that bin. The search of
+// nn_select_warp on the padded layout.
+__device__ __forceinline__ void nn_threshold_pad(const int* hist, int np, int above_prev, int lane,
+                                                 int& bsel, int& above) {
+  const int* hl = hist + 33 * lane;   // bins 32 lane .. 32 lane + 31
+  int part = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) part += hl[k];
+  int suffix = part;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_down_sync(0xffffffffu, suffix, o);
+    if (lane + o < 32) suffix += v;
+  }
+  int run = above_prev + suffix - part, fb = -1, fabove = 0;
+#pragma unroll
+  for (int k = 31; k >= 0; --k) {
+    const int b = 32 * lane + k, h = hl[k];
+    if (b > 0 && run + h >= np && fb < 0) {
+      fb = b;
+      fabove = run;
+    }
+    run += h;
+    if (b == 0 && fb < 0) {
+      fb = -2;
+      fabove = run - h;
+    }
+  }
+  const unsigned hits = __ballot_sync(0xffffffffu, fb >= 0);
+  if (hits) {
+    const int src = 31 - __clz(hits);
+    bsel = __shfl_sync(0xffffffffu, fb, src);
+    above = __shfl_sync(0xffffffffu, fabove, src);
+  } else {
+    bsel = 0;
+    above = __shfl_sync(0xffffffffu, fabove, 0);
+  }
+}
+
+// Selection for the CTA's kNnTcG events in CTA-wide phases, with the
+// thresholds, survivors and proposals of nn_select_warp: each warp finds its
+// event's threshold (level 0 from the histogram the epilogue built, level 1
+// over the threshold bin when more than kSortSmall would survive), all
+// threads then build the level-1 histograms and collect every event's
+// survivors; a warp sorts up to kSortSmall survivors in registers, larger
+// sets are sorted by the whole CTA in shared memory. Sets S.gap[h] (-1: the
+// event falls back to the full search).
+__device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
+                                                 const float* cache, int P, int i0, int tid,
+                                                 int warp, int lane) {
+  const int np = (int)min((int64_t)a.n_prop, a.ti.P);
+  const bool mine = warp < kNnTcG && S.ok[warp];
+  if (mine) {
+    const float lo = -1.5f, hi = 1.5f, scale = kBins / (hi - lo);
+    int bsel, above;
+    nn_threshold_pad(S.hist[warp], np, 0, lane, bsel, above);
+    const int inbin = S.hist[warp][hpad(bsel)];
+    const float thr = lo + bsel / scale;
+    if (lane == 0) {
+      S.thr[warp] = thr;
+      S.need1[warp] = above + inbin > kSortSmall;
+      S.lo1[warp] = thr;
+      S.hi1[warp] = lo + (bsel + 1) / scale;
+      S.above0[warp] = above;
+    }
+  } else if (warp < kNnTcG && lane == 0) {
+    S.need1[warp] = 0;
+  }
+  if (warp < kNnTcG && lane == 0) S.cnt[warp] = 0;
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int h = 0; h < kNnTcG; ++h) any |= S.ok[h] && S.need1[h];
+  if (any) {
+    for (int i = tid; i < kNnTcG * kBinsPad; i += kNnThreads) {
+      const int h = i / kBinsPad;
+      if (S.ok[h] && S.need1[h]) (&S.hist[0][0])[i] = 0;
+    }
+    __syncthreads();
+    for (int h = 0; h < kNnTcG; ++h) {
+      if (!S.ok[h] || !S.need1[h]) continue;
+      const float lo = S.lo1[h], hi = S.hi1[h], scale = kBins / (hi - lo);
+      const float* sc = cache + h * P;
+      for (int c = tid; c < P; c += kNnThreads) {
+        const float v = sc[c];
+        if (v >= lo && v < hi)
+          atomicAdd(&S.hist[h][hpad(min(kBins - 1, max(0, (int)((v - lo) * scale))))], 1);
+      }
+    }
+    __syncthreads();
+    if (mine && S.need1[warp]) {
+      const float lo = S.lo1[warp], hi = S.hi1[warp], scale = kBins / (hi - lo);
+      int bsel, above;
+      nn_threshold_pad(S.hist[warp], np, S.above0[warp], lane, bsel, above);
+      if (lane == 0) S.thr[warp] = lo + bsel / scale;
+    }
+    __syncthreads();
+  }
+  // survivors of every event, their keys in any order (sorted below)
+  for (int h = 0; h < kNnTcG; ++h) {
+    if (!S.ok[h]) continue;
+    const float thr = S.thr[h];
+    const float* sc = cache + h * P;
+    for (int c = tid; c < P; c += kNnThreads) {
+      const float v = sc[c];
+      if (v >= thr) {
+        const int k = atomicAdd(&S.cnt[h], 1);
+        if (k < kCollect) S.keys[h][k] = nn_rank_key(v + 0.f, c);
+      }
+    }
+  }
+  __syncthreads();
+  if (mine) {
+    const int item = i0 + warp;
+    const int total = S.cnt[warp], ncoll = min(total, kCollect);
+    if (total > kCollect || ncoll < np) {
+      if (lane == 0) {
+        a.prop_gap[item] = -1.f;   // threshold not usable: full search
+        S.gap[warp] = -1.f;
+        S.state[warp] = 0;
+      }
+    } else if (ncoll <= kSortSmall) {
+      const float gap = nn_sort_small_warp(a, item, S.keys[warp], ncoll, np, lane);
+      if (lane == 0) {
+        S.gap[warp] = gap;
+        S.state[warp] = 0;
+      }
+    } else if (lane == 0) {
+      S.state[warp] = 2;
+    }
+  } else if (warp < kNnTcG && lane == 0) {
+    S.gap[warp] = -1.f;
+    S.state[warp] = 0;
+  }
+  __syncthreads();
+  // larger survivor sets: bitonic sort by the whole CTA, one event at a time
+  for (int h = 0; h < kNnTcG; ++h) {
+    if (S.state[h] != 2) continue;
+    const int ncoll = min(S.cnt[h], kCollect);
+    int L = 64;
+    while (L < ncoll) L <<= 1;
+    uint64_t* keys = S.keys[h];
+    for (int k = ncoll + tid; k < L; k += kNnThreads) keys[k] = kNoKey;
+    __syncthreads();
+    for (int k = 2; k <= L; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < L; i += kNnThreads) {
+          const int l = i ^ j;
+          if (l > i) {
+            const uint64_t x = keys[i], y = keys[l];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              keys[i] = y;
+              keys[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    const int item = i0 + h;
+    for (int r = tid; r < np; r += kNnThreads)
+      a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
+    if (tid == 0) {
+      const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
+      const float gap = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
+      a.prop_gap[item] = gap;
+      S.gap[h] = gap;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void k_tables_mma(const __nv_bfloat16* __restrict__ tables, int64_t P, int nblk,
@@ -635,8 +929,8 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
     S.type[tid] = ok ? type : -1;
     S.ok[tid] = ok;
   }
+  for (int i = tid; i < kNnTcG * kBinsPad; i += kNnThreads) (&S.hist[0][0])[i] = 0;
   // B operand: the BF16 query of event h in row h (rows kNnTcG..15 zero)
-  for (int i = tid; i < kNnTcG * kBins; i += kNnThreads) (&S.hist[0][0])[i] = 0;
   for (int i = tid; i < 16 * 64; i += kNnThreads) {
     const int h = i / 64, k = i % 64, item = i0 + h;
     const float v = (h < kNnTcG && item < a.n_items) ? a.emb[(int64_t)item * 64 + k] : 0.f;
@@ -738,7 +1032,7 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
             const float sc = __uint_as_float(v[h]);
             cache[h * P + c] = sc;
             const int b = nn_bin0(sc);
-            if (b >= 0) atomicAdd(&S.hist[h][b], 1);
+            if (b >= 0) atomicAdd(&S.hist[h][hpad(b)], 1);
           }
       }
     }
@@ -756,12 +1050,15 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, ncols);
-  if (failed || warp >= kNnTcG || !S.ok[warp]) {
-    if (failed && warp < kNnTcG && lane == 0 && i0 + warp < a.n_items)
+  if (failed) {
+    if (warp < kNnTcG && lane == 0 && i0 + warp < a.n_items)
       a.prop_gap[i0 + warp] = -1.f;   // no proposals: full search
     return;
   }
-  nn_select_warp(a, i0 + warp, cache + warp * P, P, S.hist[warp], S.keys[warp], lane, true);
+  nn_select_cta_tc(a, S, cache, P, i0, tid, warp, lane);
+  if (a.fuse_rerank && warp < kNnTcG && S.ok[warp])
+    nn_rerank_warp(a, i0 + warp, S.gap[warp], reinterpret_cast<float*>(S.hist[warp]),
+                   S.keys[warp], lane);
 }
 
 // Event records from explicit block counts (the query entry point): known
@@ -973,7 +1270,19 @@ int64_t tables_mma_elems(int64_t P) {
 
 static int g_nn_path = 0;   // ccw_set_nn_path
 
-cudaError_t launch_nnsel(const WaveArgs& a, bool pdl, cudaStream_t st) {
+// Does launch_nnsel also re-rank (simulation calls whose weights fit the
+// warp's scratch)? Then no k_rerank launch follows.
+bool nnsel_fuses_rerank_shape(int64_t P, int nch, int rows, int Tj, int n_prop) {
+  return g_nn_path != 2 && P <= kScoreCache && nch * rows * Tj <= kBins && n_prop <= 64;
+}
+bool nnsel_fuses_rerank(const WaveArgs& a) {
+  return a.call != nullptr && a.part != nullptr &&
+         nnsel_fuses_rerank_shape(a.ti.P, a.ti.nch, a.ti.rows, a.ti.Tj, a.n_prop);
+}
+
+cudaError_t launch_nnsel(const WaveArgs& a0, bool pdl, cudaStream_t st) {
+  WaveArgs a = a0;
+  a.fuse_rerank = nnsel_fuses_rerank(a0) ? 1 : 0;
   if (g_nn_path == 0 && a.tables_mma && a.ti.P <= kNnTcMaxP) {
     // one CTA per SM when the scores take more than half of the tensor memory
     int smem = nn_tc_smem(a.ti.P);
