@@ -876,7 +876,8 @@ def main():
             w = configs.workload(args.workload)
             ti_t = torch.from_numpy(w["ti"]).cuda()[None]
             line["plain"] = {k: plain[k] for k in ("value", "ms_per_step", "cand_evals_per_s",
-                                                   "e2e", "roofline", "gpu_launches", "config")
+                                                   "e2e", "roofline", "gpu_launches", "config",
+                                                   "kernels")
                              if k in plain}
             line["learned_vs_plain"] = line["value"] / plain["value"]
             line["accuracy"] = compare_ensembles(

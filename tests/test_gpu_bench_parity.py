@@ -10,6 +10,8 @@ benchmark times (precision and CCF tiling from workloads.configs.BENCH_TILE).
   start, middle and end of the batch equal the oracle's simulation.
 * 3D mixed-size batch: sampled patches of the first realization of each grid
   size re-searched by the oracle as above.
+* Table 2 geometry (20 x 512^2 with hard data, top-5) at each level J:
+  sampled patches of the first and last realization, as above.
 """
 import numpy as np
 import pytest
@@ -102,6 +104,25 @@ def test_batched_full_size_realizations(ccw, name):
         ref, rlog = o.simulate(w["grid"], w["T"], w["O"], K=w["K"], seed=w["seed"], r=r)
         assert np.array_equal(log[r].cpu().numpy(), rlog), f"patch log of realization {r}"
         assert np.array_equal(out[r].cpu().numpy(), ref), f"realization {r}"
+
+
+@pytest.mark.parametrize("name", ["t2_j1_h1000", "t2_j2_h2000", "t2_j3_h1000"])
+def test_table2_batch_sampled(ccw, name):
+    """The Table 2 geometry (20 x 512^2, T 32, OR 8, top-5, 1000 or 2000 hard
+    data) in the benchmarked tiling of its level; sampled patches of the
+    first and last realization re-searched by the oracle, both replayed."""
+    w = configs.workload(name)
+    prec, tile = configs.bench_tile(name)
+    cells, vals = w["hd"]
+    g = ccw.TI(dev(w["ti"]), w["F"], w["J"], w["T"], w["O"])
+    out, log = ccw.simulate(g, w["grid"], n_real=w["n_real"], topk=w["K"], seed=w["seed"],
+                            hd_cells=dev(cells), hd_vals=dev(vals), want_log=True,
+                            precision=prec, ccf_tile=tile)
+    o = O.OracleTI(w["ti"], w["F"], w["J"])
+    for r in (0, w["n_real"] - 1):
+        replay_check(o, w["ti"].shape, w["grid"], w["T"], w["O"], w["K"], w["seed"], r,
+                     out[r].cpu().numpy(), log[r].cpu().numpy(), cells, vals, n_sample=8,
+                     rng_seed=r)
 
 
 def test_3d_mixed_batch_sampled(ccw):

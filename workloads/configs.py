@@ -73,13 +73,17 @@ BENCH_TILE = {
     "c4b": (1, 0xa040040),
     "c5": (2, 0x120020),
 }
+# Table 2 geometry (20 x 512^2, T 32, K 5, hard data): the tuner's choice at
+# each level J (16 items per N-tile; J = 1: lane epilogue, 4 M-tiles per CTA;
+# two realization lanes), also for the grid-size sweep at that level
+T2_TILE = {1: (2, 0x1140010), 2: (2, 0x310010), 3: (2, 0x110010)}
 for _j in (1, 2, 3):
     for _h in (1000, 2000):
-        BENCH_TILE[f"t2_j{_j}_h{_h}"] = (2, 0)
+        BENCH_TILE[f"t2_j{_j}_h{_h}"] = T2_TILE[_j]
 SWEEP_GRIDS = (128, 256, 512, 768, 1024)
 for _j in (1, 2, 3):
     for _g in SWEEP_GRIDS:
-        BENCH_TILE[f"sw_j{_j}_g{_g}"] = (2, 0)
+        BENCH_TILE[f"sw_j{_j}_g{_g}"] = T2_TILE[_j]
 
 
 def bench_tile(name: str):
