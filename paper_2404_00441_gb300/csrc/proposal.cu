@@ -319,36 +319,36 @@ __device__ __forceinline__ float nn_key_score(uint64_t k) {
 // descending, index ascending) are sorted (bitonic, the smallest power of two
 // >= their count and >= 64) and the first n_prop written with the gap.
 // hist: kBins ints, keys: kCollect words of this warp's shared memory.
-// The n_prop best of ncoll <= kSortSmall survivor keys (keys[0 .. ncoll)):
-// bitonic sort in registers (element e = 4 lane + r), proposals written, gap
-// written by lane 0 and returned to every lane. One warp.
-__device__ __forceinline__ float nn_sort_small_warp(const WaveArgs& a, int item,
-                                                    const uint64_t* keys, int ncoll, int np,
-                                                    int lane) {
-  // bitonic sort of kSortSmall keys in registers: element e = 4 lane + r
-  uint64_t x[4];
+// The n_prop best of ncoll <= 32 NPL survivor keys (keys[0 .. ncoll)):
+// bitonic sort in registers (element e = NPL lane + r), proposals written,
+// gap written by lane 0 and returned to every lane. One warp.
+template <int NPL>
+__device__ __noinline__ float nn_sort_regs_warp(const WaveArgs& a, int item,
+                                                   const uint64_t* keys, int ncoll, int np,
+                                                   int lane) {
+  uint64_t x[NPL];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int e = 4 * lane + r;
+  for (int r = 0; r < NPL; ++r) {
+    const int e = NPL * lane + r;
     x[r] = e < ncoll ? keys[e] : kNoKey;
   }
 #pragma unroll
-  for (int k = 2; k <= kSortSmall; k <<= 1)
+  for (int k = 2; k <= 32 * NPL; k <<= 1)
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 4) {
+      if (j >= NPL) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int e = 4 * lane + r;
-          const uint64_t y = __shfl_xor_sync(0xffffffffu, x[r], j >> 2);
+        for (int r = 0; r < NPL; ++r) {
+          const int e = NPL * lane + r;
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, x[r], j / NPL);
           const bool up = (e & k) == 0, lower = (e & j) == 0;
           x[r] = (lower == up) ? (x[r] < y ? x[r] : y) : (x[r] > y ? x[r] : y);
         }
       } else {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < NPL; ++r)
           if ((r & j) == 0) {
-            const int e = 4 * lane + r;
+            const int e = NPL * lane + r;
             const bool up = (e & k) == 0;
             const uint64_t u = x[r], v = x[r ^ j];
             if ((u > v) == up) {
@@ -358,15 +358,16 @@ __device__ __forceinline__ float nn_sort_small_warp(const WaveArgs& a, int item,
           }
       }
     }
+  uint64_t xn = x[0];
+  const int rn = (np - 1) % NPL;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int e = 4 * lane + r;
+  for (int r = 0; r < NPL; ++r) {
+    const int e = NPL * lane + r;
     if (e < np) a.prop[(int64_t)item * a.n_prop + e] = (int)(x[r] & 0xFFFFFFFFu);
+    xn = r == rn ? x[r] : xn;
   }
   const uint64_t k1 = __shfl_sync(0xffffffffu, x[0], 0);
-  const int rn = (np - 1) & 3;
-  const uint64_t xn = rn == 0 ? x[0] : rn == 1 ? x[1] : rn == 2 ? x[2] : x[3];
-  const uint64_t kn = __shfl_sync(0xffffffffu, xn, (np - 1) >> 2);
+  const uint64_t kn = __shfl_sync(0xffffffffu, xn, (np - 1) / NPL);
   const float s1 = nn_key_score(k1), sn = nn_key_score(kn);
   const float gap = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
   if (lane == 0) a.prop_gap[item] = gap;
@@ -469,33 +470,10 @@ __device__ __forceinline__ float nn_select_warp(const WaveArgs& a, int item, con
     return -1.f;
   }
   __syncwarp();
-  if (ncoll <= kSortSmall) return nn_sort_small_warp(a, item, keys, ncoll, np, lane);
-  int L = 64;
-  while (L < ncoll) L <<= 1;
-  for (int k = ncoll + lane; k < L; k += 32) keys[k] = kNoKey;
-  __syncwarp();
-  // bitonic sort of L keys, ascending
-  for (int k = 2; k <= L; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < L; i += 32) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint64_t x = keys[i], y = keys[l];
-          const bool up = (i & k) == 0;
-          if ((x > y) == up) {
-            keys[i] = y;
-            keys[l] = x;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  for (int r = lane; r < np; r += 32)
-    a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
-  const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
-  const float gap = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
-  if (lane == 0) a.prop_gap[item] = gap;
-  return gap;
+  // sorted in registers by the warp
+  if (ncoll <= kSortSmall) return nn_sort_regs_warp<4>(a, item, keys, ncoll, np, lane);
+  if (ncoll <= 2 * kSortSmall) return nn_sort_regs_warp<8>(a, item, keys, ncoll, np, lane);
+  return nn_sort_regs_warp<16>(a, item, keys, ncoll, np, lane);
 }
 
 // The exact re-rank of k_rerank done by the selecting warp right after its
@@ -684,7 +662,7 @@ struct NnTcSmem {
   int type[kNnTcG], ok[kNnTcG];
   // per event: threshold, level-1 range, count above it, survivors, state
   float thr[kNnTcG], lo1[kNnTcG], hi1[kNnTcG];
-  int above0[kNnTcG], need1[kNnTcG], cnt[kNnTcG], state[kNnTcG];
+  int above0[kNnTcG], need1[kNnTcG], cnt[kNnTcG];
   float gap[kNnTcG];
   int hist[kNnTcG][kBinsPad];
   uint64_t keys[kNnTcG][kCollect];
@@ -755,9 +733,8 @@ __device__ __forceinline__ void nn_threshold_pad(const int* hist, int np, int ab
 // event's threshold (level 0 from the histogram the epilogue built, level 1
 // over the threshold bin when more than kSortSmall would survive), all
 // threads then build the level-1 histograms and collect every event's
-// survivors; a warp sorts up to kSortSmall survivors in registers, larger
-// sets are sorted by the whole CTA in shared memory. Sets S.gap[h] (-1: the
-// event falls back to the full search).
+// survivors; each warp sorts its event's survivors (up to kCollect) in
+// registers. Sets S.gap[h] (-1: the event falls back to the full search).
 __device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
                                                  const float* cache, int P, int i0, int tid,
                                                  int warp, int lane) {
@@ -830,57 +807,20 @@ __device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
       if (lane == 0) {
         a.prop_gap[item] = -1.f;   // threshold not usable: full search
         S.gap[warp] = -1.f;
-        S.state[warp] = 0;
       }
-    } else if (ncoll <= kSortSmall) {
-      const float gap = nn_sort_small_warp(a, item, S.keys[warp], ncoll, np, lane);
-      if (lane == 0) {
-        S.gap[warp] = gap;
-        S.state[warp] = 0;
-      }
-    } else if (lane == 0) {
-      S.state[warp] = 2;
+    } else {
+      // every survivor set sorted by its own warp in registers
+      const float gap =
+          ncoll <= kSortSmall ? nn_sort_regs_warp<4>(a, item, S.keys[warp], ncoll, np, lane)
+          : ncoll <= 2 * kSortSmall
+              ? nn_sort_regs_warp<8>(a, item, S.keys[warp], ncoll, np, lane)
+              : nn_sort_regs_warp<16>(a, item, S.keys[warp], ncoll, np, lane);
+      if (lane == 0) S.gap[warp] = gap;
     }
   } else if (warp < kNnTcG && lane == 0) {
     S.gap[warp] = -1.f;
-    S.state[warp] = 0;
   }
   __syncthreads();
-  // larger survivor sets: bitonic sort by the whole CTA, one event at a time
-  for (int h = 0; h < kNnTcG; ++h) {
-    if (S.state[h] != 2) continue;
-    const int ncoll = min(S.cnt[h], kCollect);
-    int L = 64;
-    while (L < ncoll) L <<= 1;
-    uint64_t* keys = S.keys[h];
-    for (int k = ncoll + tid; k < L; k += kNnThreads) keys[k] = kNoKey;
-    __syncthreads();
-    for (int k = 2; k <= L; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = tid; i < L; i += kNnThreads) {
-          const int l = i ^ j;
-          if (l > i) {
-            const uint64_t x = keys[i], y = keys[l];
-            const bool up = (i & k) == 0;
-            if ((x > y) == up) {
-              keys[i] = y;
-              keys[l] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    const int item = i0 + h;
-    for (int r = tid; r < np; r += kNnThreads)
-      a.prop[(int64_t)item * a.n_prop + r] = (int)(keys[r] & 0xFFFFFFFFu);
-    if (tid == 0) {
-      const float s1 = nn_key_score(keys[0]), sn = nn_key_score(keys[np - 1]);
-      const float gap = (s1 - sn) / fmaxf(fabsf(s1), 1e-6f);
-      a.prop_gap[item] = gap;
-      S.gap[h] = gap;
-    }
-    __syncthreads();
-  }
 }
 
 __global__ void k_tables_mma(const __nv_bfloat16* __restrict__ tables, int64_t P, int nblk,

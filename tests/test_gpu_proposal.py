@@ -242,12 +242,12 @@ def test_infinite_gap_threshold_is_the_plain_method(ccw, ti, precision):
 
 
 def exact_scores(ccw, ti, counts):
+    """Eq. CCW scores of every TI candidate for the data events of `counts`,
+    from the CPU oracle (not the library)."""
+    from oracle import oracle as O
+    o = O.OracleTI(configs.ribbon_ti_250(), F, J)
     de = de_from_counts(counts)
-    out = []
-    for i0 in range(0, len(de), 256):
-        sc, _ = ccw.ccf_map(ti, torch.from_numpy(de[i0:i0 + 256]).cuda())
-        out.append(sc.cpu().numpy())
-    return np.concatenate(out)
+    return np.stack([o.search(T, de[i], maps=True)["scores"] for i in range(len(de))])
 
 
 @pytest.mark.parametrize("precision", [0, 2])
