@@ -162,7 +162,11 @@ __device__ void quilt_paste(const PasteGeom& g, const uint8_t* pat, int T, int O
   }
 }
 
-template <int D, int MODE>
+// Paste variants, each its own instantiation so that the common one carries
+// no code of the others (the kernel is bound by instruction fetch).
+enum : int { kPasteBlocks = 0, kPasteCut = 1, kPasteCrop = 2 };
+
+template <int D, int MODE, int PV>
 __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ WaveArgs a,
                                                      int staged_bytes) {
   __shared__ uint64_t red[2][kWarps + 1];
@@ -248,10 +252,10 @@ __global__ void __launch_bounds__(kThreads) k_finish(const __grid_constant__ Wav
     e[tid] = val;
   }
   const PasteGeom g = sim_paste_geom<D>(a, it);
-  if (D == 2 && a.allshift) {
+  if (D == 2 && PV == kPasteCrop) {
     // an all-shift candidate: the TI crop at its fine origin
     paste_crop2(g, t.ti, t.tp[0], a.fd0, pk, t.T, nth, tid);
-  } else if (D == 2 && a.cut && a.Oj > 0) {
+  } else if (D == 2 && PV == kPasteCut) {
     // the pattern into shared memory, then the boundary-cut paste (the
     // launch guarantees staged_bytes > 0 and the cut buffers behind it)
     unsigned char* pat = reinterpret_cast<unsigned char*>(staged) + ((staged_bytes + 15) & ~15);
@@ -302,7 +306,9 @@ static cudaError_t launch_t(const WaveArgs& a, bool pdl, cudaStream_t st) {
   const bool cut = D == 2 && MODE == kModeSim && a.cut && a.Oj > 0;
   const int smem =
       cut ? ((staged + 15) & ~15) + cut_smem_bytes(a.ti.T, a.Oj * a.ti.s) : staged;
-  auto fn = k_finish<D, MODE>;
+  auto fn = cut ? k_finish<D, MODE, kPasteCut>
+                : (D == 2 && MODE == kModeSim && a.allshift) ? k_finish<D, MODE, kPasteCrop>
+                                                             : k_finish<D, MODE, kPasteBlocks>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
