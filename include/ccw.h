@@ -369,7 +369,7 @@ typedef struct ccw_net ccw_net;
 
 /* ccw_set_nn_path -- which kernel scores and selects the nearest TI windows
  * of the learned proposal (the proposals are the same up to FP32 rounding of
- * the scores): 0 (default) the tcgen05 kernel for tables of at most 3584
+ * the scores): 0 (default) the tcgen05 kernel for tables of at most 3072
  * windows, else the FP32-lane kernel with several data events per CTA (at
  * most 6144 windows), else one CTA per data event; 1 never the tensor cores;
  * 2 always one CTA per data event. Process-wide; CCW_EINVAL for other
