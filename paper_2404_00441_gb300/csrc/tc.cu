@@ -261,9 +261,33 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
                              __uint_as_float(v[6]), __uint_as_float(v[7]));
       }
       __syncthreads();
-      if (mt4.w)
+      if (mt4.w && MODE != kModeMap && K == 1 && mt4.z == 0) {
+        // K = 1 without hard data: the segment's best score, the first
+        // (lowest index) of equal ones since candidate indices rise with
+        // the rows; one key for the segment
+        const int2* cj = cand + j * 128;
+        float best = -3.0e38f;
+        int bi = -1;
+#pragma unroll 4
+        for (int r = seg * seg_len; r < (seg + 1) * seg_len; ++r) {
+          const float v = S[r * sp + n];
+          const int ci = cj[r].x;
+          if (ci >= 0 && v > best) {
+            best = v;
+            bi = ci;
+          }
+        }
+        if (bi >= 0) {
+          const uint64_t key = make_key(0, __float2int_rn(best) + mt4.y, bi);
+          if (key < worst) {
+            lst[0] = key;
+            worst = key;
+          }
+        }
+      } else if (mt4.w) {
         scan_segment<MODE, kTcRegK>(a, S, sp, n, cand + j * 128, seg * seg_len, seg_len, mt4,
                                     hdl, item, K, lst, worst);
+      }
       __syncthreads();   // S is rewritten by the next M-tile
     }
     // segment lists -> shared memory (over S), then one warp per item merges
