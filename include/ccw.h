@@ -48,7 +48,7 @@ extern "C" {
 #define CCW_ENOMEM (-2)      /* device allocation failed */
 #define CCW_ECUDA (-3)       /* a CUDA call failed */
 #define CCW_ETIMEOUT (-4)    /* a bounded device wait gave up */
-#define CCW_EUNSUPPORTED (-5)/* valid request this build does not handle */
+#define CCW_EUNSUPPORTED (-5)/* valid request the library does not handle */
 
 #define CCW_UNKNOWN 255
 #define CCW_PRECISION_INEXACT 4 /* ccw_params.precision flag: FP16/BF16 past the
