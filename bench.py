@@ -16,7 +16,8 @@ Inputs are synthetic and seeded (workloads/configs.py).
 Prints one JSON line. `value` is device-timed (CUDA events on the launching
 stream, inputs resident, L2 flushed by a 256 MiB write between steps);
 `e2e` is the same metric through the public API with host buffers (hard data
-copied in from pinned memory and the realization copied back inside the
+copied in from pinned memory, and the realizations copied back to pinned host
+memory by the library, band by band as the wavefronts finish them, inside the
 timed region). `--impl reference` times the CPU oracle instead, on a bounded
 sample of patches per step.
 
@@ -645,8 +646,9 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def run(hd_dev=None):
+    def run(hd_dev=None, host=None):
         hd_dev = hd_dev or [(gr["hd_cells"], gr["hd_vals"]) for gr in groups]
+        host = host or [None] * len(groups)
         if len(groups) == 1:
             gr = groups[0]
             ccw.simulate(g, gr["grid"], n_real=gr["n_real"], topk=w["K"], seed=w["seed"],
@@ -654,11 +656,12 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
                          real_base=gr["real_base"], out=outs[0], precision=precision,
                          learned=1 if learned else 0, ccf_tile=tile,
                          vt_ext=args.vt_ext, boundary_cut=int(args.boundary_cut),
-                         all_shift=int(getattr(args, "all_shift", False)))
+                         all_shift=int(getattr(args, "all_shift", False)), out_host=host[0])
             return outs
         res = ccw.simulate_groups(
             g, [dict(grid=gr["grid"], n_real=gr["n_real"], real_base=gr["real_base"],
-                     hd_cells=h[0], hd_vals=h[1]) for gr, h in zip(groups, hd_dev)],
+                     hd_cells=h[0], hd_vals=h[1], out=o, out_host=ho)
+                for gr, h, o, ho in zip(groups, hd_dev, outs, host)],
             topk=w["K"], seed=w["seed"], precision=precision,
             learned=1 if learned else 0, ccf_tile=tile, vt_ext=args.vt_ext,
             boundary_cut=int(args.boundary_cut), all_shift=int(getattr(args, "all_shift", False)))
@@ -715,7 +718,8 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
     clk = clocks.stop()
 
     # end to end through the public API with host buffers: the hard data come
-    # in from pinned host memory and the realizations go back to it
+    # in from pinned host memory and the library copies the realizations back
+    # to pinned host memory (band by band while the later wavefronts run)
     e2e_ms = None
     h2d = d2h = 0
     if not args.no_e2e:
@@ -733,6 +737,7 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
             dev_hd.append((torch.empty_like(pc, device="cuda"), torch.empty_like(pv, device="cuda")))
             h2d += pc.numel() * 4 + pv.numel()
         d2h = sum(o.numel() for o in outs)
+        run(dev_hd, host_outs)   # builds the read-back graph for these buffers (not timed)
         barrier()
         e2e_ms = 0.0
         for _ in range(args.steps):
@@ -744,9 +749,7 @@ def run_ours(args, rank, world, local_rank, learned=None, cpu=True, keep=False):
                 if p is not None:
                     dv[0].copy_(p[0], non_blocking=True)
                     dv[1].copy_(p[1], non_blocking=True)
-            res = run(dev_hd)
-            for ho, o in zip(host_outs, res):
-                ho.copy_(o, non_blocking=True)
+            run(dev_hd, host_outs)
             e1.record(stream)
             e1.synchronize()
             e2e_ms += e0.elapsed_time(e1)

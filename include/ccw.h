@@ -246,6 +246,8 @@ typedef struct {
                                    the facies counts of every level-J block of each
                                    patch's data event, as searched (needs 2^(d J) <=
                                    255); the learned proposal trains on them */
+  uint8_t* out_host;            /* uint8 [n_real][grid] host copy of out_dev, or
+                                   NULL; see ccw_simulate_groups */
 } ccw_group;
 
 /*
@@ -256,6 +258,17 @@ typedef struct {
  * per step, so the groups share the kernel launches; each realization is
  * exactly what ccw_simulate gives for it. Synchronizes `stream` once at the
  * end. Errors as ccw_simulate.
+ * Host read-back: a group with out_host also gets its realizations copied
+ * into that host buffer (caller-owned, not retained) before the call
+ * returns. When every out_host of the call is page-locked (cudaHostAlloc or
+ * cudaHostRegister over the whole buffer) and path_random is 0, the copy
+ * streams: each band of rows along the slowest axis is copied as soon as
+ * the last patch row over it is pasted, while later wavefronts run, so
+ * that only the last band's copy follows the simulation. The graph that
+ * does this holds the out_dev and out_host pointers it was built with and
+ * is built again when they change, so reuse the same buffers across calls.
+ * Otherwise (pageable memory, mirrored paths) the copy runs after the
+ * simulation.
  */
 int ccw_simulate_groups(const ccw_ti* ti, const ccw_params* params, const ccw_group* groups,
                         int32_t n_groups, uint64_t seed, void* stream);

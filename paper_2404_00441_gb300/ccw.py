@@ -39,7 +39,7 @@ class _Group(C.Structure):
     _fields_ = [("grid", C.c_int32 * 3), ("n_real", C.c_int32), ("real_base", C.c_int32),
                 ("hd_cells_dev", C.c_void_p), ("hd_vals_dev", C.c_void_p), ("n_hd", C.c_int32),
                 ("out_dev", C.c_void_p), ("patch_log_dev", C.c_void_p),
-                ("event_counts_dev", C.c_void_p)]
+                ("event_counts_dev", C.c_void_p), ("out_host", C.c_void_p)]
 
 
 class _Desc(C.Structure):
@@ -113,6 +113,16 @@ def _ptr(t):
         return None
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t, shape):
+    """A host output buffer: a contiguous CPU uint8 tensor of `shape` (pinned
+    for the streamed read-back)."""
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous() or t.dtype != torch.uint8 or tuple(t.shape) != shape:
+        raise ValueError(f"out_host must be a contiguous CPU uint8 tensor of shape {shape}")
     return C.c_void_p(t.data_ptr())
 
 
@@ -248,8 +258,12 @@ class TI:
 
 def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None, real_base=0,
              path_random=0, score_mode=0, precision=0, want_log=False, out=None, log=None,
-             learned=0, ccf_tile=0, vt_ext=0, boundary_cut=0, all_shift=0, stream=None):
-    """``ccw_simulate``: returns (realizations uint8 [n_real, *grid[::-1]], log or None)."""
+             learned=0, ccf_tile=0, vt_ext=0, boundary_cut=0, all_shift=0, out_host=None,
+             stream=None):
+    """``ccw_simulate``: returns (realizations uint8 [n_real, *grid[::-1]], log or None).
+    With ``out_host`` (a CPU uint8 tensor of that shape, pinned for the
+    streamed copy) the realizations are also copied into it, through
+    ``ccw_simulate_groups``' host read-back."""
     lib = load()
     p = _Params()
     p.ndim = ti.ndim
@@ -275,6 +289,21 @@ def simulate(ti: TI, grid, n_real=1, topk=1, seed=0, hd_cells=None, hd_vals=None
     if want_log and log is None:
         log = torch.empty((n_real, n_patches, 4 + topk), dtype=torch.int32, device="cuda")
     n_hd = 0 if hd_vals is None else int(hd_vals.numel())
+    if out_host is not None:
+        g = (_Group * 1)()
+        g[0].grid = _i3(grid)
+        g[0].n_real = n_real
+        g[0].real_base = real_base
+        g[0].hd_cells_dev = _ptr(hd_cells) if n_hd else None
+        g[0].hd_vals_dev = _ptr(hd_vals) if n_hd else None
+        g[0].n_hd = n_hd
+        g[0].out_dev = _ptr(out)
+        g[0].patch_log_dev = _ptr(log) if want_log else None
+        g[0].event_counts_dev = None
+        g[0].out_host = _host_ptr(out_host, shape)
+        _check(lib.ccw_simulate_groups(ti.handle, C.byref(p), g, 1, seed & (2 ** 64 - 1),
+                                       _stream(stream)))
+        return out, (log if want_log else None)
     _check(lib.ccw_simulate(ti.handle, C.byref(p), _ptr(hd_cells) if n_hd else None,
                             _ptr(hd_vals) if n_hd else None, n_hd, seed & (2 ** 64 - 1),
                             _ptr(out), _ptr(log) if want_log else None, _stream(stream)))
@@ -286,7 +315,9 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
                     boundary_cut=0, all_shift=0, stream=None):
     """``ccw_simulate_groups``: several grid sizes in one batch. ``groups`` is
     a list of dicts with keys grid, n_real, real_base and optionally hd_cells,
-    hd_vals (CUDA tensors). Returns a list of (realizations, log or None)."""
+    hd_vals (CUDA tensors), out (the CUDA output) and out_host (a CPU copy of
+    it, pinned for the streamed read-back). Returns a list of (realizations,
+    log or None)."""
     lib = load()
     p = _Params()
     p.ndim = ti.ndim
@@ -307,7 +338,12 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
     for i, g in enumerate(groups):
         grid = tuple(g["grid"])
         n_real = int(g["n_real"])
-        out = torch.empty((n_real,) + grid[::-1], dtype=torch.uint8, device="cuda")
+        shape = (n_real,) + grid[::-1]
+        out = g.get("out")
+        if out is None:
+            out = torch.empty(shape, dtype=torch.uint8, device="cuda")
+        elif tuple(out.shape) != shape or out.dtype != torch.uint8:
+            raise ValueError(f"out must be a CUDA uint8 tensor of shape {shape}")
         npch, _ = lattice(grid, ti.templ, ti.overlap)
         n_patches = 1
         for v in npch:
@@ -328,6 +364,7 @@ def simulate_groups(ti: TI, groups, topk=1, seed=0, path_random=0, score_mode=0,
         arr[i].out_dev = _ptr(out)
         arr[i].patch_log_dev = _ptr(log) if want_log else None
         arr[i].event_counts_dev = _ptr(counts) if want_counts else None
+        arr[i].out_host = _host_ptr(g.get("out_host"), shape)
         keep.append((hc, hv))
         results.append((out, log, counts) if want_counts else (out, log))
     _check(lib.ccw_simulate_groups(ti.handle, C.byref(p), arr, len(groups), seed & (2 ** 64 - 1),

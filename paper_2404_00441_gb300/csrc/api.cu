@@ -52,7 +52,7 @@ cudaError_t launch_hd_overlay(const int32_t* cells, const uint8_t* vals, int n, 
                               cudaStream_t st);
 cudaError_t launch_crop_out(const uint8_t* sg, int64_t gp_vol, const int gp[3], uint8_t* out,
                             const int g[3], int d, int n_real, int path_random, uint64_t seed,
-                            int real_base, cudaStream_t st);
+                            int real_base, cudaStream_t st, int row0 = 0, int row1 = -1);
 cudaError_t launch_idwt_paste(int d, int J, const int16_t* pyr, const int nc[3], const int cd[3],
                               int Tj, int64_t P, int B, const int32_t* picks,
                               const int32_t* origins, uint8_t* grid, const int gdim[3],
@@ -209,12 +209,25 @@ struct SimPlan {
   void* cp = nullptr;   // CcfPlan (defined with the kernels' host helpers)
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [profiling]
+  // Streamed read-back (groups with a pinned out_host, unmirrored paths):
+  // a third graph also crops each band of output rows once the patch rows
+  // over it are pasted and copies it to the host while later wavefronts
+  // run, on one copy stream per lane. It bakes in the output pointers it
+  // was captured with and is captured again when they change.
+  cudaGraphExec_t exec_host = nullptr;
+  std::vector<uint8_t*> host_dev, host_host;   // per group, as captured
+  std::vector<cudaStream_t> cst;               // per lane: copy stream
+  std::vector<cudaEvent_t> cev;                // per lane: fork / join mark
+  int64_t host_launches = 0;                   // band crops per call
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;   // around each CCF launch
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_bounds;   // before events, after finish
   std::vector<cudaEvent_t> prof_prop;   // learned: [3] per step: before encoder, before selection, after
   ~SimPlan() {
     for (auto& e : exec)
       if (e) cudaGraphExecDestroy(e);
+    if (exec_host) cudaGraphExecDestroy(exec_host);
+    for (auto s : cst) cudaStreamDestroy(s);
+    for (auto e : cev) cudaEventDestroy(e);
     for (auto* v : {&prof_events, &prof_bounds})
       for (auto& pr : *v) {
         cudaEventDestroy(pr.first);
@@ -1464,11 +1477,71 @@ int build_plan(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int n_gr
   return CCW_OK;
 }
 
-// Launch phases A, B and C of every wave on `st` (while `st` is being
-// captured into the plan's graph).
+// Output rows of group g that become final with wavefront w, as a range
+// [b0, b1) of indices along the slowest axis (y in 2D, z in 3D); b0 == b1
+// when none. Patch row i of that axis (lattice index i_y in 2D, i_z in 3D)
+// ends with the wave of its last patch, (np_x - 1) + 2 i in 2D and
+// (np_x - 1) + 2 (np_y - 1) + 4 i in 3D; the next patch row starts at
+// (i + 1)(T - OR), so every row before it is final from then on.
+void band_at_wave(const GroupPlan& g, int d, int S, int w, int& b0, int& b1) {
+  b0 = b1 = 0;
+  const int slow = d - 1, step = d == 3 ? 4 : 2;
+  const int base = (g.np[0] - 1) + (d == 3 ? 2 * (g.np[1] - 1) : 0);
+  if (w < base || (w - base) % step) return;
+  const int i = (w - base) / step;
+  if (i >= g.np[slow]) return;
+  const int G = g.g[slow];
+  b0 = std::min(G, i * S);
+  b1 = i == g.np[slow] - 1 ? G : std::min(G, (i + 1) * S);
+}
+
+// Streamed read-back after wavefront w of lane `lane` (captured on `st`):
+// every band that wave completes is cropped into out_dev and copied to
+// out_host on the lane's copy stream, for the lane's realizations.
+int launch_band_copies(ccw_ti* t, SimPlan* pl, const ccw_group* hosts, int lane, int w,
+                       cudaStream_t st, std::vector<char>& used) {
+  const int d = t->ndim, S = t->T - t->O, L = (int)pl->lanes.size();
+  bool forked = false;
+  for (int i = 0; i < pl->n_groups; ++i) {
+    const GroupPlan& g = pl->groups[i];
+    if (!hosts[i].out_host) continue;
+    int b0, b1;
+    band_at_wave(g, d, S, w, b0, b1);
+    if (b0 >= b1) continue;
+    // the lane's realizations: slots r with r L / n_real == lane
+    const int r0 = (int)(((int64_t)lane * g.n_real + L - 1) / L);
+    const int r1 = (int)(((int64_t)(lane + 1) * g.n_real + L - 1) / L);
+    if (r0 >= r1) continue;
+    cudaError_t e;
+    if (!forked) {
+      if ((e = cudaEventRecord(pl->cev[lane], st)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(pl->cst[lane], pl->cev[lane], 0)) != cudaSuccess)
+        return cuda_fail(e, "read-back fork");
+      forked = true;
+      used[lane] = 1;
+    }
+    const int rs = d == 3 ? g.g[1] : 1;   // output rows per slow-axis index
+    const int64_t vol = g.g_vol;
+    uint8_t* dev = hosts[i].out_dev + r0 * vol;
+    if ((e = launch_crop_out((const uint8_t*)g.sg + r0 * g.gp_vol, g.gp_vol, g.gp, dev, g.g, d,
+                             r1 - r0, 0, 0, hosts[i].real_base + r0, pl->cst[lane], b0 * rs,
+                             b1 * rs)) != cudaSuccess)
+      return cuda_fail(e, "crop kernel");
+    ++pl->host_launches;
+    const size_t off = (size_t)b0 * rs * g.g[0];
+    if ((e = cudaMemcpy2DAsync(hosts[i].out_host + r0 * vol + off, (size_t)vol, dev + off,
+                               (size_t)vol, (size_t)(b1 - b0) * rs * g.g[0], (size_t)(r1 - r0),
+                               cudaMemcpyDeviceToHost, pl->cst[lane])) != cudaSuccess)
+      return cuda_fail(e, "read-back copy");
+  }
+  return CCW_OK;
+}
+
 // Launch phases A, B and C of every wave of lane `lane` on `st` (while `st`
 // is being captured into the plan's graph); `pe` counts the profiled steps.
-int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, size_t& pe) {
+// With `hosts`, also the streamed read-back of the bands each wave completes.
+int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, size_t& pe,
+                 const ccw_group* hosts, std::vector<char>& used) {
   const SimPlan::Lane& ln = pl->lanes[lane];
   WaveArgs a;
   fill_ti(t, pl->score_mode, a);
@@ -1558,12 +1631,31 @@ int launch_waves(ccw_ti* t, SimPlan* pl, bool prof, int lane, cudaStream_t st, s
       if (e != cudaSuccess) return cuda_fail(e, "finish kernel launch");
       if (prof) cudaEventRecordWithFlags(pl->prof_bounds[pe++].second, st, cudaEventRecordExternal);
     }
+    if (hosts)
+      if (int rc = launch_band_copies(t, pl, hosts, lane, w, st, used)) return rc;
   }
   return CCW_OK;
 }
 
-int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
+int capture_waves(ccw_ti* t, SimPlan* pl, bool prof, const ccw_group* hosts = nullptr) {
   cudaGraph_t graph = nullptr;
+  const size_t nl = pl->lanes.size();
+  std::vector<char> used(nl, 0);   // lanes whose copy stream joined the capture
+  if (hosts) {
+    pl->host_launches = 0;
+    while (pl->cst.size() < nl) {
+      cudaStream_t cs = nullptr;
+      cudaEvent_t ce = nullptr;
+      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ce, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        return cuda_fail(e, "read-back streams");
+      }
+      pl->cst.push_back(cs);
+      pl->cev.push_back(ce);
+    }
+  }
   cudaError_t e = cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "begin capture");
   // lanes >= 1 fork from the capture stream and join it at the end
@@ -1579,11 +1671,16 @@ int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
         rc = cuda_fail(e, "capture fork");
   }
   for (size_t l = 0; l < pl->lanes.size() && !rc; ++l)
-    rc = launch_waves(t, pl, prof, (int)l, l == 0 ? pl->cap : pl->lanes[l].st, pe);
+    rc = launch_waves(t, pl, prof, (int)l, l == 0 ? pl->cap : pl->lanes[l].st, pe, hosts, used);
   for (size_t l = 1; l < pl->lanes.size() && !rc; ++l)
     if ((e = cudaEventRecord(pl->lanes[l].done, pl->lanes[l].st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(pl->cap, pl->lanes[l].done, 0)) != cudaSuccess)
       rc = cuda_fail(e, "capture join");
+  for (size_t l = 0; l < nl; ++l)   // copy streams join even after an error
+    if (used[l] && ((e = cudaEventRecord(pl->cev[l], pl->cst[l])) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(pl->cap, pl->cev[l], 0)) != cudaSuccess) &&
+        !rc)
+      rc = cuda_fail(e, "read-back join");
   e = cudaStreamEndCapture(pl->cap, &graph);
   if (fork) cudaEventDestroy(fork);
   if (rc) {
@@ -1591,7 +1688,7 @@ int capture_waves(ccw_ti* t, SimPlan* pl, bool prof) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(e, "end capture");
-  e = cudaGraphInstantiate(&pl->exec[prof ? 1 : 0], graph, 0);
+  e = cudaGraphInstantiate(hosts ? &pl->exec_host : &pl->exec[prof ? 1 : 0], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
   return CCW_OK;
@@ -1758,8 +1855,41 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
       return cuda_fail(e, "log clear");
   }
   const bool persist = static_cast<const CcfPlan*>(pl->cp)->persist;
+  // host read-back: streamed inside the graph when every host buffer is
+  // pinned and the paths are unmirrored (a band of rows is then the same
+  // rows of every realization), else one copy per group after the crop
+  bool any_host = false, all_pinned = true;
+  for (int i = 0; i < n_groups; ++i) {
+    if (!groups[i].out_host) continue;
+    any_host = true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, groups[i].out_host) != cudaSuccess ||
+        at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      all_pinned = false;
+    }
+  }
+  const bool stream_host = any_host && all_pinned && !prof && !persist && p->path_random == 0;
   if (persist) {
     if (int rc = launch_persist_call(t, pl, prof, st)) return rc;
+  } else if (stream_host) {
+    bool same = pl->exec_host && (int)pl->host_dev.size() == n_groups;
+    for (int i = 0; same && i < n_groups; ++i)
+      same = pl->host_dev[i] == groups[i].out_dev && pl->host_host[i] == groups[i].out_host;
+    if (!same) {
+      if (pl->exec_host) cudaGraphExecDestroy(pl->exec_host);
+      pl->exec_host = nullptr;
+      pl->host_dev.clear();
+      pl->host_host.clear();
+      if (int rc = capture_waves(t, pl, false, groups)) return rc;
+      for (int i = 0; i < n_groups; ++i) {
+        pl->host_dev.push_back(groups[i].out_dev);
+        pl->host_host.push_back(groups[i].out_host);
+      }
+    }
+    if ((e = cudaGraphLaunch(pl->exec_host, st)) != cudaSuccess)
+      return cuda_fail(e, "graph launch");
+    g_launches += pl->launches_per_call + pl->host_launches;
   } else {
     const int gi = prof ? 1 : 0;
     if (!pl->exec[gi])
@@ -1770,11 +1900,16 @@ int simulate_groups(ccw_ti* t, const ccw_params* p, const ccw_group* groups, int
   }
   for (int i = 0; i < n_groups; ++i) {
     const GroupPlan& g = pl->groups[i];
+    if (stream_host && groups[i].out_host) continue;   // cropped and copied in the graph
     if ((e = launch_crop_out((const uint8_t*)g.sg, g.gp_vol, g.gp, groups[i].out_dev, g.g, d,
                              g.n_real, p->path_random, seed, groups[i].real_base, st)) !=
         cudaSuccess)
       return cuda_fail(e, "crop kernel");
     ++g_launches;
+    if (groups[i].out_host &&
+        (e = cudaMemcpyAsync(groups[i].out_host, groups[i].out_dev, (size_t)(g.g_vol * g.n_real),
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "read-back copy");
   }
   int status = 0;
   if ((e = cudaMemcpyAsync(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) !=
@@ -2056,6 +2191,7 @@ extern "C" int ccw_simulate(const ccw_ti* tc, const ccw_params* p, const int32_t
   g.out_dev = out_dev;
   g.patch_log_dev = patch_log_dev;
   g.event_counts_dev = nullptr;
+  g.out_host = nullptr;
   return simulate_groups(const_cast<ccw_ti*>(tc), p, &g, 1, seed, stream);
 }
 

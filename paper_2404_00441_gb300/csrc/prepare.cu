@@ -138,10 +138,12 @@ __global__ void k_hd_overlay(const int32_t* __restrict__ cells, const uint8_t* _
 
 // Crop the padded grids of n_real realizations into the caller's output,
 // undoing each realization's path mirroring (Algorithm 1, line 3): one CTA
-// per output row at a time, 32-bit words when every row start is aligned.
+// per output row at a time (rows row0 .. row1 - 1 of the gy * gz rows of
+// every realization), 32-bit words when every row start is aligned.
 __global__ void k_crop_out(const uint8_t* __restrict__ sg, int64_t gp_vol, int gpx, int gpy,
                            uint8_t* __restrict__ out, int gx, int gy, int gz, int d, int gpz,
-                           int path_random, uint64_t seed, int real_base, int vec) {
+                           int path_random, uint64_t seed, int real_base, int vec, int row0,
+                           int row1) {
   const int slot = blockIdx.y;
   const uint32_t r = (uint32_t)(real_base + slot);
   const uint32_t flips = path_random ? (draw_word(seed, r, 0u, 1u) & ((1u << d) - 1u)) : 0u;
@@ -152,7 +154,7 @@ __global__ void k_crop_out(const uint8_t* __restrict__ sg, int64_t gp_vol, int g
   const uint8_t* src = sg + (int64_t)slot * gp_vol;
   uint8_t* dst = out + (int64_t)slot * gx * rows;
   const bool words = vec && ((ox & 3) == 0);
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+  for (int row = row0 + blockIdx.x; row < row1 && row < rows; row += gridDim.x) {
     const int y = row % gy, z = row / gy;
     const uint8_t* s = src + ox + (int64_t)gpx * ((y + oy) + (int64_t)gpy * (z + oz));
     uint8_t* o = dst + (int64_t)row * gx;
@@ -288,8 +290,10 @@ cudaError_t launch_hd_overlay(const int32_t* cells, const uint8_t* vals, int n, 
 
 cudaError_t launch_crop_out(const uint8_t* sg, int64_t gp_vol, const int gp[3], uint8_t* out,
                             const int g[3], int d, int n_real, int path_random, uint64_t seed,
-                            int real_base, cudaStream_t st) {
-  const int rows = g[1] * g[2];
+                            int real_base, cudaStream_t st, int row0, int row1) {
+  if (row1 < 0) row1 = g[1] * g[2];
+  const int rows = row1 - row0;
+  if (rows <= 0 || n_real <= 0) return cudaSuccess;
   // word copies need 4-aligned row starts in both arrays
   const int vec = ((g[0] | gp[0]) & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 3) == 0 &&
                   (reinterpret_cast<uintptr_t>(sg) & 3) == 0;
@@ -301,7 +305,8 @@ cudaError_t launch_crop_out(const uint8_t* sg, int64_t gp_vol, const int gp[3], 
     dim3 grid(bx, nr);
     k_crop_out<<<grid, threads, 0, st>>>(sg + (int64_t)r0 * gp_vol, gp_vol, gp[0], gp[1],
                                          out + (int64_t)r0 * g[0] * rows, g[0], g[1], g[2], d,
-                                         gp[2], path_random, seed, real_base + r0, vec);
+                                         gp[2], path_random, seed, real_base + r0, vec, row0,
+                                         row1);
   }
   return cudaGetLastError();
 }
