@@ -383,9 +383,11 @@ typedef struct ccw_net ccw_net;
 /* ccw_set_nn_path -- which kernel scores and selects the nearest TI windows
  * of the learned proposal (the proposals are the same up to FP32 rounding of
  * the scores): 0 (default) the tcgen05 kernel for tables of at most 3072
- * windows, else the FP32-lane kernel with several data events per CTA (at
- * most 6144 windows), else one CTA per data event; 1 never the tensor cores;
- * 2 always one CTA per data event. Process-wide; CCW_EINVAL for other
+ * windows (8 data events per CTA, 12 when a launch has more than 8 per SM
+ * and 12 fit in shared memory), else the FP32-lane kernel with several data
+ * events per CTA (at most 6144 windows), else one CTA per data event; 1
+ * never the tensor cores; 2 always one CTA per data event; 3 as 0 with 12
+ * events per CTA whenever they fit. Process-wide; CCW_EINVAL for other
  * values. */
 int ccw_set_nn_path(int32_t path);
 

@@ -441,7 +441,8 @@ def profile_read_proposal():
 
 def set_nn_path(path: int):
     """``ccw_set_nn_path``: 0 auto (tensor cores for small tables), 1 never the
-    tensor cores, 2 one CTA per data event."""
+    tensor cores, 2 one CTA per data event, 3 as 0 with twelve data events per
+    tensor-core CTA whenever they fit."""
     _check(load().ccw_set_nn_path(int(path)))
 
 

@@ -638,35 +638,44 @@ __global__ void __launch_bounds__(kNnThreads) k_nnsel_multi(const __grid_constan
 // The same selection with the scores from the tcgen05 tensor cores: the
 // tables are kept a second time in the MMA's K-major core-matrix layout, one
 // 16 KB block per 128 windows ([16 row groups][8 K chunks][8 rows][16 bytes],
-// zero rows past P); a CTA takes kNnTcG data events (MMA N = 16, columns
-// kNnTcG..15 zero), and for each mask type among them streams that type's
-// blocks through two shared-memory stages (bulk copies) into one MMA chain
-// (M = 128 windows, K = 64), the scores of every block in their own tensor
-// memory columns. The scores then move to shared memory, and one warp per
-// event selects as k_nnsel_multi does. For tables of at most kNnTcMaxP windows.
+// zero rows past P); a CTA takes G = 8 or 12 data events (MMA N = 16,
+// columns G..15 zero; one warp per event, at least 8), and for each mask type
+// among them streams that type's blocks through 2-8 shared-memory stages
+// (bulk copies) into one MMA chain (M = 128 windows, K = 64), the scores of
+// every block in their own tensor memory columns. The scores then move to
+// shared memory, and the selection runs in CTA-wide phases; the survivors'
+// keys take the stages' space once the MMAs are done. Twelve events per CTA
+// let a wavefront of up to 12 x (SM count) events run in one round of CTAs.
+// For tables of at most kNnTcMaxP windows.
 // ---------------------------------------------------------------------------
-constexpr int kNnTcG = 8;
 constexpr int kNnTcMaxP = 24 * 128;
 constexpr int kNnTcBlock = 128 * 64;   // BF16 values per 128-window block
-constexpr int kNnTcMaxStages = 6;
+constexpr int kNnTcMaxStages = 8;
+constexpr int kNnTcSmemMax = 227 * 1024;
 
 // Histograms of the tensor-core selector: bin b at b + b / 32, so that lane L
 // reading its 32 bins 32 L .. 32 L + 31 touches 32 different banks.
 constexpr int kBinsPad = kBins + kBins / 32;
 __device__ __forceinline__ int hpad(int b) { return b + (b >> 5); }
 
+template <int G>
 struct NnTcSmem {
   uint64_t bar_load[kNnTcMaxStages], bar_mma[kNnTcMaxStages], bar_done;
   uint32_t tslot;
   int flag;
-  int type[kNnTcG], ok[kNnTcG];
+  int type[G], ok[G];
   // per event: threshold, level-1 range, count above it, survivors, state
-  float thr[kNnTcG], lo1[kNnTcG], hi1[kNnTcG];
-  int above0[kNnTcG], need1[kNnTcG], cnt[kNnTcG];
-  float gap[kNnTcG];
-  int hist[kNnTcG][kBinsPad];
-  uint64_t keys[kNnTcG][kCollect];
+  float thr[G], lo1[G], hi1[G];
+  int above0[G], need1[G], cnt[G];
+  float gap[G];
+  int hist[G][kBinsPad];
 };
+
+// Threads of k_nnsel_tc<G>: one warp per event, at least 8 warps.
+template <int G>
+__host__ __device__ constexpr int nn_tc_threads() {
+  return G > 8 ? 32 * G : 256;
+}
 
 // Offset (bytes) of element (row, k) of a K-major operand block with 8-row
 // groups of all 8 K chunks: [rows / 8][8 chunks][8 rows][16 bytes].
@@ -674,16 +683,28 @@ __host__ __device__ __forceinline__ int nn_tc_off(int row, int k) {
   return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// k_nnsel_tc's shared memory for P windows: the fixed part, then as many
-// 16 KB stages (2 .. kNnTcMaxStages) as fit beside the scores.
-__host__ __device__ inline int nn_tc_head() { return ((int)sizeof(NnTcSmem) + 127) & ~127; }
-__host__ __device__ inline int nn_tc_stages(int64_t P) {
-  const int64_t room = 227 * 1024 - nn_tc_head() - 2048 - (int64_t)sizeof(float) * kNnTcG * P;
-  const int64_t n = room / 16384;
-  return (int)(n < 2 ? 2 : n > kNnTcMaxStages ? kNnTcMaxStages : n);
+// k_nnsel_tc<G>'s shared memory for P windows: the fixed part, the B
+// operand, then as many 16 KB stages as fit beside the scores (at least 2,
+// and enough to hold the survivors' keys, G x kCollect words, afterwards).
+template <int G>
+__host__ __device__ inline int nn_tc_head() {
+  return ((int)sizeof(NnTcSmem<G>) + 127) & ~127;
 }
+template <int G>
+__host__ __device__ inline int nn_tc_min_stages() {
+  const int k = (G * kCollect * 8 + 16383) / 16384;
+  return k < 2 ? 2 : k;
+}
+template <int G>
+__host__ __device__ inline int nn_tc_stages(int64_t P) {
+  const int64_t room = kNnTcSmemMax - nn_tc_head<G>() - 2048 - (int64_t)sizeof(float) * G * P;
+  const int64_t n = room / 16384;
+  const int lo = nn_tc_min_stages<G>();
+  return (int)(n < lo ? lo : n > kNnTcMaxStages ? kNnTcMaxStages : n);
+}
+template <int G>
 __host__ __device__ inline int nn_tc_smem(int64_t P) {
-  return nn_tc_head() + 2048 + nn_tc_stages(P) * 16384 + (int)(sizeof(float) * kNnTcG * P);
+  return nn_tc_head<G>() + 2048 + nn_tc_stages<G>(P) * 16384 + (int)(sizeof(float) * G * P);
 }
 
 // The threshold bin of a padded histogram (one warp, lane L taking bins
@@ -728,18 +749,21 @@ __device__ __forceinline__ void nn_threshold_pad(const int* hist, int np, int ab
   }
 }
 
-// Selection for the CTA's kNnTcG events in CTA-wide phases, with the
+// Selection for the CTA's G events in CTA-wide phases, with the
 // thresholds, survivors and proposals of nn_select_warp: each warp finds its
 // event's threshold (level 0 from the histogram the epilogue built, level 1
 // over the threshold bin when more than kSortSmall would survive), all
 // threads then build the level-1 histograms and collect every event's
-// survivors; each warp sorts its event's survivors (up to kCollect) in
-// registers. Sets S.gap[h] (-1: the event falls back to the full search).
-__device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
-                                                 const float* cache, int P, int i0, int tid,
-                                                 int warp, int lane) {
+// survivors; each warp sorts its event's survivors (up to kCollect, in
+// keys[h * kCollect ..]) in registers. Sets S.gap[h] (-1: the event falls
+// back to the full search).
+template <int G>
+__device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem<G>& S,
+                                                 const float* cache, uint64_t* keys, int P,
+                                                 int i0, int tid, int warp, int lane) {
+  constexpr int NT = nn_tc_threads<G>();
   const int np = (int)min((int64_t)a.n_prop, a.ti.P);
-  const bool mine = warp < kNnTcG && S.ok[warp];
+  const bool mine = warp < G && S.ok[warp];
   if (mine) {
     const float lo = -1.5f, hi = 1.5f, scale = kBins / (hi - lo);
     int bsel, above;
@@ -753,25 +777,25 @@ __device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
       S.hi1[warp] = lo + (bsel + 1) / scale;
       S.above0[warp] = above;
     }
-  } else if (warp < kNnTcG && lane == 0) {
+  } else if (warp < G && lane == 0) {
     S.need1[warp] = 0;
   }
-  if (warp < kNnTcG && lane == 0) S.cnt[warp] = 0;
+  if (warp < G && lane == 0) S.cnt[warp] = 0;
   __syncthreads();
   bool any = false;
 #pragma unroll
-  for (int h = 0; h < kNnTcG; ++h) any |= S.ok[h] && S.need1[h];
+  for (int h = 0; h < G; ++h) any |= S.ok[h] && S.need1[h];
   if (any) {
-    for (int i = tid; i < kNnTcG * kBinsPad; i += kNnThreads) {
+    for (int i = tid; i < G * kBinsPad; i += NT) {
       const int h = i / kBinsPad;
       if (S.ok[h] && S.need1[h]) (&S.hist[0][0])[i] = 0;
     }
     __syncthreads();
-    for (int h = 0; h < kNnTcG; ++h) {
+    for (int h = 0; h < G; ++h) {
       if (!S.ok[h] || !S.need1[h]) continue;
       const float lo = S.lo1[h], hi = S.hi1[h], scale = kBins / (hi - lo);
       const float* sc = cache + h * P;
-      for (int c = tid; c < P; c += kNnThreads) {
+      for (int c = tid; c < P; c += NT) {
         const float v = sc[c];
         if (v >= lo && v < hi)
           atomicAdd(&S.hist[h][hpad(min(kBins - 1, max(0, (int)((v - lo) * scale))))], 1);
@@ -787,15 +811,15 @@ __device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
     __syncthreads();
   }
   // survivors of every event, their keys in any order (sorted below)
-  for (int h = 0; h < kNnTcG; ++h) {
+  for (int h = 0; h < G; ++h) {
     if (!S.ok[h]) continue;
     const float thr = S.thr[h];
     const float* sc = cache + h * P;
-    for (int c = tid; c < P; c += kNnThreads) {
+    for (int c = tid; c < P; c += NT) {
       const float v = sc[c];
       if (v >= thr) {
         const int k = atomicAdd(&S.cnt[h], 1);
-        if (k < kCollect) S.keys[h][k] = nn_rank_key(v + 0.f, c);
+        if (k < kCollect) keys[h * kCollect + k] = nn_rank_key(v + 0.f, c);
       }
     }
   }
@@ -810,14 +834,14 @@ __device__ __forceinline__ void nn_select_cta_tc(const WaveArgs& a, NnTcSmem& S,
       }
     } else {
       // every survivor set sorted by its own warp in registers
-      const float gap =
-          ncoll <= kSortSmall ? nn_sort_regs_warp<4>(a, item, S.keys[warp], ncoll, np, lane)
-          : ncoll <= 2 * kSortSmall
-              ? nn_sort_regs_warp<8>(a, item, S.keys[warp], ncoll, np, lane)
-              : nn_sort_regs_warp<16>(a, item, S.keys[warp], ncoll, np, lane);
+      uint64_t* kw = keys + warp * kCollect;
+      const float gap = ncoll <= kSortSmall ? nn_sort_regs_warp<4>(a, item, kw, ncoll, np, lane)
+                        : ncoll <= 2 * kSortSmall
+                            ? nn_sort_regs_warp<8>(a, item, kw, ncoll, np, lane)
+                            : nn_sort_regs_warp<16>(a, item, kw, ncoll, np, lane);
       if (lane == 0) S.gap[warp] = gap;
     }
-  } else if (warp < kNnTcG && lane == 0) {
+  } else if (warp < G && lane == 0) {
     S.gap[warp] = -1.f;
   }
   __syncthreads();
@@ -839,22 +863,27 @@ __global__ void k_tables_mma(const __nv_bfloat16* __restrict__ tables, int64_t P
   }
 }
 
-__global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constant__ WaveArgs a) {
+template <int G>
+__global__ void __launch_bounds__(nn_tc_threads<G>(), 1)
+    k_nnsel_tc(const __grid_constant__ WaveArgs a) {
+  constexpr int NT = nn_tc_threads<G>();
   extern __shared__ __align__(128) unsigned char nn_smem[];
-  NnTcSmem& S = *reinterpret_cast<NnTcSmem*>(nn_smem);
+  NnTcSmem<G>& S = *reinterpret_cast<NnTcSmem<G>*>(nn_smem);
   const TiDev& t = a.ti;
   const int P = (int)t.P;
-  const int NS = nn_tc_stages(P);
-  unsigned char* eb = nn_smem + nn_tc_head();                          // B: 16 rows
+  const int NS = nn_tc_stages<G>(P);
+  unsigned char* eb = nn_smem + nn_tc_head<G>();                       // B: 16 rows
   unsigned char* stage = eb + 2048;                                    // NS x 16 KB
-  float* cache = reinterpret_cast<float*>(stage + NS * 16384);        // [kNnTcG][P]
+  float* cache = reinterpret_cast<float*>(stage + NS * 16384);        // [G][P]
+  // the survivors' keys [G][kCollect] over the stages, once the MMAs are done
+  uint64_t* keys = reinterpret_cast<uint64_t*>(stage);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int i0 = blockIdx.x * kNnTcG;
+  const int i0 = blockIdx.x * G;
   const int nblk = (P + 127) / 128;
   pdl_trigger();
   pdl_wait();
   unsigned long long* stats = a.call ? a.call->learn_stats : nullptr;
-  if (tid < kNnTcG) {
+  if (tid < G) {
     const int item = i0 + tid;
     int type = -1, ok = 0;
     if (item < a.n_items) {
@@ -869,11 +898,11 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
     S.type[tid] = ok ? type : -1;
     S.ok[tid] = ok;
   }
-  for (int i = tid; i < kNnTcG * kBinsPad; i += kNnThreads) (&S.hist[0][0])[i] = 0;
-  // B operand: the BF16 query of event h in row h (rows kNnTcG..15 zero)
-  for (int i = tid; i < 16 * 64; i += kNnThreads) {
+  for (int i = tid; i < G * kBinsPad; i += NT) (&S.hist[0][0])[i] = 0;
+  // B operand: the BF16 query of event h in row h (rows G..15 zero)
+  for (int i = tid; i < 16 * 64; i += NT) {
     const int h = i / 64, k = i % 64, item = i0 + h;
-    const float v = (h < kNnTcG && item < a.n_items) ? a.emb[(int64_t)item * 64 + k] : 0.f;
+    const float v = (h < G && item < a.n_items) ? a.emb[(int64_t)item * 64 + k] : 0.f;
     *reinterpret_cast<__nv_bfloat16*>(eb + nn_tc_off(h, k)) = __float2bfloat16_rn(v);
   }
   uint32_t ncols = 32;
@@ -895,13 +924,15 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
   const uint32_t tmem = S.tslot;
   const uint32_t idesc = instr_desc(true, 128, 16);
   const uint32_t eb_addr = smem_u32(eb), st_addr = smem_u32(stage);
-  const int quarter = warp & 3, half = warp >> 2;
+  // warp w reads tensor memory lanes 32 (w % 4) ..; the NT / 128 warps of a
+  // lane quarter take every (NT / 128)-th block
+  const int quarter = warp & 3, part = warp >> 2, parts = NT / 128;
   const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
   // blocks are numbered over all passes (b = passes * nblk + j): block b
   // uses stage b % NS, the (b / NS)-th use of that stage's barriers
   int issued = 0, waited = 0;   // thread 0: blocks whose copy was issued / landed
   uint32_t passes = 0;
-  for (int g = 0; g < kNnTcG; ++g) {
+  for (int g = 0; g < G; ++g) {
     const int type = S.type[g];
     if (type < 0) continue;
     bool first = true;
@@ -960,14 +991,14 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
     mbar_try_wait(&S.bar_done, passes & 1u);   // every thread observes the phase
     ++passes;
     tc_fence_after();
-    for (int j = half; j < nblk; j += 2) {
+    for (int j = part; j < nblk; j += parts) {
       uint32_t v[16];
       tmem_ld16(lane_base + (uint32_t)(j * 16), v);
       const int c = 128 * j + quarter * 32 + lane;
       if (c < P) {
         // scores to shared memory, and the level-0 histogram of each event
 #pragma unroll
-        for (int h = 0; h < kNnTcG; ++h)
+        for (int h = 0; h < G; ++h)
           if (S.type[h] == type) {
             const float sc = __uint_as_float(v[h]);
             cache[h * P + c] = sc;
@@ -991,14 +1022,14 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_nnsel_tc(const __grid_constan
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, ncols);
   if (failed) {
-    if (warp < kNnTcG && lane == 0 && i0 + warp < a.n_items)
+    if (warp < G && lane == 0 && i0 + warp < a.n_items)
       a.prop_gap[i0 + warp] = -1.f;   // no proposals: full search
     return;
   }
-  nn_select_cta_tc(a, S, cache, P, i0, tid, warp, lane);
-  if (a.fuse_rerank && warp < kNnTcG && S.ok[warp])
+  nn_select_cta_tc<G>(a, S, cache, keys, P, i0, tid, warp, lane);
+  if (a.fuse_rerank && warp < G && S.ok[warp])
     nn_rerank_warp(a, i0 + warp, S.gap[warp], reinterpret_cast<float*>(S.hist[warp]),
-                   S.keys[warp], lane);
+                   keys + warp * kCollect, lane);
 }
 
 // Event records from explicit block counts (the query entry point): known
@@ -1220,24 +1251,40 @@ bool nnsel_fuses_rerank(const WaveArgs& a) {
          nnsel_fuses_rerank_shape(a.ti.P, a.ti.nch, a.ti.rows, a.ti.Tj, a.n_prop);
 }
 
+template <int G>
+static cudaError_t launch_nnsel_tc(const WaveArgs& a, bool pdl, cudaStream_t st) {
+  // one CTA per SM when the scores take more than half of the tensor memory
+  int smem = nn_tc_smem<G>(a.ti.P);
+  if ((a.ti.P + 127) / 128 * 16 > 256 && smem < 120 * 1024) smem = 120 * 1024;
+  static int configured = 0;
+  if (smem > configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_nnsel_tc<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  return launch_pdl(k_nnsel_tc<G>, dim3((a.n_items + G - 1) / G), dim3(nn_tc_threads<G>()),
+                    smem, st, pdl, a);
+}
+
 cudaError_t launch_nnsel(const WaveArgs& a0, bool pdl, cudaStream_t st) {
   WaveArgs a = a0;
   a.fuse_rerank = nnsel_fuses_rerank(a0) ? 1 : 0;
-  if (g_nn_path == 0 && a.tables_mma && a.ti.P <= kNnTcMaxP) {
-    // one CTA per SM when the scores take more than half of the tensor memory
-    int smem = nn_tc_smem(a.ti.P);
-    if ((a.ti.P + 127) / 128 * 16 > 256 && smem < 120 * 1024) smem = 120 * 1024;
-    static int configured = 0;
-    if (smem > configured) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_nnsel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      configured = smem;
+  if ((g_nn_path == 0 || g_nn_path == 3) && a.tables_mma && a.ti.P <= kNnTcMaxP) {
+    // twelve events per CTA when eight would need more CTAs than there are
+    // SMs (and they fit beside the scores), else eight
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
     }
-    return launch_pdl(k_nnsel_tc, dim3((a.n_items + kNnTcG - 1) / kNnTcG), dim3(kNnThreads),
-                      smem, st, pdl, a);
+    const bool g12 = nn_tc_smem<12>(a.ti.P) <= kNnTcSmemMax &&
+                     (g_nn_path == 3 || a.n_items > 8 * sms);
+    return g12 ? launch_nnsel_tc<12>(a, pdl, st) : launch_nnsel_tc<8>(a, pdl, st);
   }
-  if (g_nn_path <= 1 && a.ti.P <= kScoreCache) {
+  if ((g_nn_path <= 1 || g_nn_path == 3) && a.ti.P <= kScoreCache) {
     const int smem = (int)(sizeof(NnMultiSmem) + sizeof(float) * kNnG * a.ti.P);
     static int configured = 0;
     if (smem > configured) {
@@ -1279,7 +1326,7 @@ cudaError_t launch_rerank(const WaveArgs& a, bool pdl, cudaStream_t st) {
 }  // namespace ccw
 
 extern "C" int ccw_set_nn_path(int32_t path) {
-  if (path < 0 || path > 2) return CCW_EINVAL;
+  if (path < 0 || path > 3) return CCW_EINVAL;
   ccw::g_nn_path = path;
   return CCW_OK;
 }

@@ -176,7 +176,7 @@ def test_tables_equal_the_fp64_encoder_oracle(ccw, ti):
     ti.attach_proposal(None)
 
 
-@pytest.fixture(params=[0, 1, 2])
+@pytest.fixture(params=[0, 1, 2, 3])
 def nn_path(request, ccw):
     ccw.set_nn_path(request.param)
     yield request.param
@@ -188,7 +188,8 @@ def test_nearest_windows_equal_a_numpy_ranking(ccw, ti, nn_path):
     same tables by dot product with the event's BF16 embedding (score
     descending, candidate ascending), up to FP32 rounding at the cut; its gap
     is the relative spread of their scores. Each selector kernel: tensor
-    cores, FP32 lanes with several events per CTA, one CTA per event."""
+    cores (8 and 12 events per CTA), FP32 lanes with several events per CTA,
+    one CTA per event."""
     net = ccw.Net(F, TJ, seed=6)
     ti.attach_proposal(net, 64, 0.0)
     tables = ti.export(4).float().cpu().numpy().astype(np.float64)
@@ -250,10 +251,20 @@ def exact_scores(ccw, ti, counts):
     return np.stack([o.search(T, de[i], maps=True)["scores"] for i in range(len(de))])
 
 
+@pytest.fixture(params=[0, 3])
+def tc_events(request, ccw):
+    """The tensor-core selector with 8 (auto at this size) or 12 data events
+    per CTA."""
+    ccw.set_nn_path(request.param)
+    yield request.param
+    ccw.set_nn_path(0)
+
+
 @pytest.mark.parametrize("precision", [0, 2])
-def test_settled_patches_take_the_exact_best_proposal(ccw, ti, precision):
+def test_settled_patches_take_the_exact_best_proposal(ccw, ti, precision, tc_events):
     """The CCF kernels (FP32 lanes or tensor cores) skip settled patches; the
-    finish kernel takes their picks from the re-ranked proposals."""
+    finish kernel takes their picks from the re-ranked proposals (fused into
+    the selector)."""
     net = ccw.Net(F, TJ, seed=1)
     ti.attach_proposal(net, 64, -0.5)    # every patch with proposals is settled
     out, log, counts = run(ccw, ti, 4, 1, precision=precision)
