@@ -930,7 +930,7 @@ __global__ void __launch_bounds__(nn_tc_threads<G>(), 1)
   const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
   // blocks are numbered over all passes (b = passes * nblk + j): block b
   // uses stage b % NS, the (b / NS)-th use of that stage's barriers
-  int issued = 0, waited = 0;   // thread 0: blocks whose copy was issued / landed
+  int issued = 0;   // thread 0: blocks whose copy was issued
   uint32_t passes = 0;
   for (int g = 0; g < G; ++g) {
     const int type = S.type[g];
@@ -938,53 +938,50 @@ __global__ void __launch_bounds__(nn_tc_threads<G>(), 1)
     bool first = true;
     for (int h = 0; h < g; ++h) first &= S.type[h] != type;
     if (!first) continue;   // scored with an earlier event of this type
+    const int b0 = (int)passes * nblk;
+    // CTAs start at different blocks of the table so that they do not all
+    // read the same L2 lines at the same time
+    const int start = (int)((blockIdx.x * 5u) % (unsigned)nblk);
+    volatile int* vflag = &S.flag;
     if (tid == 0) {
+      // copies: block b into stage b % NS once the MMAs of block b - NS,
+      // the stage's previous use, are done
       const __nv_bfloat16* tab = a.tables_mma + (int64_t)type * nblk * kNnTcBlock;
-      const int b0 = (int)passes * nblk;
-      // CTAs start at different blocks of the table so that they do not all
-      // read the same L2 lines at the same time
-      const int start = (int)((blockIdx.x * 5u) % (unsigned)nblk);
-      auto blk = [&](int b) { return (start + b - b0) % nblk; };
-      auto issue = [&](int b) {
+      for (int b = b0; b < b0 + nblk; ++b) {
         const int sidx = b % NS;
+        if (b >= NS && !mbar_wait_bounded(&S.bar_mma[sidx], (uint32_t)(b / NS - 1) & 1u)) {
+          *vflag = 1;
+          break;
+        }
+        if (*vflag) break;
         mbar_arrive_expect_tx(&S.bar_load[sidx], 16384u);
-        bulk_g2s(stage + sidx * 16384, tab + (int64_t)blk(b) * kNnTcBlock, 16384u,
-                 &S.bar_load[sidx]);
+        bulk_g2s(stage + sidx * 16384, tab + (int64_t)((start + b - b0) % nblk) * kNnTcBlock,
+                 16384u, &S.bar_load[sidx]);
         issued = b + 1;
-      };
-      for (int b = b0; b < b0 + NS && b < b0 + nblk; ++b) issue(b);
+      }
+    } else if (tid == 32) {
+      // MMAs: block b's scores into columns 16 x (its table block); each
+      // thread alone polls its barriers (the others wait at the CTA barrier)
       bool ok = true;
       for (int b = b0; b < b0 + nblk; ++b) {
         const int sidx = b % NS;
-        if (!mbar_wait_bounded(&S.bar_load[sidx], (uint32_t)(b / NS) & 1u)) {
+        if (*vflag || !mbar_wait_bounded(&S.bar_load[sidx], (uint32_t)(b / NS) & 1u)) {
           ok = false;
           break;
         }
-        waited = b + 1;
         tc_fence_after();
+        const uint32_t col = (uint32_t)(((start + b - b0) % nblk) * 16);
 #pragma unroll
         for (int k16 = 0; k16 < 4; ++k16)
-          mma_f16(tmem + (uint32_t)(blk(b) * 16),
+          mma_f16(tmem + col,
                   smem_desc(st_addr + (uint32_t)(sidx * 16384 + k16 * 256), 128u, 1024u),
                   smem_desc(eb_addr + (uint32_t)(k16 * 256), 128u, 1024u), idesc,
                   k16 > 0 ? 1u : 0u);
         mma_commit(&S.bar_mma[sidx]);
-        // refill the stage of the previous block once its MMAs are done
-        // (the tensor pipe meanwhile works on this block)
-        const int pb = b - 1;
-        if (pb >= b0 && pb + NS < b0 + nblk) {
-          if (!mbar_wait_bounded(&S.bar_mma[pb % NS], (uint32_t)(pb / NS) & 1u)) {
-            ok = false;
-            break;
-          }
-          issue(pb + NS);
-        }
       }
-      if (!ok) S.flag = 1;
+      if (!ok) *vflag = 1;
       mma_commit(&S.bar_done);
-      // thread 0 alone waits (the others wait at the barrier, not polling
-      // beside it in its warp)
-      if (!mbar_wait_bounded(&S.bar_done, passes & 1u)) S.flag = 1;
+      if (!mbar_wait_bounded(&S.bar_done, passes & 1u)) *vflag = 1;
     }
     __syncthreads();
     if (S.flag) break;
@@ -1015,7 +1012,8 @@ __global__ void __launch_bounds__(nn_tc_threads<G>(), 1)
     // a copy or commit never arrived: let what is in flight land (bounded)
     if (a.status) atomicOr(a.status, kStatusTimeout);
     mbar_wait_bounded(&S.bar_done, passes & 1u);
-    for (int b = waited; b < issued; ++b)
+    // the last copy issued into each stage (an earlier one has landed)
+    for (int b = issued - NS > 0 ? issued - NS : 0; b < issued; ++b)
       mbar_wait_bounded(&S.bar_load[b % NS], (uint32_t)(b / NS) & 1u);
   }
   __syncthreads();
