@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kEncThreads, 1)
   uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + g.o_bar + 16);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + g.o_bar + 8);
   volatile int* flag = reinterpret_cast<volatile int*>(sm + g.o_bar + 12);
+  pdl_trigger();
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(wbar, 1);
@@ -172,6 +173,10 @@ __global__ void __launch_bounds__(kEncThreads, 1)
   // every plane starts zero: the padding rows and columns are never written
   for (int i = g.o_a4 / 16 + tid; i < g.o_bar / 16; i += kEncThreads)
     reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  // the predecessor's records are complete from here on, and every earlier
+  // kernel has released its tensor memory (allocating before this wait could
+  // block a predecessor's allocation on the same SM while this CTA waits)
+  pdl_wait();
   if (warp == 0) tmem_alloc(tslot, g.tmem_cols);
   // one thread waits for the copy (the others wait at the barrier, not
   // polling beside it), then every thread observes the completed phase
@@ -452,7 +457,7 @@ cudaError_t enc_tc_build_image(const float* P, int C, int tj, void* img, cudaStr
 // here into temporary memory when NULL); returns cudaErrorNotSupported
 // (nothing launched) when the shape does not fit.
 static cudaError_t encode_tc(const float* P, const void* wimg, int C, int tj, EncSrc src, int N,
-                             float* emb, int* status, cudaStream_t st) {
+                             float* emb, int* status, cudaStream_t st, bool pdl = false) {
   EncTc g;
   if (!enc_tc_plan(C, tj, &g)) return cudaErrorNotSupported;
   if (N <= 0) return cudaSuccess;
@@ -482,9 +487,9 @@ static cudaError_t encode_tc(const float* P, const void* wimg, int C, int tj, En
   }
   const int ngroups = (N + g.G - 1) / g.G;
   const int grid = ngroups < sms ? ngroups : sms;
-  k_encode_tc<<<grid, kEncThreads, g.smem, st>>>((const unsigned char*)wimg, net_shape(C, tj), g,
-                                                  src, N, emb, status);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e =
+      launch_pdl(k_encode_tc, dim3(grid), dim3(kEncThreads), g.smem, st, pdl && !tmp,
+                 (const unsigned char*)wimg, net_shape(C, tj), g, src, N, emb, status);
   if (tmp) cudaFreeAsync(tmp, st);
   return e;
 }
@@ -498,15 +503,18 @@ cudaError_t net_infer_tc(const float* P, const void* wimg, int C, int tj, const 
 
 // The same pass on the block counts of event records (no separate input
 // kernel): sample i = record rec + i * stride.
+// With `pdl` the kernel is launched with programmatic stream serialization:
+// its set-up overlaps the predecessor (the event kernel of the same step).
 cudaError_t net_infer_tc_records(const float* P, const void* wimg, int C, int tj,
                                  const unsigned char* rec, int64_t stride, int counts_off,
-                                 float inv, int N, float* emb, int* status, cudaStream_t st) {
+                                 float inv, int N, float* emb, int* status, cudaStream_t st,
+                                 bool pdl) {
   EncSrc src{};
   src.rec = rec;
   src.stride = stride;
   src.counts_off = counts_off;
   src.inv = inv;
-  return encode_tc(P, wimg, C, tj, src, N, emb, status, st);
+  return encode_tc(P, wimg, C, tj, src, N, emb, status, st, pdl);
 }
 
 }  // namespace ccw

@@ -881,7 +881,24 @@ __global__ void __launch_bounds__(nn_tc_threads<G>(), 1)
   const int i0 = blockIdx.x * G;
   const int nblk = (P + 127) / 128;
   pdl_trigger();
+  // set-up that reads nothing the predecessor writes, while it finishes
+  for (int i = tid; i < G * kBinsPad; i += NT) (&S.hist[0][0])[i] = 0;
+  uint32_t ncols = 32;
+  while ((int)ncols < nblk * 16) ncols <<= 1;
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&S.bar_load[k], 1);
+      mbar_init(&S.bar_mma[k], 1);
+    }
+    mbar_init(&S.bar_done, 1);
+    S.flag = 0;
+    fence_mbar_init();
+  }
+  // the embeddings and event records are complete, and every earlier kernel
+  // has released its tensor memory (allocating before this wait could block
+  // a predecessor's allocation on the same SM while this CTA waits for it)
   pdl_wait();
+  if (warp == 0) tmem_alloc(&S.tslot, ncols);
   unsigned long long* stats = a.call ? a.call->learn_stats : nullptr;
   if (tid < G) {
     const int item = i0 + tid;
@@ -898,25 +915,12 @@ __global__ void __launch_bounds__(nn_tc_threads<G>(), 1)
     S.type[tid] = ok ? type : -1;
     S.ok[tid] = ok;
   }
-  for (int i = tid; i < G * kBinsPad; i += NT) (&S.hist[0][0])[i] = 0;
   // B operand: the BF16 query of event h in row h (rows G..15 zero)
   for (int i = tid; i < 16 * 64; i += NT) {
     const int h = i / 64, k = i % 64, item = i0 + h;
     const float v = (h < G && item < a.n_items) ? a.emb[(int64_t)item * 64 + k] : 0.f;
     *reinterpret_cast<__nv_bfloat16*>(eb + nn_tc_off(h, k)) = __float2bfloat16_rn(v);
   }
-  uint32_t ncols = 32;
-  while ((int)ncols < nblk * 16) ncols <<= 1;
-  if (tid == 0) {
-    for (int k = 0; k < NS; ++k) {
-      mbar_init(&S.bar_load[k], 1);
-      mbar_init(&S.bar_mma[k], 1);
-    }
-    mbar_init(&S.bar_done, 1);
-    S.flag = 0;
-    fence_mbar_init();
-  }
-  if (warp == 0) tmem_alloc(&S.tslot, ncols);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -1186,7 +1190,8 @@ int64_t enc_tc_image_bytes(int C, int tj);
 bool net_infer_fused_fits(int C, int tj);
 cudaError_t net_infer_tc_records(const float* P, const void* wimg, int C, int tj,
                                  const unsigned char* rec, int64_t stride, int counts_off,
-                                 float inv, int N, float* emb, int* status, cudaStream_t st);
+                                 float inv, int N, float* emb, int* status, cudaStream_t st,
+                                 bool pdl);
 
 // Kernel launches of one launch_encode_items.
 int encode_items_launches(int F, int Tj, bool img) {
@@ -1200,7 +1205,7 @@ cudaError_t launch_encode_items(const WaveArgs& a, float* x, float* act, bool pd
     // the tensor-core pass reads the block counts from the event records
     return net_infer_tc_records(a.net, a.enc_img, a.ti.F, a.ti.Tj, a.ev.base, a.ev.stride,
                                 a.ev.counts_off, 1.f / (float)a.ti.sd, a.n_items, a.emb,
-                                a.status, st);
+                                a.status, st, pdl);
   cudaError_t e = launch_pdl(k_event_inputs, dim3(a.n_items), dim3(128), 0, st, pdl, a, x);
   if (e != cudaSuccess) return e;
   return net_infer(a.net, a.ti.F, a.ti.Tj, x, a.n_items, act, a.emb, st, a.status, 0,
