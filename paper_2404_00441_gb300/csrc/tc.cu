@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
     bulk_g2s(Bs, reinterpret_cast<const unsigned char*>(a.bmat) + (int64_t)ntile * b_bytes,
              b_bytes, &bar[kTcBarB]);
   }
+  int searched = 0;   // items of this thread that need the search
   for (int i = tid; i < nt; i += kTcThreads) {
     const int item = ntile * nt + i;
     int4 m = make_int4(0, 0, 0, 0);
@@ -157,6 +158,15 @@ __global__ void __launch_bounds__(kTcThreads) k_ccf_tc(const __grid_constant__ W
       m.w = (MODE == kModeMap) ? 1 : (m.x > 0 && !em[kEvResolved]);
     }
     meta[i] = m;
+    searched |= m.w;
+  }
+  // an N-tile none of whose items needs the search (no data, or settled by
+  // the learned proposal) writes nothing: its copies land and it returns
+  if (!__syncthreads_or(searched)) {
+    if (tid == 0 && (!mbar_wait_bounded(&bar[kTcBarA], 0u) ||
+                     !mbar_wait_bounded(&bar[kTcBarB], 0u)) && a.status)
+      atomicOr(a.status, kStatusTimeout);
+    return;
   }
   unsigned long long* work = (MODE == kModeSim) ? a.call->work : a.work;
   if (work && mg == 0 && blockIdx.z == 0 && MODE != kModeMap) {
