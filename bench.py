@@ -144,7 +144,8 @@ def profiled_traffic(kernel: str, workload: str, tile: int, items_per_launch: fl
     import hashlib
     if items_per_launch <= 0:
         return None
-    src = {"k_ccf_tc": "tc.cu", "k_ccf_tcs": "tcs.cu", "k_ccf_simt": "ccf_simt.cu"}[kernel]
+    src = {"k_ccf_tc": "tc.cu", "k_ccf_tcs": "tcs.cu", "k_ccf_simt": "ccf_simt.cu",
+           "k_nnsel_tc": "proposal.cu", "k_encode_tc": "encoder_tc.cu"}[kernel]
     path = os.path.join(ROOT, "paper_2404_00441_gb300", "csrc", src)
     try:
         with open(path, "rb") as f:
@@ -529,7 +530,15 @@ def ours_line(args, world, m):
                                                     "on tcgen05, selection and exact "
                                                     "re-rank)"),
                 "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
-                "traffic": None, "kernel_ms_per_step": ms,
+                # one launch per wavefront
+                "traffic": profiled_traffic(top, args.workload, tile,
+                                            m["items_per_step"] / max(m.get("wavefronts") or 1,
+                                                                      1)),
+                "traffic_note": "cold-cache DRAM bytes (read + write) per launch: ncu's bytes "
+                                "per data event (profiles/traffic.txt) times the call's mean "
+                                "data events per launch; null unless taken on this workload, "
+                                "tiling and kernel source",
+                "kernel_ms_per_step": ms,
                 "timing": "CUDA events around the proposal kernels inside the captured graph, "
                           "second pass of the same K steps",
                 "peak_source": tsrc,
