@@ -64,3 +64,43 @@ def test_wavefront_driver_equals_raster_simulation():
         assert res["pick"] == rlog[p, 0]
         sg[win] = np.where(hw != 255, hw, o.reconstruct(T, res["pick"]))
     assert np.array_equal(sg[:grid[1], :grid[0]], ref)
+
+
+@pytest.mark.parametrize("cut", [0, 1])
+def test_rows_before_the_next_patch_row_are_final_2d(cut):
+    """The host read-back copies output rows y < (i + 1)(T - OR) as soon as
+    patch row i is pasted: no later patch, boundary cut included, writes
+    them. Checked in raster order on the oracle (the wavefront order reaches
+    the same states, test above): the realization after the first i + 1
+    patch rows agrees there with the finished one."""
+    ti = synth.ribbon_ti(120, 110, n_ribbons=6, seed=4)
+    T, Ov = 16, 4
+    S = T - Ov
+    grid = (95, 83)
+    o = O.OracleTI(ti, 2, 1)
+    npch, _ = O.lattice(2, grid, T, Ov)
+    full, _ = o.simulate(grid, T, Ov, K=2, seed=5, r=1, cut=cut)
+    for i in range(npch[1] - 1):
+        part, _ = o.simulate(grid, T, Ov, K=2, seed=5, r=1, cut=cut,
+                             max_patches=(i + 1) * npch[0])
+        y1 = min(grid[1], (i + 1) * S)
+        assert np.array_equal(part[:y1], full[:y1]), i
+        # and the next rows are not final yet: the next patch row writes them
+        assert not np.array_equal(part[y1:], full[y1:]), i
+
+
+def test_slabs_before_the_next_patch_slab_are_final_3d():
+    """The same in 3D along z: after patch slab i the cells z < (i + 1)(T - OR)
+    are final."""
+    ti = synth.tube_lobe_ti_3d(40, 36, 32, seed=5)
+    T, Ov = 8, 2
+    S = T - Ov
+    grid = (26, 24, 22)
+    o = O.OracleTI(ti, 4, 1)
+    npch, _ = O.lattice(3, grid, T, Ov)
+    full, _ = o.simulate(grid, T, Ov, K=3, seed=9, r=0)
+    per_slab = npch[0] * npch[1]
+    for i in range(npch[2] - 1):
+        part, _ = o.simulate(grid, T, Ov, K=3, seed=9, r=0, max_patches=(i + 1) * per_slab)
+        z1 = min(grid[2], (i + 1) * S)
+        assert np.array_equal(part[:z1], full[:z1]), i
