@@ -3,7 +3,9 @@ together. With T >= 2 OR this gives exactly the raster-order result of
 Algorithm 1: patches of one wavefront never share a cell, and every patch
 that shares a cell with patch p comes before p in both orders. Checked here
 on the CPU with the oracle's own search and reconstruction steps driven in
-wavefront order."""
+wavefront order (2D and 3D, forward and mirrored paths), which also pins the
+oracle's loop of Algorithm 1 (window placement, data event, paste, crop)
+against a restatement of it."""
 import itertools
 
 import numpy as np
@@ -104,3 +106,81 @@ def test_slabs_before_the_next_patch_slab_are_final_3d():
         part, _ = o.simulate(grid, T, Ov, K=3, seed=9, r=0, max_patches=(i + 1) * per_slab)
         z1 = min(grid[2], (i + 1) * S)
         assert np.array_equal(part[:z1], full[:z1]), i
+
+
+def drive_in_wavefronts(o, grid, T, Ov, K, cells, vals, seed, r, flips):
+    """Algorithm 1 restated with the oracle's search and reconstruction
+    steps, patches in wavefront order (reversed inside each wave), on a path
+    mirrored along the axes set in `flips`: the grid sits at the high end of
+    the padded lattice along a mirrored axis, whose patch origins run from
+    the high end down; the patterns themselves are not mirrored. Returns the
+    cropped realization."""
+    d = len(grid)
+    npch, gp = O.lattice(d, grid, T, Ov)
+    S = T - Ov
+    off = [gp[a] - grid[a] if flips >> a & 1 else 0 for a in range(d)]
+    shape = tuple(gp[a] for a in reversed(range(d)))
+    hd = np.full(shape, 255, np.uint8)
+    for c, v in zip(cells, vals):
+        idx = tuple(c[a] + off[a] for a in reversed(range(d)))
+        hd[idx] = min(hd[idx], v)
+    sg = np.full(shape, 255, np.uint8)
+    pats = list(itertools.product(*[range(npch[a]) for a in reversed(range(d))]))
+    ips = [tuple(reversed(q)) for q in pats]              # (ix, iy[, iz])
+    def raster(ip):
+        idx = 0
+        for a in reversed(range(d)):
+            idx = idx * npch[a] + ip[a]
+        return idx
+    order = sorted(ips, key=lambda ip: (wave_of(ip), -raster(ip)))
+    for ip in order:
+        p = raster(ip)
+        org = [gp[a] - T - S * ip[a] if flips >> a & 1 else S * ip[a] for a in range(d)]
+        win = tuple(slice(org[a], org[a] + T) for a in reversed(range(d)))
+        hw = hd[win]
+        de = np.where(hw != 255, hw, sg[win])
+        res = o.search(T, de, hw, K=K, seed=seed, r=r, p=p)
+        sg[win] = np.where(hw != 255, hw, o.reconstruct(T, res["pick"]))
+    crop = tuple(slice(off[a], off[a] + grid[a]) for a in reversed(range(d)))
+    return sg[crop]
+
+
+def test_wavefront_driver_equals_raster_simulation_mirrored():
+    """Mirrored paths (path_random = 1): each of the three non-trivial flips
+    of a 2D path, hard data included."""
+    ti = synth.channel_lens_ti(160, 150, seed=2, tol=0.2)
+    F, J, T, Ov, K = 3, 1, 16, 4, 3
+    grid = (75, 61)
+    cells, vals = synth.sample_hard_data(synth.channel_lens_ti(75, 61, seed=3, tol=0.3), 20, 4)
+    o = O.OracleTI(ti, F, J)
+    seed = 23
+    seen = set()
+    for r in range(64):
+        flips = O.path_flips(2, seed, r)
+        if flips == 0 or flips in seen:
+            continue
+        seen.add(flips)
+        ref, _ = o.simulate(grid, T, Ov, K=K, path_random=1, hd_cells=cells, hd_vals=vals,
+                            seed=seed, r=r)
+        got = drive_in_wavefronts(o, grid, T, Ov, K, cells, vals, seed, r, flips)
+        assert np.array_equal(got, ref), (r, flips)
+    assert seen == {1, 2, 3}
+
+
+def test_wavefront_driver_equals_raster_simulation_3d():
+    """3D (w = i_x + 2 i_y + 4 i_z), forward and one mirrored path, hard
+    data included."""
+    ti = synth.tube_lobe_ti_3d(36, 32, 30, seed=5)
+    F, J, T, Ov, K = 4, 1, 8, 2, 3
+    grid = (22, 20, 18)
+    cells, vals = synth.sample_hard_data(synth.tube_lobe_ti_3d(22, 20, 18, seed=6), 25, 7)
+    o = O.OracleTI(ti, F, J)
+    seed = 31
+    ref, _ = o.simulate(grid, T, Ov, K=K, hd_cells=cells, hd_vals=vals, seed=seed, r=0)
+    got = drive_in_wavefronts(o, grid, T, Ov, K, cells, vals, seed, 0, 0)
+    assert np.array_equal(got, ref)
+    r = next(r for r in range(64) if O.path_flips(3, seed, r) == 7)
+    ref, _ = o.simulate(grid, T, Ov, K=K, path_random=1, hd_cells=cells, hd_vals=vals,
+                        seed=seed, r=r)
+    got = drive_in_wavefronts(o, grid, T, Ov, K, cells, vals, seed, r, 7)
+    assert np.array_equal(got, ref)
