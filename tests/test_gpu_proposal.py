@@ -339,3 +339,42 @@ def test_trained_proposal_gains_and_keeps_statistics(ccw, ti):
     assert np.all(np.abs(vp - vl) <= 0.1 * vp + 0.005)
     assert np.all(np.abs(sp["js"] - sl["js"]) <= 0.02)
     ti.attach_proposal(None)
+
+
+def test_benchmarked_learned_batch_sampled(ccw, ti):
+    """The learned+batched form in the launch configuration the benchmark
+    times (256 realizations of 512^2, its BF16 tiling; the widest wavefronts
+    hold 1,792 data events, so the selector runs 12 per CTA): sampled settled
+    patches take the exact best of their proposals, sampled searched patches
+    the exact best candidate (scores from the CPU oracle)."""
+    prec, tile = configs.bench_tile("c5")
+    net = ccw.Net(F, TJ, seed=1)
+    ti.attach_proposal(net, 64, -0.5)    # every patch with proposals is settled
+    out, log, counts = ccw.simulate_groups(
+        ti, [dict(grid=GRID, n_real=256)], topk=1, seed=5, want_log=True, want_counts=True,
+        learned=1, precision=prec, ccf_tile=tile)[0]
+    flags = log[..., 3].cpu().numpy()
+    picks = log[..., 0].cpu().numpy()
+    scores = log[..., 1].cpu().numpy()
+    settled = (flags & ccw.LOG_FLAG_PROPOSAL) != 0
+    assert settled.mean() > 0.5
+    rng = np.random.default_rng(3)
+    sidx = np.argwhere(settled)
+    sidx = sidx[rng.choice(len(sidx), min(150, len(sidx)), replace=False)]
+    c = counts[tuple(torch.from_numpy(sidx.T).cuda())].contiguous()
+    prop, gap, _ = ti.proposal_query(c)
+    prop = prop.cpu().numpy()
+    sc = exact_scores(ccw, ti, c.cpu().numpy())
+    for j, (r, p) in enumerate(sidx):
+        s = sc[j][prop[j]]
+        best = np.lexsort((prop[j], -s))[0]
+        assert picks[r, p] == prop[j][best] and scores[r, p] == s[best], (r, p)
+    full = ((flags & ccw.LOG_FLAG_DONE) != 0) & ~settled & ((flags & 1) == 0)
+    fidx = np.argwhere(full)
+    assert len(fidx) > 0
+    fidx = fidx[rng.choice(len(fidx), min(60, len(fidx)), replace=False)]
+    cf = counts[tuple(torch.from_numpy(fidx.T).cuda())].cpu().numpy()
+    scf = exact_scores(ccw, ti, cf)
+    for j, (r, p) in enumerate(fidx):
+        assert picks[r, p] == scf[j].argmax() and scores[r, p] == scf[j].max(), (r, p)
+    ti.attach_proposal(None)
